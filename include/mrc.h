@@ -1,0 +1,180 @@
+/*
+ * mrc.h -- C ABI of libmrc: FFT-Newton inversion of matrix-valued sequences
+ * and the Markov renewal functionals derived from it, on one NVIDIA GB300.
+ *
+ * Method: Kordalis & Trevezas, "Algebraic and FFT-Based Methods for
+ * Discrete-Time Matrix Convolutions with Applications to Semi-Markov Models"
+ * (arXiv 2605.30379).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - A matrix-valued sequence X in S_{r,c} (Section 2) truncated to k < N is an
+ *   array of N*r*c doubles, row-major per coefficient, time slowest:
+ *       X[k*r*c + i*c + j] = X(k)_{ij}.
+ * - Array arguments are DEVICE pointers owned by the caller unless stated
+ *   otherwise.  They must stay valid until the work queued on `stream` has
+ *   finished.  Outputs must not alias inputs.
+ * - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *   stream.  Every call only enqueues work on `stream` and returns, except
+ *   where `report` (host pointer) is non-NULL: then the call synchronises the
+ *   stream, reads the device status word and fills `report`.
+ * - Host-side argument errors are returned before anything is enqueued.
+ *   Errors found on the device (a singular A(0)) are written to a status word
+ *   in the context; they are returned by a call with a non-NULL report, or by
+ *   mrc_sync_status().  No C++ exception crosses this boundary.
+ * - One context per host thread; a context is bound to the device it was
+ *   created on.  The context owns its workspace (device memory, grown on
+ *   demand up to max_workspace_bytes) and the twiddle tables.
+ * - Sizes: 1 <= d <= 512, 1 <= N <= 2^20; calls whose workspace would exceed
+ *   the context cap return MRC_ERR_NO_MEMORY.
+ */
+#ifndef MRC_H
+#define MRC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mrc_ctx mrc_ctx;
+
+typedef enum {
+    MRC_OK = 0,
+    MRC_ERR_INVALID_ARG = 1,   /* bad size, NULL pointer or option */
+    MRC_ERR_SINGULAR_A0 = 2,   /* A(0) singular: no convolutional inverse (Theorem 2.2) */
+    MRC_ERR_NO_MEMORY = 3,     /* workspace above the context cap or cudaMalloc failed */
+    MRC_ERR_CUDA = 4,          /* a CUDA runtime call or kernel launch failed */
+    MRC_ERR_NOT_CONVERGED = 5, /* refinement left max|rho| above target_residual */
+    MRC_ERR_TIMEOUT = 6,       /* reserved: a bounded device wait gave up */
+    MRC_ERR_UNIMPLEMENTED = 7
+} mrc_status;
+
+typedef enum {
+    MRC_FP64 = 0,  /* every stage in IEEE binary64 on the FP64 pipes */
+    MRC_MIXED = 1  /* FP32 Newton + double-float (FP32-pair) residual refinement */
+} mrc_precision;
+
+typedef struct {
+    int prec;               /* mrc_precision */
+    int refine_sweeps;      /* MRC_MIXED: residual/correction sweeps (default 1, max 4) */
+    double target_residual; /* MRC_MIXED with a report: max|rho_L| bound checked after refinement (0 = no check) */
+    int autotune;           /* reserved; 0 */
+} mrc_options;
+
+typedef struct {
+    double res_left_l1;   /* sum_k ||rho_L(k)||_F over k < N (Frobenius form of ||.||_{1,N}) */
+    double res_right_l1;  /* same for rho_R, when computed; else -1 */
+    double res_max_abs;   /* max_{k,i,j} |rho_L(k)_{ij}| (or of rho_R when only R was asked) */
+    int levels;           /* Newton doubling levels run */
+    int sweeps;           /* refinement sweeps run */
+    double ms;            /* device time of the call (CUDA events) */
+} mrc_report;
+
+/* Library and status helpers. */
+const char *mrc_status_string(mrc_status s);
+const char *mrc_version(void);
+
+/* Create a context on `device` (cudaSetDevice is called).  max_workspace_bytes
+ * caps the device workspace (0 = no cap).  *ctx receives an owned handle. */
+mrc_status mrc_create(mrc_ctx **ctx, int device, size_t max_workspace_bytes);
+
+/* Free the context's workspace and handle.  Synchronises the device first. */
+mrc_status mrc_destroy(mrc_ctx *ctx);
+
+/* Synchronise `stream`, return and clear the context's device status word. */
+mrc_status mrc_sync_status(mrc_ctx *ctx, void *stream);
+
+/* Bytes of workspace mrc_inverse would use for (d, N, prec). */
+size_t mrc_inverse_workspace_bytes(int d, int64_t N, int prec);
+
+/*
+ * mrc_inverse -- psi = A^{(-1)} mod x^N in the truncated algebra A_{d,N}
+ * (Proposition 2.3), by Newton doubling B_{r+1} = B_r * (2 e0 - A * B_r)
+ * mod x^{2^{r+1}} (Eq. (newton), Appendix D "Newton inversion") with the
+ * products done by zero-padded FFT (Eq. (fft-convolution)) and B_0(0) = A(0)^{-1}
+ * by Gauss-Jordan with partial pivoting.
+ *   d, N    : matrix dimension and horizon.
+ *   A       : device, [N][d][d] doubles, the sequence to invert; A(0) must be
+ *             nonsingular.  For the Markov renewal sequence pass A = e0 - q.
+ *   psi     : device, [N][d][d] doubles, receives the inverse.
+ *   opt     : host, may be NULL (= MRC_FP64).  MRC_MIXED runs the Newton levels
+ *             in FP32 and then `refine_sweeps` sweeps of
+ *             psi <- psi + psi * (e0 - A * psi) with the residual in double-float.
+ *   stream  : cudaStream_t.
+ *   report  : host, may be NULL; if set, the call synchronises, fills levels,
+ *             sweeps and ms, and (MRC_MIXED with target_residual > 0) the final
+ *             left residual norms.
+ * Errors: MRC_ERR_INVALID_ARG, MRC_ERR_NO_MEMORY, MRC_ERR_CUDA, and with a
+ * report MRC_ERR_SINGULAR_A0 / MRC_ERR_NOT_CONVERGED.
+ */
+mrc_status mrc_inverse(mrc_ctx *ctx, int d, int64_t N, const double *A, double *psi,
+                       const mrc_options *opt, void *stream, mrc_report *report);
+
+/*
+ * mrc_inverse_batched -- mrc_inverse over `nmodels` independent models with
+ * their own d[b] and N[b] (host arrays), A[b]/psi[b] device pointers held in
+ * HOST arrays of pointers.  All models are enqueued on `stream` in order.
+ * report (nullable, host) receives one mrc_report per model.
+ */
+mrc_status mrc_inverse_batched(mrc_ctx *ctx, int nmodels, const int *d, const int64_t *N,
+                               const double *const *A, double *const *psi,
+                               const mrc_options *opt, void *stream, mrc_report *report);
+
+/*
+ * mrc_residual -- left and right residuals of a computed inverse
+ * (Proposition 2.6; the accuracy check of Section 5):
+ *   rho_L = e0 - A * psi,  rho_R = e0 - psi * A,  k < N,
+ * computed by FFT in double-float (prec MRC_MIXED) or FP64 (MRC_FP64).
+ *   sides     : 1 = left only, 2 = right only, 3 = both.
+ *   rho_left, rho_right : device [N][d][d] doubles or NULL (norms only).
+ *   report    : host, may be NULL; if set the call synchronises and fills
+ *               res_left_l1 / res_right_l1 / res_max_abs.
+ */
+mrc_status mrc_residual(mrc_ctx *ctx, int d, int64_t N, const double *A, const double *psi, int sides,
+                        double *rho_left, double *rho_right, int prec, void *stream, mrc_report *report);
+
+/*
+ * mrc_transition -- transition probabilities P = psi * Hbar
+ * (Eq. (transition-discrete)), with the survival diagonal
+ * Hbar(k) = diag(1 - sum_j sum_{l=1..k} q_ij(l)) built on the device.
+ *   psi : device [N][d][d], the Markov renewal sequence (e0 - q)^{(-1)}.
+ *   q   : device [N][d][d], the discrete semi-Markov kernel (q(0) = 0).
+ *   P   : device [N][d][d], output.
+ *   prec: MRC_FP64 or MRC_MIXED (double-float convolution).
+ */
+mrc_status mrc_transition(mrc_ctx *ctx, int d, int64_t N, const double *psi, const double *q, double *P,
+                          int prec, void *stream);
+
+/*
+ * mrc_first_entrance -- first entrance into D (Eqs. (first-entrance-mass),
+ * (first-entrance-cdf)): g_D = (e0^C - q_CC)^{(-1)} * q_CD,
+ * G_D(k) = sum_{l<=k} g_D(l), F_D(k) = alpha_C G_D(k) 1_D, S_D = 1 - F_D.
+ * Reliability is S_D with D the failed states.
+ *   q       : device [N][d][d] kernel.
+ *   D, nD   : HOST array of nD distinct state indices in [0, d); C is the
+ *             complement in increasing order.  1 <= nD < d.
+ *   alpha_C : device [|C|] initial distribution on C.
+ *   g       : device [N][|C|][|D|] or NULL.
+ *   F, S    : device [N] or NULL.
+ *   opt     : precision of the inverse of e0^C - q_CC (as mrc_inverse) and of
+ *             the product with q_CD.
+ */
+mrc_status mrc_first_entrance(mrc_ctx *ctx, int d, int64_t N, const double *q, const int *D, int nD,
+                              const double *alpha_C, double *g, double *F, double *S,
+                              const mrc_options *opt, void *stream);
+
+/*
+ * mrc_occupation -- occupation probability A_B(k) = alpha P(k) 1_{E,B}
+ * (Table 2); availability when B is the set of up states.
+ *   P     : device [N][d][d];  alpha : device [d];
+ *   B, nB : HOST list of states in B;  out : device [N].
+ */
+mrc_status mrc_occupation(mrc_ctx *ctx, int d, int64_t N, const double *P, const double *alpha,
+                          const int *B, int nB, double *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRC_H */

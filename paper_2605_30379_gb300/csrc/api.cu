@@ -1,0 +1,548 @@
+// api.cu -- C ABI of libmrc and the host-side Newton driver.
+//
+// The driver only sequences kernels on the caller's stream; every arithmetic
+// step of the method runs in the CUDA kernels of k_*.cu and misc.cu.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/mrc.h"
+#include "mrc_internal.h"
+
+#define MRC_TW_LOG 21  // twiddle tables cover transform lengths up to 2^21
+
+struct mrc_ctx {
+    int device = 0;
+    size_t cap = 0;        // 0 = unlimited
+    void *ws = nullptr;    // workspace
+    size_t ws_size = 0;
+    void *tw[3] = {nullptr, nullptr, nullptr};
+    int *d_status = nullptr;
+    double *d_acc = nullptr;  // [4] norm accumulators
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+struct PrecOps {
+    cudaError_t (*fft)(const FftSrc &, const FftDst &, int64_t, int, int, void *, const void *, int, cudaStream_t);
+    cudaError_t (*pairmul)(const void *, const void *, void *, int64_t, int, int, int, const void *, int, cudaStream_t);
+    cudaError_t (*pairdiag)(const void *, const void *, void *, int64_t, int, int, const void *, int, cudaStream_t);
+    cudaError_t (*twiddles)(void *, int, cudaStream_t);
+    cudaError_t (*init)(void);
+    size_t cxb;
+};
+
+const PrecOps OPS[3] = {
+    {mrc_fft_f64, mrc_pairmul_f64, mrc_pairdiag_f64, mrc_twiddles_f64, mrc_init_f64, 16},
+    {mrc_fft_f32, mrc_pairmul_f32, mrc_pairdiag_f32, mrc_twiddles_f32, mrc_init_f32, 8},
+    {mrc_fft_dd, mrc_pairmul_dd, mrc_pairdiag_dd, mrc_twiddles_dd, mrc_init_dd, 16},
+};
+
+int64_t pow2ceil(int64_t x)
+{
+    int64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Bump allocator over the context workspace.
+struct Arena {
+    char *base;
+    size_t off = 0;
+    void *take(size_t bytes)
+    {
+        void *p = base + off;
+        off += align_up(bytes);
+        return p;
+    }
+};
+
+#define CK(call)                                          \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) {                          \
+            fprintf(stderr, "libmrc: %s -> %s\n", #call, cudaGetErrorString(e_)); \
+            return MRC_ERR_CUDA;                          \
+        }                                                 \
+    } while (0)
+
+mrc_status ensure_tw(mrc_ctx *c, int prec, cudaStream_t st)
+{
+    if (c->tw[prec]) return MRC_OK;
+    void *p = nullptr;
+    if (cudaMalloc(&p, OPS[prec].cxb << MRC_TW_LOG) != cudaSuccess) return MRC_ERR_NO_MEMORY;
+    CK(OPS[prec].twiddles(p, MRC_TW_LOG, st));
+    c->tw[prec] = p;
+    return MRC_OK;
+}
+
+mrc_status ensure_ws(mrc_ctx *c, size_t need)
+{
+    if (need <= c->ws_size) return MRC_OK;
+    if (c->cap && need > c->cap) return MRC_ERR_NO_MEMORY;
+    if (c->ws) {
+        cudaDeviceSynchronize();
+        cudaFree(c->ws);
+        c->ws = nullptr;
+        c->ws_size = 0;
+    }
+    if (cudaMalloc(&c->ws, need) != cudaSuccess) {
+        cudaGetLastError();
+        return MRC_ERR_NO_MEMORY;
+    }
+    c->ws_size = need;
+    return MRC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace plans
+int64_t base_size(int d, int64_t N)
+{
+    int64_t m0 = d <= 8 ? 32 : (d <= 32 ? 8 : 2);
+    return std::min<int64_t>(m0, N);
+}
+
+int64_t newton_maxM(int d, int64_t N)
+{
+    int64_t m0 = base_size(d, N), M = 0;
+    for (int64_t m = m0; m < N; m <<= 1) M = m;
+    return M;
+}
+
+size_t ws_newton(int d, int64_t N, int prec)
+{
+    const size_t E = (size_t)d * d;
+    size_t b = align_up(sizeof(double) * 2 * E);  // Gauss-Jordan work
+    const int64_t M = newton_maxM(d, N);
+    b += 4 * align_up((size_t)M * E * OPS[prec].cxb);
+    return b;
+}
+
+size_t ws_product(int64_t Mr, size_t EX, size_t EY, size_t EC, int prec)
+{
+    size_t cxb = OPS[prec].cxb;
+    size_t emax = std::max(EX, std::max(EY, EC));
+    return align_up(Mr * EX * cxb) + align_up(Mr * EY * cxb) + align_up(Mr * EC * cxb) + align_up(Mr * emax * cxb);
+}
+
+size_t ws_inverse(int d, int64_t N, int prec)
+{
+    const size_t E = (size_t)d * d;
+    if (prec == MRC_FP64) return ws_newton(d, N, PREC_F64);
+    size_t a = ws_newton(d, N, PREC_F32);
+    // Gauss-Jordan scratch stays reserved below the refinement buffers
+    size_t b = align_up(sizeof(double) * 2 * E) + ws_product(pow2ceil(N), E, E, E, PREC_DD) +
+               align_up((size_t)N * E * sizeof(double));
+    return std::max(a, b);
+}
+
+// ---------------------------------------------------------------------------
+// C = X * Y truncated to rows [0, N) (linear convolution via L = 2 Mr,
+// Mr = pow2ceil(N)), X: [NX rows][r][m], Y: [NY rows][m][c] real FP64.
+// Output: REAL64 rows [0, N) into `out` with scale s (and +I at row 0 if eye).
+mrc_status conv_product(mrc_ctx *c, Arena &ar, int prec, const double *X, int64_t NX, const double *Y, int64_t NY,
+                        int r, int m, int cc, int64_t N, double *out, double sign, int eye_d, int add,
+                        bool diag, cudaStream_t st)
+{
+    const PrecOps &op = OPS[prec];
+    const int64_t Mr = pow2ceil(N);
+    // diag: X is r x cc, Y is a cc-vector per time index
+    const size_t EX = diag ? (size_t)r * cc : (size_t)r * m, EY = diag ? (size_t)cc : (size_t)m * cc;
+    const size_t EC = (size_t)r * cc;
+    const size_t emax = std::max(EX, std::max(EY, EC));
+    void *bX = ar.take(Mr * EX * op.cxb);
+    void *bY = ar.take(Mr * EY * op.cxb);
+    void *bC = ar.take(Mr * EC * op.cxb);
+    void *bT = ar.take(Mr * emax * op.cxb);
+    const void *tw = c->tw[prec];
+    FftSrc sx{SRC_REAL64, X, 0, std::min(NX, N), (int)EX, 0};
+    FftSrc sy{SRC_REAL64, Y, 0, std::min(NY, N), (int)EY, 0};
+    FftDst dx{DST_CPLX, bX, (int)EX, 0, 0, 0, 1.0, 0};
+    FftDst dy{DST_CPLX, bY, (int)EY, 0, 0, 0, 1.0, 0};
+    CK(op.fft(sx, dx, Mr, (int)EX, -1, bT, tw, MRC_TW_LOG, st));
+    CK(op.fft(sy, dy, Mr, (int)EY, -1, bT, tw, MRC_TW_LOG, st));
+    if (diag) CK(op.pairdiag(bX, bY, bC, Mr, r, cc, tw, MRC_TW_LOG, st));
+    else CK(op.pairmul(bX, bY, bC, Mr, r, m, cc, tw, MRC_TW_LOG, st));
+    FftSrc sc{SRC_CPLX, bC, 0, Mr, (int)EC, 0};
+    FftDst dc{add ? DST_REAL64_ADD : DST_REAL64, out, (int)EC, 0, N, 0, sign / (double)Mr, eye_d};
+    CK(op.fft(sc, dc, Mr, (int)EC, +1, bT, tw, MRC_TW_LOG, st));
+    return MRC_OK;
+}
+
+// Newton doubling levels in working precision `prec`: psi rows [0, m0) are
+// already correct; each level m -> min(2m, N) follows Eq. (newton) with the
+// middle product (L = 2m): E = A*B (cyclic), R = -E[m, 2m), B[m, 2m) = (B*R)[0, m).
+mrc_status newton_levels(mrc_ctx *c, Arena &ar, int prec, int d, int64_t N, const double *A, double *psi,
+                         int64_t m0, int *levels, cudaStream_t st)
+{
+    const PrecOps &op = OPS[prec];
+    const int E = d * d;
+    const int64_t Mmax = newton_maxM(d, N);
+    if (Mmax == 0) return MRC_OK;
+    void *b0 = ar.take((size_t)Mmax * E * op.cxb);
+    void *b1 = ar.take((size_t)Mmax * E * op.cxb);
+    void *b2 = ar.take((size_t)Mmax * E * op.cxb);
+    void *bt = ar.take((size_t)Mmax * E * op.cxb);
+    const void *tw = c->tw[prec];
+    int lv = 0;
+    for (int64_t m = m0; m < N; m <<= 1, ++lv) {
+        const int64_t M = m, m2 = std::min<int64_t>(2 * m, N);
+        FftSrc sA{SRC_REAL64, A, 0, std::min<int64_t>(2 * m, N), E, 0};
+        FftSrc sB{SRC_REAL64, psi, 0, m, E, 0};
+        FftDst to0{DST_CPLX, b0, E, 0, 0, 0, 1.0, 0};
+        FftDst to1{DST_CPLX, b1, E, 0, 0, 0, 1.0, 0};
+        CK(op.fft(sA, to0, M, E, -1, bt, tw, MRC_TW_LOG, st));               // A-hat
+        CK(op.fft(sB, to1, M, E, -1, bt, tw, MRC_TW_LOG, st));               // B-hat
+        CK(op.pairmul(b0, b1, b2, M, d, d, d, tw, MRC_TW_LOG, st));          // (A B)-hat
+        FftSrc s2{SRC_CPLX, b2, 0, M, E, 0};
+        FftDst t0s{DST_CPLX, b0, E, 0, 0, 0, 1.0 / (double)M, 0};
+        CK(op.fft(s2, t0s, M, E, +1, bt, tw, MRC_TW_LOG, st));               // A*B, packed time
+        FftSrc sR{SRC_CPLX, b0, M / 2, M / 2, E, 1};                          // R = -(A*B)[m, 2m)
+        FftDst to2{DST_CPLX, b2, E, 0, 0, 0, 1.0, 0};
+        CK(op.fft(sR, to2, M, E, -1, bt, tw, MRC_TW_LOG, st));               // R-hat
+        CK(op.pairmul(b1, b2, b0, M, d, d, d, tw, MRC_TW_LOG, st));          // (B R)-hat
+        FftSrc s0{SRC_CPLX, b0, 0, M, E, 0};
+        FftDst toP{DST_REAL64, psi, E, 0, m2 - m, m, 1.0 / (double)M, 0};
+        CK(op.fft(s0, toP, M, E, +1, bt, tw, MRC_TW_LOG, st));               // B[m, m2)
+    }
+    if (levels) *levels = lv;
+    return MRC_OK;
+}
+
+bool valid_dN(int d, int64_t N) { return d >= 1 && d <= 512 && N >= 1 && N <= ((int64_t)1 << 20); }
+
+mrc_status inverse_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A, double *psi, int prec, int sweeps,
+                        int *levels, cudaStream_t st)
+{
+    const size_t E = (size_t)d * d;
+    double *gjw = (double *)ar.take(sizeof(double) * 2 * E);
+    CK(mrc_gauss_jordan(A, psi, gjw, d, c->d_status, st));
+    const int64_t m0 = base_size(d, N);
+    CK(mrc_base_case(A, psi, d, m0, st));
+    const size_t mark = ar.off;
+    mrc_status s = newton_levels(c, ar, prec == MRC_FP64 ? PREC_F64 : PREC_F32, d, N, A, psi, m0, levels, st);
+    if (s != MRC_OK) return s;
+    ar.off = mark;
+    if (prec == MRC_MIXED) {
+        double *rho = (double *)ar.take(sizeof(double) * (size_t)N * E);
+        const size_t mark2 = ar.off;
+        for (int sw = 0; sw < sweeps; ++sw) {
+            ar.off = mark2;
+            // rho_L = e0 - A * psi in double-float (Proposition 2.6)
+            s = conv_product(c, ar, PREC_DD, A, N, psi, N, d, d, d, N, rho, -1.0, d, 0, false, st);
+            if (s != MRC_OK) return s;
+            ar.off = mark2;
+            // psi <- psi + psi * rho_L (Eq. (newton) from a full-length approximation), FP32 product
+            s = conv_product(c, ar, PREC_F32, psi, N, rho, N, d, d, d, N, psi, 1.0, 0, 1, false, st);
+            if (s != MRC_OK) return s;
+        }
+    }
+    return MRC_OK;
+}
+
+mrc_status read_status(mrc_ctx *c, cudaStream_t st)
+{
+    int h = 0;
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemcpy(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(c->d_status, 0, sizeof(int)));
+    return (mrc_status)h;
+}
+
+mrc_status residual_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A, const double *psi, int sides,
+                         double *rl, double *rr, int prec, cudaStream_t st, mrc_report *rep)
+{
+    const size_t E = (size_t)d * d;
+    const int p = prec == MRC_FP64 ? PREC_F64 : PREC_DD;
+    double *tmp = nullptr;
+    if ((sides & 1 && !rl) || (sides & 2 && !rr)) tmp = (double *)ar.take(sizeof(double) * N * E);
+    double h[4] = {-1, -1, -1, -1};
+    if (sides & 1) {
+        double *o = rl ? rl : tmp;
+        const size_t mk = ar.off;
+        mrc_status s = conv_product(c, ar, p, A, N, psi, N, d, d, d, N, o, -1.0, d, 0, false, st);
+        if (s != MRC_OK) return s;
+        ar.off = mk;
+        if (rep) {
+            CK(mrc_norms(o, (int)E, N, c->d_acc, st));
+            CK(cudaMemcpyAsync(h, c->d_acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            rep->res_left_l1 = h[0];
+            rep->res_max_abs = h[1];
+        }
+    }
+    if (sides & 2) {
+        double *o = rr ? rr : tmp;
+        const size_t mk = ar.off;
+        mrc_status s = conv_product(c, ar, p, psi, N, A, N, d, d, d, N, o, -1.0, d, 0, false, st);
+        if (s != MRC_OK) return s;
+        ar.off = mk;
+        if (rep) {
+            CK(mrc_norms(o, (int)E, N, c->d_acc, st));
+            CK(cudaMemcpyAsync(h + 2, c->d_acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            rep->res_right_l1 = h[2];
+            if (!(sides & 1)) rep->res_max_abs = h[3];
+        }
+    }
+    return MRC_OK;
+}
+
+size_t ws_residual(int d, int64_t N, int prec, bool need_tmp)
+{
+    const size_t E = (size_t)d * d;
+    const int p = prec == MRC_FP64 ? PREC_F64 : PREC_DD;
+    return ws_product(pow2ceil(N), E, E, E, p) + (need_tmp ? align_up(sizeof(double) * N * E) : 0);
+}
+
+} // namespace
+
+// ===========================================================================
+extern "C" {
+
+const char *mrc_status_string(mrc_status s)
+{
+    switch (s) {
+    case MRC_OK: return "ok";
+    case MRC_ERR_INVALID_ARG: return "invalid argument";
+    case MRC_ERR_SINGULAR_A0: return "A(0) is singular";
+    case MRC_ERR_NO_MEMORY: return "out of workspace memory";
+    case MRC_ERR_CUDA: return "CUDA error";
+    case MRC_ERR_NOT_CONVERGED: return "refinement did not reach the target residual";
+    case MRC_ERR_TIMEOUT: return "device wait timed out";
+    case MRC_ERR_UNIMPLEMENTED: return "unimplemented";
+    }
+    return "unknown status";
+}
+
+const char *mrc_version(void) { return "libmrc 0.1 (sm_103a)"; }
+
+mrc_status mrc_create(mrc_ctx **out, int device, size_t max_workspace_bytes)
+{
+    if (!out) return MRC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (cudaSetDevice(device) != cudaSuccess) return MRC_ERR_CUDA;
+    for (int p = 0; p < 3; ++p)
+        if (OPS[p].init() != cudaSuccess) return MRC_ERR_CUDA;
+    mrc_ctx *c = new mrc_ctx();
+    c->device = device;
+    c->cap = max_workspace_bytes;
+    if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_acc, 4 * sizeof(double)) != cudaSuccess) {
+        delete c;
+        return MRC_ERR_NO_MEMORY;
+    }
+    cudaMemset(c->d_status, 0, sizeof(int));
+    cudaEventCreate(&c->ev0);
+    cudaEventCreate(&c->ev1);
+    *out = c;
+    return MRC_OK;
+}
+
+mrc_status mrc_destroy(mrc_ctx *c)
+{
+    if (!c) return MRC_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    cudaFree(c->ws);
+    for (int p = 0; p < 3; ++p) cudaFree(c->tw[p]);
+    cudaFree(c->d_status);
+    cudaFree(c->d_acc);
+    cudaEventDestroy(c->ev0);
+    cudaEventDestroy(c->ev1);
+    delete c;
+    return MRC_OK;
+}
+
+mrc_status mrc_sync_status(mrc_ctx *c, void *stream)
+{
+    if (!c) return MRC_ERR_INVALID_ARG;
+    return read_status(c, (cudaStream_t)stream);
+}
+
+size_t mrc_inverse_workspace_bytes(int d, int64_t N, int prec)
+{
+    if (!valid_dN(d, N)) return 0;
+    return ws_inverse(d, N, prec);
+}
+
+mrc_status mrc_inverse(mrc_ctx *c, int d, int64_t N, const double *A, double *psi, const mrc_options *opt,
+                       void *stream, mrc_report *report)
+{
+    if (!c || !A || !psi || !valid_dN(d, N)) return MRC_ERR_INVALID_ARG;
+    const int prec = opt ? opt->prec : MRC_FP64;
+    if (prec != MRC_FP64 && prec != MRC_MIXED) return MRC_ERR_INVALID_ARG;
+    int sweeps = opt ? opt->refine_sweeps : 1;
+    if (prec == MRC_MIXED && sweeps <= 0) sweeps = 1;
+    if (sweeps > 4) return MRC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaSetDevice(c->device);
+    mrc_status s;
+    if ((s = ensure_tw(c, prec == MRC_FP64 ? PREC_F64 : PREC_F32, st)) != MRC_OK) return s;
+    if (prec == MRC_MIXED && (s = ensure_tw(c, PREC_DD, st)) != MRC_OK) return s;
+    const bool check = report && prec == MRC_MIXED && opt && opt->target_residual > 0;
+    size_t need = ws_inverse(d, N, prec);
+    if (check) need = std::max(need, ws_residual(d, N, MRC_MIXED, true));
+    if ((s = ensure_ws(c, need)) != MRC_OK) return s;
+    Arena ar{(char *)c->ws};
+    int levels = 0;
+    if (report) CK(cudaEventRecord(c->ev0, st));
+    s = inverse_impl(c, ar, d, N, A, psi, prec, sweeps, &levels, st);
+    if (s != MRC_OK) return s;
+    if (report) {
+        CK(cudaEventRecord(c->ev1, st));
+        memset(report, 0, sizeof(*report));
+        report->res_left_l1 = report->res_right_l1 = report->res_max_abs = -1.0;
+        report->levels = levels;
+        report->sweeps = prec == MRC_MIXED ? sweeps : 0;
+        s = read_status(c, st);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        report->ms = ms;
+        if (s != MRC_OK) return s;
+        if (check) {
+            Arena ar2{(char *)c->ws};
+            s = residual_impl(c, ar2, d, N, A, psi, 1, nullptr, nullptr, MRC_MIXED, st, report);
+            if (s != MRC_OK) return s;
+            if (!(report->res_max_abs <= opt->target_residual)) return MRC_ERR_NOT_CONVERGED;
+        }
+    }
+    return MRC_OK;
+}
+
+mrc_status mrc_inverse_batched(mrc_ctx *c, int nmodels, const int *d, const int64_t *N, const double *const *A,
+                               double *const *psi, const mrc_options *opt, void *stream, mrc_report *report)
+{
+    if (!c || nmodels < 0 || (nmodels > 0 && (!d || !N || !A || !psi))) return MRC_ERR_INVALID_ARG;
+    for (int b = 0; b < nmodels; ++b)
+        if (!valid_dN(d[b], N[b]) || !A[b] || !psi[b]) return MRC_ERR_INVALID_ARG;
+    const int prec = opt ? opt->prec : MRC_FP64;
+    size_t need = 0;
+    for (int b = 0; b < nmodels; ++b) need = std::max(need, ws_inverse(d[b], N[b], prec));
+    mrc_status s;
+    cudaSetDevice(c->device);
+    if ((s = ensure_ws(c, need)) != MRC_OK) return s;
+    for (int b = 0; b < nmodels; ++b) {
+        s = mrc_inverse(c, d[b], N[b], A[b], psi[b], opt, stream, report ? report + b : nullptr);
+        if (s != MRC_OK) return s;
+    }
+    return MRC_OK;
+}
+
+mrc_status mrc_residual(mrc_ctx *c, int d, int64_t N, const double *A, const double *psi, int sides, double *rho_left,
+                        double *rho_right, int prec, void *stream, mrc_report *report)
+{
+    if (!c || !A || !psi || !valid_dN(d, N) || sides < 1 || sides > 3) return MRC_ERR_INVALID_ARG;
+    if (prec != MRC_FP64 && prec != MRC_MIXED) return MRC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaSetDevice(c->device);
+    mrc_status s;
+    const int p = prec == MRC_FP64 ? PREC_F64 : PREC_DD;
+    if ((s = ensure_tw(c, p, st)) != MRC_OK) return s;
+    const bool need_tmp = ((sides & 1) && !rho_left) || ((sides & 2) && !rho_right);
+    if ((s = ensure_ws(c, ws_residual(d, N, prec, need_tmp))) != MRC_OK) return s;
+    Arena ar{(char *)c->ws};
+    if (report) {
+        memset(report, 0, sizeof(*report));
+        report->res_left_l1 = report->res_right_l1 = report->res_max_abs = -1.0;
+    }
+    return residual_impl(c, ar, d, N, A, psi, sides, rho_left, rho_right, prec, st, report);
+}
+
+mrc_status mrc_transition(mrc_ctx *c, int d, int64_t N, const double *psi, const double *q, double *P, int prec,
+                          void *stream)
+{
+    if (!c || !psi || !q || !P || !valid_dN(d, N)) return MRC_ERR_INVALID_ARG;
+    if (prec != MRC_FP64 && prec != MRC_MIXED) return MRC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaSetDevice(c->device);
+    const int p = prec == MRC_FP64 ? PREC_F64 : PREC_DD;
+    mrc_status s;
+    if ((s = ensure_tw(c, p, st)) != MRC_OK) return s;
+    const size_t E = (size_t)d * d;
+    const int64_t nch = (N + 1023) / 1024;
+    size_t need = align_up(sizeof(double) * N * d) + align_up(sizeof(double) * nch * d) +
+                  ws_product(pow2ceil(N), E, d, E, p);
+    if ((s = ensure_ws(c, need)) != MRC_OK) return s;
+    Arena ar{(char *)c->ws};
+    double *h = (double *)ar.take(sizeof(double) * N * d);
+    double *work = (double *)ar.take(sizeof(double) * nch * d);
+    CK(mrc_row_sums(q, h, d, N, st));
+    CK(mrc_scan_cols(h, d, N, work, -1.0, 1.0, st));  // Hbar_j(k) = 1 - sum_{l<=k} sum_j' q_jj'(l)
+    return conv_product(c, ar, p, psi, N, h, N, d, 1, d, N, P, 1.0, 0, 0, true, st);
+}
+
+mrc_status mrc_first_entrance(mrc_ctx *c, int d, int64_t N, const double *q, const int *D, int nD,
+                              const double *alpha_C, double *g, double *F, double *S, const mrc_options *opt,
+                              void *stream)
+{
+    if (!c || !q || !D || !alpha_C || !valid_dN(d, N) || nD < 1 || nD >= d) return MRC_ERR_INVALID_ARG;
+    std::vector<int> inD(d, 0), Ci, Di;
+    for (int t = 0; t < nD; ++t) {
+        if (D[t] < 0 || D[t] >= d || inD[D[t]]) return MRC_ERR_INVALID_ARG;
+        inD[D[t]] = 1;
+    }
+    for (int i = 0; i < d; ++i) (inD[i] ? Di : Ci).push_back(i);
+    const int nC = (int)Ci.size();
+    const int prec = opt ? opt->prec : MRC_FP64;
+    if (prec != MRC_FP64 && prec != MRC_MIXED) return MRC_ERR_INVALID_ARG;
+    int sweeps = opt && opt->refine_sweeps > 0 ? opt->refine_sweeps : 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaSetDevice(c->device);
+    mrc_status s;
+    const int pc = prec == MRC_FP64 ? PREC_F64 : PREC_DD;
+    if ((s = ensure_tw(c, prec == MRC_FP64 ? PREC_F64 : PREC_F32, st)) != MRC_OK) return s;
+    if ((s = ensure_tw(c, pc, st)) != MRC_OK) return s;
+    const size_t ECC = (size_t)nC * nC, ECD = (size_t)nC * nD;
+    size_t fixed = align_up(sizeof(double) * N * ECC) * 2 + align_up(sizeof(double) * N * ECD) * 2 +
+                   align_up(sizeof(double) * N) * 2 + align_up(sizeof(double) * ((N + 1023) / 1024));
+    size_t need = fixed + std::max(ws_inverse(nC, N, prec), ws_product(pow2ceil(N), ECC, ECD, ECD, pc));
+    if ((s = ensure_ws(c, need)) != MRC_OK) return s;
+    Arena ar{(char *)c->ws};
+    double *ACC = (double *)ar.take(sizeof(double) * N * ECC);
+    double *psiC = (double *)ar.take(sizeof(double) * N * ECC);
+    double *QCD = (double *)ar.take(sizeof(double) * N * ECD);
+    double *gw = (double *)ar.take(sizeof(double) * N * ECD);
+    double *Fw = (double *)ar.take(sizeof(double) * N);
+    double *fk = (double *)ar.take(sizeof(double) * N);
+    double *work = (double *)ar.take(sizeof(double) * ((N + 1023) / 1024));
+    CK(mrc_gather_blocks(q, d, N, Ci.data(), nC, Di.data(), nD, ACC, QCD, st));
+    const size_t mark = ar.off;
+    s = inverse_impl(c, ar, nC, N, ACC, psiC, prec, sweeps, nullptr, st);
+    if (s != MRC_OK) return s;
+    ar.off = mark;
+    double *gout = g ? g : gw;
+    s = conv_product(c, ar, pc, psiC, N, QCD, N, nC, nC, nD, N, gout, 1.0, 0, 0, false, st);
+    if (s != MRC_OK) return s;
+    if (F || S) {
+        double *Fo = F ? F : Fw;
+        CK(mrc_weighted_rowsum(gout, nC, nD, N, alpha_C, fk, st));
+        CK(cudaMemcpyAsync(Fo, fk, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+        CK(mrc_scan_cols(Fo, 1, N, work, 1.0, 0.0, st));
+        if (S) CK(mrc_one_minus(Fo, S, N, st));
+    }
+    return MRC_OK;
+}
+
+mrc_status mrc_occupation(mrc_ctx *c, int d, int64_t N, const double *P, const double *alpha, const int *B, int nB,
+                          double *out, void *stream)
+{
+    if (!c || !P || !alpha || !B || !out || !valid_dN(d, N) || nB < 0 || nB > d) return MRC_ERR_INVALID_ARG;
+    std::vector<int> inB(d, 0);
+    for (int t = 0; t < nB; ++t) {
+        if (B[t] < 0 || B[t] >= d) return MRC_ERR_INVALID_ARG;
+        inB[B[t]] = 1;
+    }
+    cudaSetDevice(c->device);
+    CK(mrc_occupation_k(P, d, N, alpha, inB.data(), out, (cudaStream_t)stream));
+    return MRC_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,167 @@
+// arith.cuh -- scalar and complex arithmetic for the three working precisions
+// of the FFT-Newton path: FP64 (double), FP32 (float) and double-float (dd,
+// an unevaluated sum hi + lo of two floats, ~48-bit significand).
+//
+// The double-float operations are built from the classical error-free
+// transformations: Knuth's TwoSum (TAOCP vol. 2, 4.2.2), Dekker's
+// FastTwoSum (Dekker 1971) and the FMA form of TwoProd (the exact product
+// error is fma(a, b, -fl(a*b))).  Every step uses explicitly rounded
+// intrinsics (__fadd_rn, __fmul_rn, __fmaf_rn) so the compiler cannot contract
+// or reassociate them.  Addition is the "sloppy" variant (one TwoSum on the
+// high parts, low parts added once), whose error is a small multiple of
+// 2^-46 (|x| + |y|): the normwise bound the FFT and matrix-product error
+// analysis of Proposition 2.1 needs.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+struct dd {
+    float hi, lo;
+};
+
+template <class T>
+struct __align__(2 * sizeof(T)) cx {
+    T re, im;
+};
+
+__device__ __forceinline__ dd dd_two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ dd dd_fast_two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+
+__device__ __forceinline__ dd dd_add(dd x, dd y)
+{
+    dd s = dd_two_sum(x.hi, y.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    return dd_fast_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ dd dd_neg(dd x) { return {-x.hi, -x.lo}; }
+
+__device__ __forceinline__ dd dd_sub(dd x, dd y) { return dd_add(x, dd_neg(y)); }
+
+__device__ __forceinline__ dd dd_mul(dd x, dd y)
+{
+    float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return dd_fast_two_sum(p, e);
+}
+
+// a*b + c with one normalisation
+__device__ __forceinline__ dd dd_fma(dd a, dd b, dd c)
+{
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    dd s = dd_two_sum(p, c.hi);
+    float t = __fadd_rn(s.lo, __fadd_rn(e, c.lo));
+    return dd_fast_two_sum(s.hi, t);
+}
+
+__device__ __forceinline__ dd dd_from_double(double x)
+{
+    float hi = __double2float_rn(x);
+    float lo = __double2float_rn(x - (double)hi);
+    return {hi, lo};
+}
+
+__device__ __forceinline__ double dd_to_double(dd x) { return (double)x.hi + (double)x.lo; }
+
+// ---------------------------------------------------------------------------
+// Real arithmetic traits.  scal(a, s) multiplies by a host scalar s that is a
+// signed power of two (1/M, -1/M, 0.5): exact in every precision.
+template <class T>
+struct Ar;
+
+template <>
+struct Ar<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return a + b; }
+    static __device__ __forceinline__ double sub(double a, double b) { return a - b; }
+    static __device__ __forceinline__ double mul(double a, double b) { return a * b; }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    static __device__ __forceinline__ double neg(double a) { return -a; }
+    static __device__ __forceinline__ double scal(double a, double s) { return a * s; }
+    static __device__ __forceinline__ double from_d(double x) { return x; }
+    static __device__ __forceinline__ double to_d(double x) { return x; }
+    static __device__ __forceinline__ double zero() { return 0.0; }
+};
+
+template <>
+struct Ar<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return a + b; }
+    static __device__ __forceinline__ float sub(float a, float b) { return a - b; }
+    static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ float neg(float a) { return -a; }
+    static __device__ __forceinline__ float scal(float a, double s) { return a * (float)s; }
+    static __device__ __forceinline__ float from_d(double x) { return __double2float_rn(x); }
+    static __device__ __forceinline__ double to_d(float x) { return (double)x; }
+    static __device__ __forceinline__ float zero() { return 0.0f; }
+};
+
+template <>
+struct Ar<dd> {
+    static __device__ __forceinline__ dd add(dd a, dd b) { return dd_add(a, b); }
+    static __device__ __forceinline__ dd sub(dd a, dd b) { return dd_sub(a, b); }
+    static __device__ __forceinline__ dd mul(dd a, dd b) { return dd_mul(a, b); }
+    static __device__ __forceinline__ dd fma(dd a, dd b, dd c) { return dd_fma(a, b, c); }
+    static __device__ __forceinline__ dd neg(dd a) { return dd_neg(a); }
+    static __device__ __forceinline__ dd scal(dd a, double s)
+    {
+        float f = (float)s;
+        return {a.hi * f, a.lo * f};
+    }
+    static __device__ __forceinline__ dd from_d(double x) { return dd_from_double(x); }
+    static __device__ __forceinline__ double to_d(dd x) { return dd_to_double(x); }
+    static __device__ __forceinline__ dd zero() { return {0.0f, 0.0f}; }
+};
+
+// ---------------------------------------------------------------------------
+// Complex helpers
+template <class T>
+__device__ __forceinline__ cx<T> c_zero() { return {Ar<T>::zero(), Ar<T>::zero()}; }
+template <class T>
+__device__ __forceinline__ cx<T> c_add(cx<T> a, cx<T> b) { return {Ar<T>::add(a.re, b.re), Ar<T>::add(a.im, b.im)}; }
+template <class T>
+__device__ __forceinline__ cx<T> c_sub(cx<T> a, cx<T> b) { return {Ar<T>::sub(a.re, b.re), Ar<T>::sub(a.im, b.im)}; }
+template <class T>
+__device__ __forceinline__ cx<T> c_conj(cx<T> a) { return {a.re, Ar<T>::neg(a.im)}; }
+template <class T>
+__device__ __forceinline__ cx<T> c_neg(cx<T> a) { return {Ar<T>::neg(a.re), Ar<T>::neg(a.im)}; }
+template <class T>
+__device__ __forceinline__ cx<T> c_scal(cx<T> a, double s) { return {Ar<T>::scal(a.re, s), Ar<T>::scal(a.im, s)}; }
+// a * b
+template <class T>
+__device__ __forceinline__ cx<T> c_mul(cx<T> a, cx<T> b)
+{
+    return {Ar<T>::fma(a.re, b.re, Ar<T>::neg(Ar<T>::mul(a.im, b.im))),
+            Ar<T>::fma(a.re, b.im, Ar<T>::mul(a.im, b.re))};
+}
+// c += a * b
+template <class T>
+__device__ __forceinline__ void c_mac(cx<T> &c, cx<T> a, cx<T> b)
+{
+    c.re = Ar<T>::fma(a.re, b.re, c.re);
+    c.re = Ar<T>::fma(Ar<T>::neg(a.im), b.im, c.re);
+    c.im = Ar<T>::fma(a.re, b.im, c.im);
+    c.im = Ar<T>::fma(a.im, b.re, c.im);
+}
+// i * a
+template <class T>
+__device__ __forceinline__ cx<T> c_mul_i(cx<T> a) { return {Ar<T>::neg(a.im), a.re}; }
+
+template <class T>
+__device__ __forceinline__ cx<T> c_from_d(double re, double im) { return {Ar<T>::from_d(re), Ar<T>::from_d(im)}; }

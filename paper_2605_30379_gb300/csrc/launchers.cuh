@@ -1,0 +1,146 @@
+// launchers.cuh -- host-side launchers for one working precision T.  Each
+// k_<prec>.cu includes this file once with MRC_T / MRC_SUF defined.
+#pragma once
+#include "kernels.cuh"
+
+namespace {
+
+inline int ilog2_i64(int64_t x)
+{
+    int l = 0;
+    while (((int64_t)1 << l) < x) ++l;
+    return l;
+}
+
+template <class T>
+constexpr int default_ec() { return sizeof(cx<T>) == 8 ? 16 : 8; }
+
+template <class T>
+size_t fft_smem_bytes(int logR, int ec)
+{
+    const size_t R = (size_t)1 << logR;
+    return (R * ec + (R >> 1) + R) * sizeof(cx<T>);
+}
+
+// Radix plan: one pass up to 2^9, else two passes of sizes 2^ceil(l/2), 2^floor(l/2).
+inline int fft_plan(int logM, int *logRs)
+{
+    if (logM <= 9) { logRs[0] = logM; return 1; }
+    logRs[0] = (logM + 1) / 2;
+    logRs[1] = logM / 2;
+    return 2;
+}
+
+template <class T>
+cudaError_t fft_run(const FftSrc &src, const FftDst &dst, int64_t M, int E, int dir, void *scratch,
+                    const void *tw, int tw_log, cudaStream_t st)
+{
+    const int logM = ilog2_i64(M);
+    if (((int64_t)1 << logM) != M || logM > 20 || logM + 1 > tw_log) return cudaErrorInvalidValue;
+    int logRs[2];
+    const int np = fft_plan(logM, logRs);
+    int ec = default_ec<T>();
+    if (ec > E) ec = E;
+    int logNs = 0;
+    for (int ps = 0; ps < np; ++ps) {
+        FftArgs a{};
+        a.M = M;
+        a.logR = logRs[ps];
+        a.logNs = logNs;
+        a.Ns = (int64_t)1 << logNs;
+        a.E = E;
+        a.ec = ec;
+        a.dir = dir;
+        a.tw = tw;
+        a.tw_log = tw_log;
+        if (ps == 0) {
+            a.src_mode = src.mode; a.src = src.ptr; a.src_row0 = src.row0; a.src_nvalid = src.nvalid;
+            a.src_ld = src.ld; a.src_neg = src.neg;
+        } else {
+            a.src_mode = SRC_CPLX; a.src = scratch; a.src_row0 = 0; a.src_nvalid = M; a.src_ld = E; a.src_neg = 0;
+        }
+        if (ps == np - 1) {
+            a.dst_mode = dst.mode; a.dst = dst.ptr; a.dst_ld = dst.ld; a.dst_lo = dst.lo; a.dst_hi = dst.hi;
+            a.dst_row0 = dst.row0; a.dst_scale = dst.scale; a.dst_eye_d = dst.eye_d;
+        } else {
+            a.dst_mode = DST_CPLX; a.dst = scratch; a.dst_ld = E; a.dst_lo = 0; a.dst_hi = 0; a.dst_row0 = 0;
+            a.dst_scale = 1.0; a.dst_eye_d = 0;
+        }
+        dim3 grid((unsigned)(M >> a.logR), (unsigned)((E + ec - 1) / ec));
+        fft_pass_kernel<T><<<grid, 256, fft_smem_bytes<T>(a.logR, ec), st>>>(a);
+        logNs += a.logR;
+    }
+    return cudaGetLastError();
+}
+
+template <class T, int BM, int BN, int BK, int TM, int TN>
+cudaError_t pairmul_launch(const PairArgs &a, cudaStream_t st)
+{
+    const int tiles = ((a.r + BM - 1) / BM) * ((a.c + BN - 1) / BN);
+    dim3 grid((unsigned)a.npairs, (unsigned)tiles);
+    pairmul_kernel<T, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t pairmul_run(const void *zx, const void *zy, void *zc, int64_t M, int r, int m, int c, const void *tw,
+                        int tw_log, cudaStream_t st)
+{
+    PairArgs a{};
+    a.zx = zx; a.zy = zy; a.zc = zc; a.tw = tw; a.tw_log = tw_log; a.M = M; a.logM = ilog2_i64(M);
+    a.npairs = M >= 2 ? M / 2 + 1 : 1;
+    a.r = r; a.m = m; a.c = c;
+    const int mx = r > c ? r : c;
+    if (mx <= 16) return pairmul_launch<T, 16, 16, 16, 2, 2>(a, st);
+    if (mx <= 32) return pairmul_launch<T, 32, 32, 16, 2, 2>(a, st);
+    return pairmul_launch<T, 64, 64, 8, 4, 4>(a, st);
+}
+
+template <class T>
+cudaError_t pairdiag_run(const void *zx, const void *zy, void *zc, int64_t M, int r, int c, const void *tw,
+                         int tw_log, cudaStream_t st)
+{
+    PairArgs a{};
+    a.zx = zx; a.zy = zy; a.zc = zc; a.tw = tw; a.tw_log = tw_log; a.M = M; a.logM = ilog2_i64(M);
+    a.npairs = M >= 2 ? M / 2 + 1 : 1;
+    a.r = r; a.m = 0; a.c = c;
+    const int64_t total = a.npairs * (int64_t)r * c;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    pairdiag_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t twiddles_run(void *tw, int tw_log, cudaStream_t st)
+{
+    twiddle_kernel<T><<<152 * 8, 256, 0, st>>>(reinterpret_cast<cx<T> *>(tw), tw_log);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t init_run()
+{
+    return cudaFuncSetAttribute(fft_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+} // namespace
+
+#define MRC_DEFINE_PREC(T, SUF)                                                                             \
+    cudaError_t mrc_fft_##SUF(const FftSrc &src, const FftDst &dst, int64_t M, int E, int dir, void *scratch, \
+                              const void *tw, int tw_log, cudaStream_t st)                                  \
+    {                                                                                                       \
+        return fft_run<T>(src, dst, M, E, dir, scratch, tw, tw_log, st);                                    \
+    }                                                                                                       \
+    cudaError_t mrc_pairmul_##SUF(const void *zx, const void *zy, void *zc, int64_t M, int r, int m, int c,   \
+                                  const void *tw, int tw_log, cudaStream_t st)                              \
+    {                                                                                                       \
+        return pairmul_run<T>(zx, zy, zc, M, r, m, c, tw, tw_log, st);                                      \
+    }                                                                                                       \
+    cudaError_t mrc_pairdiag_##SUF(const void *zx, const void *zy, void *zc, int64_t M, int r, int c,         \
+                                   const void *tw, int tw_log, cudaStream_t st)                             \
+    {                                                                                                       \
+        return pairdiag_run<T>(zx, zy, zc, M, r, c, tw, tw_log, st);                                        \
+    }                                                                                                       \
+    cudaError_t mrc_twiddles_##SUF(void *tw, int tw_log, cudaStream_t st) { return twiddles_run<T>(tw, tw_log, st); } \
+    cudaError_t mrc_init_##SUF(void) { return init_run<T>(); }

@@ -1,0 +1,351 @@
+// misc.cu -- FP64 kernels around the FFT-Newton core: Gauss-Jordan inverse of
+// A(0), the direct recursion for the first m0 coefficients, survival
+// diagonal scans, residual norms, block gathers for first-entrance kernels and
+// the occupation / first-entrance reductions.
+#include <math.h>
+#include "mrc_internal.h"
+
+#define MRC_ST_SINGULAR 2
+
+namespace {
+
+__device__ __forceinline__ void warp_argmax(double &v, int &i)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        double v2 = __shfl_down_sync(0xffffffffu, v, o);
+        int i2 = __shfl_down_sync(0xffffffffu, i, o);
+        if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
+    }
+}
+
+// Block-wide argmax of (v, i); the result is broadcast through shared memory.
+__device__ void block_argmax(double &v, int &i, double *sv, int *si)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    warp_argmax(v, i);
+    if (lane == 0) { sv[wid] = v; si[wid] = i; }
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < nw ? sv[lane] : -1.0;
+        i = lane < nw ? si[lane] : 0x7fffffff;
+        warp_argmax(v, i);
+        if (lane == 0) { sv[0] = v; si[0] = i; }
+    }
+    __syncthreads();
+    v = sv[0];
+    i = si[0];
+    __syncthreads();
+}
+
+// Gauss-Jordan with partial pivoting on [A0 | I] (d x 2d, row-major in W).
+// One CTA.  A pivot with |p| <= d 2^-52 max|A0| marks A0 singular: the
+// status word is set, `out` is filled with NaN and the kernel returns.
+__global__ void __launch_bounds__(1024) gj_kernel(const double *__restrict__ A0, double *__restrict__ out,
+                                                  double *__restrict__ W, int d, int *status)
+{
+    __shared__ double sv[32];
+    __shared__ int si[32];
+    extern __shared__ double fac[];  // [d]
+    const int n2 = 2 * d, tid = threadIdx.x, nt = blockDim.x;
+    double amax = 0.0;
+    for (int t = tid; t < d * n2; t += nt) {
+        int i = t / n2, j = t - i * n2;
+        double v = j < d ? A0[i * d + j] : ((j - d) == i ? 1.0 : 0.0);
+        W[t] = v;
+        if (j < d) amax = fmax(amax, fabs(v));
+    }
+    int dummy = 0;
+    block_argmax(amax, dummy, sv, si);
+    const double tol = (double)d * 0x1p-52 * amax;
+    for (int col = 0; col < d; ++col) {
+        double best = -1.0;
+        int piv = 0x7fffffff;
+        for (int i = col + tid; i < d; i += nt) {
+            double v = fabs(W[i * n2 + col]);
+            if (v > best || (v == best && i < piv)) { best = v; piv = i; }
+        }
+        block_argmax(best, piv, sv, si);
+        if (!(best > tol)) {
+            if (tid == 0) atomicExch(status, MRC_ST_SINGULAR);
+            for (int t = tid; t < d * d; t += nt) out[t] = __longlong_as_double(0x7ff8000000000000ll);
+            return;
+        }
+        if (piv != col)
+            for (int j = tid; j < n2; j += nt) {
+                double t = W[col * n2 + j];
+                W[col * n2 + j] = W[piv * n2 + j];
+                W[piv * n2 + j] = t;
+            }
+        __syncthreads();
+        const double p = W[col * n2 + col];
+        __syncthreads();
+        for (int j = tid; j < n2; j += nt) W[col * n2 + j] /= p;
+        __syncthreads();
+        for (int i = tid; i < d; i += nt) fac[i] = W[i * n2 + col];
+        __syncthreads();
+        for (int t = tid; t < d * n2; t += nt) {
+            int i = t / n2, j = t - i * n2;
+            if (i != col) W[t] = fma(-fac[i], W[col * n2 + j], W[t]);
+        }
+        __syncthreads();
+    }
+    for (int t = tid; t < d * d; t += nt) {
+        int i = t / d, j = t - i * d;
+        out[t] = W[i * n2 + d + j];
+    }
+}
+
+// Direct recursion for the first m0 coefficients (left form, Theorem 2.2):
+//   psi(k) = A(0)^{-1} [ - sum_{l=1..k} A(l) psi(k-l) ],  k = 1..m0-1,
+// with psi(0) = A(0)^{-1} already in place.  CTA j owns column j (columns
+// are independent in the left recursion), thread i owns row i.
+__global__ void base_case_kernel(const double *__restrict__ A, double *__restrict__ psi, int d, int m0)
+{
+    extern __shared__ double t[];  // [d]
+    const int j = blockIdx.x;
+    const int64_t E = (int64_t)d * d;
+    for (int k = 1; k < m0; ++k) {
+        for (int i = threadIdx.x; i < d; i += blockDim.x) {
+            double s = 0.0;
+            for (int l = 1; l <= k; ++l) {
+                const double *Al = A + l * E + (int64_t)i * d;
+                const double *Pk = psi + (int64_t)(k - l) * E + j;
+                for (int u = 0; u < d; ++u) s = fma(-Al[u], Pk[(int64_t)u * d], s);
+            }
+            t[i] = s;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < d; i += blockDim.x) {
+            double v = 0.0;
+            for (int u = 0; u < d; ++u) v = fma(psi[(int64_t)i * d + u], t[u], v);
+            psi[(int64_t)k * E + (int64_t)i * d + j] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// rs[k][i] = sum_j q[k][i][j] for k >= 1, rs[0][i] = 0.
+__global__ void row_sums_kernel(const double *__restrict__ q, double *__restrict__ rs, int d, int64_t N)
+{
+    const int64_t n = N * d;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t k = t / d;
+        int i = (int)(t - k * d);
+        double s = 0.0;
+        if (k >= 1)
+            for (int j = 0; j < d; ++j) s += q[k * d * d + (int64_t)i * d + j];
+        rs[t] = s;
+    }
+}
+
+constexpr int SCAN_CH = 1024;
+
+__global__ void scan_chunk_sums(const double *__restrict__ x, int ncol, int64_t N, double *__restrict__ work)
+{
+    const int64_t nch = (N + SCAN_CH - 1) / SCAN_CH;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nch * ncol; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t ch = t / ncol;
+        int c = (int)(t - ch * ncol);
+        int64_t k1 = min(N, (ch + 1) * SCAN_CH);
+        double s = 0.0;
+        for (int64_t k = ch * SCAN_CH; k < k1; ++k) s += x[k * ncol + c];
+        work[t] = s;
+    }
+}
+
+__global__ void scan_chunk_offsets(double *work, int ncol, int64_t nch)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncol; c += gridDim.x * blockDim.x) {
+        double run = 0.0;
+        for (int64_t ch = 0; ch < nch; ++ch) {
+            double v = work[ch * ncol + c];
+            work[ch * ncol + c] = run;
+            run += v;
+        }
+    }
+}
+
+__global__ void scan_apply(double *__restrict__ x, int ncol, int64_t N, const double *__restrict__ work, double scale,
+                           double offset)
+{
+    const int64_t nch = (N + SCAN_CH - 1) / SCAN_CH;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nch * ncol; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t ch = t / ncol;
+        int c = (int)(t - ch * ncol);
+        int64_t k1 = min(N, (ch + 1) * SCAN_CH);
+        double run = work[t];
+        for (int64_t k = ch * SCAN_CH; k < k1; ++k) {
+            run += x[k * ncol + c];
+            x[k * ncol + c] = offset + scale * run;
+        }
+    }
+}
+
+// acc[0] += sum_k ||rho(k)||_F ; acc[1] = max |rho| (as ordered bits of a nonnegative double)
+__global__ void norms_kernel(const double *__restrict__ rho, int E, int64_t N, double *acc)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double fro_sum = 0.0, mx = 0.0;
+    for (int64_t k = warp; k < N; k += nwarps) {
+        double s = 0.0;
+        for (int e = lane; e < E; e += 32) {
+            double v = rho[k * E + e];
+            s = fma(v, v, s);
+            mx = fmax(mx, fabs(v));
+        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) fro_sum += sqrt(s);
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+        atomicAdd(&acc[0], fro_sum);
+        atomicMax(reinterpret_cast<unsigned long long *>(&acc[1]), (unsigned long long)__double_as_longlong(mx));
+    }
+}
+
+struct IdxList {
+    int n;
+    int idx[512];
+};
+
+// ACC(k) = delta(k) I - q_CC(k), QCD(k) = q_CD(k)  (Eq. (first-entrance-mass))
+__global__ void gather_blocks_kernel(const double *__restrict__ q, int d, int64_t N, IdxList C, IdxList D,
+                                     double *__restrict__ ACC, double *__restrict__ QCD)
+{
+    const int nC = C.n, nD = D.n;
+    const int64_t per = (int64_t)nC * (nC + nD);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N * per; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t k = t / per;
+        int rem = (int)(t - k * per);
+        int a = rem / (nC + nD), b = rem - a * (nC + nD);
+        if (b < nC) {
+            double v = -q[k * d * d + (int64_t)C.idx[a] * d + C.idx[b]];
+            if (k == 0 && a == b) v += 1.0;
+            ACC[k * nC * nC + (int64_t)a * nC + b] = v;
+        } else {
+            b -= nC;
+            QCD[k * nC * nD + (int64_t)a * nD + b] = q[k * d * d + (int64_t)C.idx[a] * d + D.idx[b]];
+        }
+    }
+}
+
+// out[k] = sum_{a,b} alpha[a] g[k][a][b]
+__global__ void weighted_rowsum_kernel(const double *__restrict__ g, int nC, int nD, int64_t N,
+                                       const double *__restrict__ alpha, double *__restrict__ out)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int a = 0; a < nC; ++a) {
+            double r = 0.0;
+            for (int b = 0; b < nD; ++b) r += g[k * nC * nD + (int64_t)a * nD + b];
+            s = fma(alpha[a], r, s);
+        }
+        out[k] = s;
+    }
+}
+
+// out[k] = alpha P(k) 1_B
+__global__ void occupation_kernel(const double *__restrict__ P, int d, int64_t N, const double *__restrict__ alpha,
+                                  IdxList B, double *__restrict__ out)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < d; ++i) {
+            double r = 0.0;
+            for (int b = 0; b < B.n; ++b) r += P[k * d * d + (int64_t)i * d + B.idx[b]];
+            s = fma(alpha[i], r, s);
+        }
+        out[k] = s;
+    }
+}
+
+__global__ void one_minus_kernel(const double *__restrict__ x, double *__restrict__ y, int64_t n)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        y[t] = 1.0 - x[t];
+}
+
+inline unsigned grid_for(int64_t n, int bs = 256)
+{
+    int64_t b = (n + bs - 1) / bs;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (unsigned)b;
+}
+
+} // namespace
+
+cudaError_t mrc_gauss_jordan(const double *A0, double *out, double *work, int d, int *status, cudaStream_t st)
+{
+    gj_kernel<<<1, 1024, sizeof(double) * d, st>>>(A0, out, work, d, status);
+    return cudaGetLastError();
+}
+
+cudaError_t mrc_base_case(const double *A, double *psi, int d, int64_t m0, cudaStream_t st)
+{
+    if (m0 <= 1) return cudaSuccess;
+    int bs = d < 32 ? 32 : (d > 512 ? 512 : ((d + 31) / 32) * 32);
+    base_case_kernel<<<d, bs, sizeof(double) * d, st>>>(A, psi, d, (int)m0);
+    return cudaGetLastError();
+}
+
+cudaError_t mrc_row_sums(const double *q, double *rs, int d, int64_t N, cudaStream_t st)
+{
+    row_sums_kernel<<<grid_for(N * d), 256, 0, st>>>(q, rs, d, N);
+    return cudaGetLastError();
+}
+
+cudaError_t mrc_scan_cols(double *x, int ncol, int64_t N, double *work, double scale, double offset, cudaStream_t st)
+{
+    const int64_t nch = (N + SCAN_CH - 1) / SCAN_CH;
+    scan_chunk_sums<<<grid_for(nch * ncol), 256, 0, st>>>(x, ncol, N, work);
+    scan_chunk_offsets<<<grid_for(ncol), 256, 0, st>>>(work, ncol, nch);
+    scan_apply<<<grid_for(nch * ncol), 256, 0, st>>>(x, ncol, N, work, scale, offset);
+    return cudaGetLastError();
+}
+
+cudaError_t mrc_norms(const double *rho, int E, int64_t N, double *acc, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(acc, 0, 2 * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    norms_kernel<<<grid_for(N * 32), 256, 0, st>>>(rho, E, N, acc);
+    return cudaGetLastError();
+}
+
+cudaError_t mrc_gather_blocks(const double *q, int d, int64_t N, const int *Cidx, int nC, const int *Didx, int nD,
+                              double *ACC, double *QCD, cudaStream_t st)
+{
+    IdxList C{}, D{};
+    C.n = nC;
+    D.n = nD;
+    for (int i = 0; i < nC; ++i) C.idx[i] = Cidx[i];
+    for (int i = 0; i < nD; ++i) D.idx[i] = Didx[i];
+    gather_blocks_kernel<<<grid_for(N * nC * (nC + nD)), 256, 0, st>>>(q, d, N, C, D, ACC, QCD);
+    return cudaGetLastError();
+}
+
+cudaError_t mrc_weighted_rowsum(const double *g, int nC, int nD, int64_t N, const double *alpha, double *out,
+                                cudaStream_t st)
+{
+    weighted_rowsum_kernel<<<grid_for(N), 256, 0, st>>>(g, nC, nD, N, alpha, out);
+    return cudaGetLastError();
+}
+
+cudaError_t mrc_occupation_k(const double *P, int d, int64_t N, const double *alpha, const int *inB, double *out,
+                             cudaStream_t st)
+{
+    IdxList B{};
+    B.n = 0;
+    for (int j = 0; j < d; ++j)
+        if (inB[j]) B.idx[B.n++] = j;
+    occupation_kernel<<<grid_for(N), 256, 0, st>>>(P, d, N, alpha, B, out);
+    return cudaGetLastError();
+}
+
+cudaError_t mrc_one_minus(const double *x, double *y, int64_t n, cudaStream_t st)
+{
+    one_minus_kernel<<<grid_for(n), 256, 0, st>>>(x, y, n);
+    return cudaGetLastError();
+}

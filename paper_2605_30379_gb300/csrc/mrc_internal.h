@@ -1,0 +1,97 @@
+// mrc_internal.h -- argument blocks and launcher declarations shared by the
+// per-precision kernel units and the host driver.  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+enum { SRC_CPLX = 0, SRC_REAL64 = 1 };
+enum { DST_CPLX = 0, DST_REAL64 = 1, DST_REAL64_ADD = 2 };
+enum { PREC_F64 = 0, PREC_F32 = 1, PREC_DD = 2 };
+
+struct FftArgs {
+    int64_t M;      // transform length, power of two
+    int logR;       // this pass: radix 2^logR
+    int logNs;      // product of earlier radices = 2^logNs
+    int64_t Ns;
+    int E;          // entries per row processed
+    int ec;         // entries per CTA
+    int dir;        // -1 forward (exp(-2 pi i ...)), +1 inverse (no 1/M; see dst_scale)
+    const void *tw; // forward twiddle table of 2^tw_log entries (working precision)
+    int tw_log;
+    // source
+    int src_mode;
+    const void *src;
+    int64_t src_row0;   // first row read
+    int64_t src_nvalid; // CPLX: valid packed rows; REAL64: valid real rows; beyond: zero
+    int src_ld;         // row stride (elements)
+    int src_neg;
+    // destination
+    int dst_mode;
+    void *dst;
+    int dst_ld;
+    int64_t dst_lo, dst_hi; // REAL64*: kept window of real rows
+    int64_t dst_row0;       // REAL64*: destination row of real row dst_lo
+    double dst_scale;       // signed power of two
+    int dst_eye_d;          // REAL64*: if > 0 add 1 to the diagonal of real row 0 (d = this)
+};
+
+struct PairArgs {
+    const void *zx, *zy;
+    void *zc;
+    const void *tw;
+    int tw_log;
+    int64_t M;
+    int logM;
+    int64_t npairs;
+    int r, m, c; // X: r x m, Y: m x c (pairdiag: Y is a c-vector, m unused)
+};
+
+// Source / destination descriptors used by the host-side FFT driver.
+struct FftSrc {
+    int mode;
+    const void *ptr;
+    int64_t row0, nvalid;
+    int ld;
+    int neg;
+};
+struct FftDst {
+    int mode;
+    void *ptr;
+    int ld;
+    int64_t lo, hi, row0;
+    double scale;
+    int eye_d;
+};
+
+// Per-precision launchers (k_f64.cu, k_f32.cu, k_dd.cu).
+#define MRC_DECLARE_PREC(SUF)                                                                         \
+    cudaError_t mrc_fft_##SUF(const FftSrc &src, const FftDst &dst, int64_t M, int E, int dir,        \
+                              void *scratch, const void *tw, int tw_log, cudaStream_t st);            \
+    cudaError_t mrc_pairmul_##SUF(const void *zx, const void *zy, void *zc, int64_t M, int r, int m,  \
+                                  int c, const void *tw, int tw_log, cudaStream_t st);                \
+    cudaError_t mrc_pairdiag_##SUF(const void *zx, const void *zy, void *zc, int64_t M, int r, int c, \
+                                   const void *tw, int tw_log, cudaStream_t st);                      \
+    cudaError_t mrc_twiddles_##SUF(void *tw, int tw_log, cudaStream_t st);                            \
+    cudaError_t mrc_init_##SUF(void);
+
+MRC_DECLARE_PREC(f64)
+MRC_DECLARE_PREC(f32)
+MRC_DECLARE_PREC(dd)
+
+// Element sizes of one complex value per precision.
+static inline size_t mrc_cx_bytes(int prec) { return prec == PREC_F32 ? 8 : 16; }
+
+// misc.cu
+cudaError_t mrc_gauss_jordan(const double *A0, double *out, double *work, int d, int *status, cudaStream_t st);
+cudaError_t mrc_base_case(const double *A, double *psi, int d, int64_t m0, cudaStream_t st);
+cudaError_t mrc_row_sums(const double *q, double *rs, int d, int64_t N, cudaStream_t st);
+cudaError_t mrc_scan_cols(double *x, int ncol, int64_t N, double *work, double scale, double offset,
+                          cudaStream_t st);
+cudaError_t mrc_norms(const double *rho, int E, int64_t N, double *acc, cudaStream_t st);
+cudaError_t mrc_gather_blocks(const double *q, int d, int64_t N, const int *Cidx, int nC, const int *Didx,
+                              int nD, double *ACC, double *QCD, cudaStream_t st);
+cudaError_t mrc_weighted_rowsum(const double *g, int nC, int nD, int64_t N, const double *alpha, double *out,
+                                cudaStream_t st);
+cudaError_t mrc_occupation_k(const double *P, int d, int64_t N, const double *alpha, const int *inB, double *out,
+                             cudaStream_t st);
+cudaError_t mrc_one_minus(const double *x, double *y, int64_t n, cudaStream_t st);

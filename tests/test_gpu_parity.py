@@ -1,0 +1,199 @@
+"""GPU parity: libmrc (through the C ABI) against the FP64 oracle on the same
+seeded inputs.
+
+Tolerances (stated in the design doc):
+* FP64 path: max_{k,i,j} |psi - psi_oracle| <= 1e-11 (absolute; every output
+  is a probability or a bounded renewal density).
+* mixed path: e_rel = sum_k ||psi(k) - psi_ref(k)||_F / sum_k ||psi_ref(k)||_F
+  <= 1e-10 and max |rho_L| <= 1e-10.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2605_30379_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+TOL_REL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def mrc():
+    from paper_2605_30379_gb300 import build
+    build.build()
+    from paper_2605_30379_gb300 import mrc as m
+    m.load()
+    return m
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+
+
+def e_rel(got, ref):
+    num = np.sqrt(((got - ref) ** 2).sum(axis=(1, 2))).sum()
+    den = np.sqrt((ref ** 2).sum(axis=(1, 2))).sum()
+    return num / den
+
+
+# ------------------------------------------------------------- inverse FP64
+@pytest.mark.parametrize("d,N,seed", [
+    (4, 1024, 0),    # the small d=4 horizon-1024 Weibull workload
+    (1, 1, 1), (1, 2, 1), (2, 3, 1), (3, 5, 2),   # degenerate / ragged horizons
+    (3, 1000, 3), (5, 513, 4), (9, 300, 5),        # non power-of-two N, odd d
+    (17, 700, 6), (40, 260, 7), (64, 130, 8),      # several product tiles, ragged
+    (16, 4096, 9),                                  # d=16 horizon-2^12 Weibull workload
+])
+def test_inverse_fp64_matches_oracle(mrc, d, N, seed):
+    if d == 1:
+        rng = np.random.default_rng(seed)
+        q = np.zeros((N, 1, 1))
+        q[1:, 0, 0] = rng.uniform(0, 1, N - 1) / max(1, N)
+    else:
+        q, _ = synth.weibull_model(d, N, seed=seed)
+    A = synth.identity_minus(q)
+    ref = oracle.inverse_left(A)
+    psi = mrc.inverse(dev(A), prec="fp64").cpu().numpy()
+    assert np.abs(psi - ref).max() <= TOL64
+
+
+def test_inverse_fp64_general_A0_lognormal(mrc):
+    """Mean-value reduction: A(0) = I - Q(h)/2 is not the identity."""
+    A, _ = synth.lognormal_model(8, 1500, seed=10, h=0.05)
+    ref = oracle.inverse_left(A)
+    psi = mrc.inverse(dev(A), prec="fp64").cpu().numpy()
+    assert np.abs(psi - ref).max() <= TOL64
+
+
+def test_inverse_fp64_signed_dense(mrc):
+    """A sequence with mixed signs and a dense non-identity A(0)."""
+    rng = np.random.default_rng(11)
+    d, N = 6, 777
+    A = rng.standard_normal((N, d, d)) * (0.5 ** np.arange(N))[:, None, None] * 0.3
+    A[0] += 2.0 * np.eye(d)
+    ref = oracle.inverse_left(A)
+    psi = mrc.inverse(dev(A), prec="fp64").cpu().numpy()
+    assert np.abs(psi - ref).max() <= TOL64 * max(1.0, np.abs(ref).max())
+
+
+def test_markov_closed_form_d16(mrc):
+    """Geometric sojourns: psi(k) = M^{k-1} diag(p) P^emb."""
+    d, N = 16, 4096
+    q, prm = synth.geometric_model(d, N, seed=12)
+    M = np.diag(1 - prm["p"]) + np.diag(prm["p"]) @ prm["P"]
+    J = np.diag(prm["p"]) @ prm["P"]
+    psi = mrc.inverse(dev(synth.identity_minus(q)), prec="fp64").cpu().numpy()
+    Mk = np.eye(d)
+    worst = 0.0
+    for k in range(1, N):
+        worst = max(worst, np.abs(psi[k] - Mk @ J).max())
+        Mk = Mk @ M
+    assert worst <= TOL64
+    assert np.all(psi[0] == np.eye(d))
+
+
+def test_singular_A0_reports_error(mrc):
+    A = np.zeros((64, 3, 3))
+    A[0] = [[1, 2, 3], [2, 4, 6], [0, 0, 1.0]]
+    with pytest.raises(mrc.MrcError) as ei:
+        mrc.inverse(dev(A), prec="fp64", report=True)
+    assert ei.value.status == 2
+    # the context stays usable after the error
+    q, _ = synth.weibull_model(3, 64, seed=1)
+    A2 = synth.identity_minus(q)
+    psi = mrc.inverse(dev(A2), prec="fp64", report=True)[0].cpu().numpy()
+    assert np.abs(psi - oracle.inverse_left(A2)).max() <= TOL64
+
+
+# ------------------------------------------------------------ inverse mixed
+@pytest.mark.parametrize("d,N,seed", [(4, 1024, 0), (3, 777, 1), (16, 2048, 2), (33, 300, 3)])
+def test_inverse_mixed_matches_oracle(mrc, d, N, seed):
+    q, _ = synth.weibull_model(d, N, seed=seed)
+    A = synth.identity_minus(q)
+    ref = oracle.inverse_left(A)
+    psi, rep = mrc.inverse(dev(A), prec="mixed", sweeps=1, target_residual=1e-10, report=True)
+    psi = psi.cpu().numpy()
+    assert e_rel(psi, ref) <= TOL_REL
+    assert rep["res_max_abs"] <= TOL_REL
+
+
+def test_inverse_mixed_lognormal_general_A0(mrc):
+    A, _ = synth.lognormal_model(12, 1024, seed=4, h=0.05)
+    ref = oracle.inverse_left(A)
+    psi = mrc.inverse(dev(A), prec="mixed").cpu().numpy()
+    assert e_rel(psi, ref) <= TOL_REL
+
+
+# ------------------------------------------------------------------ residual
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_residual_matches_oracle(mrc, prec):
+    rng = np.random.default_rng(20)
+    q, _ = synth.weibull_model(5, 600, seed=20)
+    A = synth.identity_minus(q)
+    psi = oracle.inverse_left(A) + 1e-6 * rng.standard_normal(A.shape)
+    rl_ref, rr_ref = oracle.residuals(A, psi)
+    rl, rr, rep = mrc.residual(dev(A), dev(psi), sides=3, prec=prec)
+    rl, rr = rl.cpu().numpy(), rr.cpu().numpy()
+    assert np.abs(rl - rl_ref).max() <= 1e-12
+    assert np.abs(rr - rr_ref).max() <= 1e-12
+    assert abs(rep["res_left_l1"] - oracle.norm1_frob(rl_ref)) <= 1e-9 * oracle.norm1_frob(rl_ref)
+    assert abs(rep["res_right_l1"] - oracle.norm1_frob(rr_ref)) <= 1e-9 * oracle.norm1_frob(rr_ref)
+    assert abs(rep["res_max_abs"] - np.abs(rl_ref).max()) <= 1e-12
+
+
+# ---------------------------------------------------------- derived outputs
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_transition_matches_oracle(mrc, prec):
+    d, N = 6, 900
+    q, _ = synth.weibull_model(d, N, seed=21)
+    psi = oracle.inverse_left(synth.identity_minus(q))
+    ref = oracle.transition(psi, q)
+    P = mrc.transition(dev(psi), dev(q), prec=prec).cpu().numpy()
+    assert np.abs(P - ref).max() <= TOL64
+    assert np.abs(P.sum(axis=2) - 1.0).max() <= 1e-12
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("mixed", 1e-10)])
+def test_first_entrance_matches_oracle(mrc, prec, tol):
+    d, N = 7, 800
+    q, _ = synth.weibull_model(d, N, seed=22)
+    D = [2, 6]
+    alphaC = np.array([0.1, 0.2, 0.3, 0.2, 0.2])
+    g_ref, F_ref, S_ref = oracle.first_entrance(q, D, alphaC)
+    g, F, S = mrc.first_entrance(dev(q), D, torch.tensor(alphaC), prec=prec)
+    assert np.abs(g.cpu().numpy() - g_ref).max() <= tol
+    assert np.abs(F.cpu().numpy() - F_ref).max() <= tol
+    assert np.abs(S.cpu().numpy() - S_ref).max() <= tol
+
+
+def test_paper_first_entrance_example(mrc):
+    """Section 5.1 example: D = {1}, C = {2, 3}, alpha_C = (1, 0), N = 128."""
+    q = synth.poisson_paper_e4(128)
+    g_ref, F_ref, S_ref = oracle.first_entrance(q, [0], np.array([1.0, 0.0]))
+    g, F, S = mrc.first_entrance(dev(q), [0], torch.tensor([1.0, 0.0]), prec="fp64")
+    mass = g.cpu().numpy()[:, 0, 0]
+    assert np.abs(mass - g_ref[:, 0, 0]).max() <= 1e-15
+    assert abs(F.cpu().numpy()[-1] - 1.0) < 1e-6
+
+
+def test_occupation_matches_oracle(mrc):
+    d, N = 5, 400
+    q, _ = synth.weibull_model(d, N, seed=23)
+    psi = oracle.inverse_left(synth.identity_minus(q))
+    P = oracle.transition(psi, q)
+    alpha = np.array([0.3, 0.1, 0.2, 0.2, 0.2])
+    ref = oracle.occupation(P, alpha, [0, 1, 3])
+    got = mrc.occupation(dev(P), torch.tensor(alpha), [0, 1, 3]).cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-14
+
+
+def test_batched_matches_single(mrc):
+    models = synth.batch_models(n=6, seed=3, d_range=(3, 12), logN_range=(6.0, 9.0))
+    As = [dev(m["A"]) for m in models]
+    outs = mrc.inverse_batched(As, prec="fp64")
+    for m, o in zip(models, outs):
+        ref = oracle.inverse_left(m["A"])
+        assert np.abs(o.cpu().numpy() - ref).max() <= TOL64
