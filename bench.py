@@ -1,0 +1,386 @@
+#!/usr/bin/env python3
+"""Throughput benchmark: psi coefficients/s of FFT-Newton inversion on GB300.
+
+One step = one call of the public inverse (mrc_inverse) on the whole workload:
+Gauss-Jordan of A(0), all Newton doubling levels and, for the mixed path, the
+double-float residual and FP32 correction sweep.  Inputs are resident in HBM
+when the timed region starts; the e2e figure repeats the measurement with the
+host->device copy of A and the device->host copy of psi inside the timed
+region.
+
+Default workload (the precision configuration of the metric): d = 64 states,
+horizon N = 2^18, Lognormal sojourns sigma ~ U[1,2], mu ~ U[0,3] reduced by the
+endpoint mean-value rule with h = 0.05 (A(0) = I - Q(h)/2), Dirichlet(1)
+zero-diagonal embedded chain, seed 0.  A and psi are 8.6 GB each, far larger
+than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mrc|reference]
+                    [--workload NAME] [--prec mixed|fp64]
+
+Multi-GPU (torchrun): the workload is one model, which does not shard
+(replicas only): each rank inverts its own replica; value = all ranks'
+coefficients / max-over-ranks time ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (d, N, kind, extra)
+    "lognormal_d64_N262144": (64, 1 << 18, "lognormal", {}),
+    "weibull_d16_N65536": (16, 1 << 16, "weibull", {}),
+    "weibull_d4_N1024": (4, 1024, "weibull", {}),
+    "lognormal_d64_N65536": (64, 1 << 16, "lognormal", {}),
+    "weibull_d256_N32768": (256, 1 << 15, "weibull", {"alpha": 0.5, "shape": (0.5, 3.0)}),
+}
+DEFAULT_WORKLOAD = "lognormal_d64_N262144"
+
+# kernel classes of the library's profiler (include/mrc.h MRC_K_*)
+KCLASS = {1: "fft_f64", 2: "fft_f32", 3: "fft_dd", 4: "pairmul_f64", 5: "pairmul_f32", 6: "pairmul_dd", 7: "misc"}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP32 instruction issue: 152 SMs x 128 lanes per clock.  A double-float
+# complex multiply-accumulate (4 dd fma, 15 FP32 instructions each) is 8
+# dd-flops, i.e. 7.5 FP32 instructions per dd-flop.  FP64 DFMA rate measured
+# on this machine's GB300 by a dependent-chain-free FMA loop: 1.19 TFLOP/s.
+FP32_LANES = 152 * 128
+DD_INSTR_PER_FLOP = 7.5
+FP64_TFLOPS_MEASURED = 1.19
+
+
+def roofline_for(kclass, ms_total, launches, bytes_, flops, peaks, sm_mhz):
+    if not launches:
+        return None
+    per_ms = ms_total / launches
+    name = KCLASS[kclass]
+    clk = (sm_mhz or 2070.0) * 1e6
+    if name.startswith("fft_f32") or name == "misc":
+        ach = bytes_ / launches / (per_ms * 1e-3) / 1e9
+        peak = peaks["hbm_gbs"]
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": None, "launches": launches, "avg_ms": per_ms,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    if name.endswith("_dd"):
+        ach = flops / launches / (per_ms * 1e-3) / 1e12
+        peak = FP32_LANES * clk / DD_INSTR_PER_FLOP / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "launches": launches, "avg_ms": per_ms,
+                "peak_source": f"double-float flops: 152x128 FP32 lanes x {clk/1e6:.0f} MHz / 7.5 instr per dd-flop"}
+    if name.endswith("_f64"):
+        ach = flops / launches / (per_ms * 1e-3) / 1e12
+        peak = FP64_TFLOPS_MEASURED
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "launches": launches, "avg_ms": per_ms,
+                "peak_source": "FP64 DFMA loop measured on GB300 (1.19 TFLOP/s)"}
+    # pairmul_f32: FP32 FFMA bound at d >= 16 (intensity d/3 flop/B above the FFMA/HBM ridge)
+    ach = flops / launches / (per_ms * 1e-3) / 1e12
+    peak = FP32_LANES * 2 * clk / 1e12
+    return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": None, "launches": launches, "avg_ms": per_ms,
+            "peak_source": f"FP32 FFMA: 152x128 lanes x 2 x {clk/1e6:.0f} MHz"}
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_input(name):
+    from paper_2605_30379_gb300 import synth
+    d, N, kind, extra = WORKLOADS[name]
+    if kind == "lognormal":
+        A, _ = synth.lognormal_model(d, N, seed=0, h=0.05)
+    else:
+        q, _ = synth.weibull_model(d, N, seed=0, **extra)
+        A = synth.identity_minus(q)
+    return A
+
+
+def cpu_oracle_sample(A_host, d, budget_s=15.0):
+    """Time the FP64 oracle (direct recursion) on a prefix of the same input,
+    doubling the prefix until one call takes >= budget_s / 4 (then one timed call)."""
+    import oracle
+    n = 64
+    while True:
+        t0 = time.perf_counter()
+        oracle.inverse_left(A_host[:n])
+        dt = time.perf_counter() - t0
+        if dt >= budget_s / 4 or 2 * n > A_host.shape[0]:
+            break
+        n *= 2
+    t0 = time.perf_counter()
+    oracle.inverse_left(A_host[:n])
+    dt = time.perf_counter() - t0
+    return n, dt, oracle.num_threads()
+
+
+def run_reference(args, rank, world):
+    """The oracle timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    name = args.workload
+    d, N, kind, _ = WORKLOADS[name]
+    from paper_2605_30379_gb300 import synth
+    # prefix of the same seeded workload (the generator is prefix-consistent)
+    if kind == "lognormal":
+        A, _ = synth.lognormal_model(d, min(N, 8192), seed=0, h=0.05)
+    else:
+        q, _ = synth.weibull_model(d, min(N, 8192), seed=0, **WORKLOADS[name][3])
+        A = synth.identity_minus(q)
+    import oracle
+    n, dt, cores = cpu_oracle_sample(A, d, budget_s=8.0)
+    for _ in range(args.warmup):
+        oracle.inverse_left(A[:n])
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.inverse_left(A[:n])
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    value = n * d * d / (ms * 1e-3)
+    sample = f"prefix k < {n} of the {name} workload (the oracle costs d^3 n^2 / 2, so its rate falls as 1/n)"
+    out = {"impl": "reference", "metric": "psi coefficients/s (N*d^2)", "value": value,
+           "unit": "coefficients/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic", "config": {"workload": name, "d": d, "N": N},
+           "cpu_baseline": {"value": value, "unit": "coefficients/s", "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "coefficients/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mrc", choices=["mrc", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-breakdown", action="store_true", help="skip the per-kernel-class timing steps")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2605_30379_gb300 import mrc
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    d, N, kind, _ = WORKLOADS[args.workload]
+    coeffs = N * d * d
+    A_host_np = make_input(args.workload)
+    A_pin = torch.from_numpy(A_host_np).pin_memory()
+    A = A_pin.to("cuda", non_blocking=False)
+    psi = torch.empty_like(A)
+    psi_pin = torch.empty(A.shape, dtype=torch.float64).pin_memory()
+    lib = mrc.load()
+    import ctypes
+    lib.mrc_launch_count.restype = ctypes.c_ulonglong
+    lib.mrc_profile_begin.argtypes = [ctypes.c_int]
+    lib.mrc_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    stream = torch.cuda.current_stream()
+
+    def step(prec=args.prec):
+        mrc.inverse(A, prec=prec, sweeps=1, out=psi)
+
+    def prof(kclass, fn):
+        lib.mrc_profile_begin(kclass)
+        fn()
+        ms, n, b, f = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+        lib.mrc_profile_end(ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b), ctypes.byref(f))
+        return ms.value, n.value, b.value, f.value
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # per-class device time of one step (untimed), to pick the dominant kernel
+    breakdown = {}
+    for kc in ([] if args.no_breakdown else KCLASS):
+        ms, n, b, f = prof(kc, step)
+        if n:
+            breakdown[KCLASS[kc]] = {"ms": ms, "launches": n}
+    dominant = max((kc for kc in KCLASS if KCLASS[kc] in breakdown), key=lambda kc: breakdown[KCLASS[kc]]["ms"],
+                   default=6 if args.prec == "mixed" else 4)
+
+    # ---- timed region (device-resident inputs)
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    lib.mrc_profile_begin(dominant)
+    l0 = lib.mrc_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = lib.mrc_launch_count() - l0
+    pms, pn, pb, pf = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+    lib.mrc_profile_end(ctypes.byref(pms), ctypes.byref(pn), ctypes.byref(pb), ctypes.byref(pf))
+    barrier()
+    clocks = sampler.stop()
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    value = world * coeffs / (ms_step * 1e-3)
+
+    # ---- the plain FP64 path on the same inputs
+    fp64 = None
+    if args.prec == "mixed" and args.fp64_steps > 0:
+        step("fp64")
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for _ in range(args.fp64_steps):
+            step("fp64")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = max_over_ranks(e0.elapsed_time(e1) / args.fp64_steps)
+        fp64 = {"value": world * coeffs / (ms64 * 1e-3), "ms_per_step": ms64, "steps": args.fp64_steps}
+        step()  # leave the mixed result in psi for the accuracy check
+        torch.cuda.synchronize()
+
+    # ---- accuracy of the timed path: double-float residual of psi
+    _, _, rep = mrc.residual(A, psi, sides=3, prec="mixed", want_rho=False)
+
+    # ---- e2e through the public API with host buffers
+    ms_e2e = None
+    if not args.no_e2e:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            A.copy_(A_pin, non_blocking=True)
+            step()
+            psi_pin.copy_(psi, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+
+    peaks, peak_kind = load_peaks()
+    roof = roofline_for(dominant, pms.value, pn.value, pb.value, pf.value, peaks,
+                        clocks["sm_mhz"] if clocks else None)
+    if roof:
+        roof["peak_kind"] = peak_kind
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n, dt, cores = cpu_oracle_sample(A_host_np, d)
+        cpu = {"value": n * d * d / dt, "unit": "coefficients/s", "cores": cores, "kind": "oracle",
+               "sample": f"one call on the prefix k < {n} of the same workload, {dt:.1f} s "
+                         f"(direct recursion, cost d^3 n^2 / 2: its rate falls as 1/n)"}
+
+    if rank == 0:
+        out = {
+            "metric": "psi coefficients/s (N*d^2), mixed precision at <= 1e-10 residual",
+            "value": value, "unit": "coefficients/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+dd" if args.prec == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "d": d, "N": N, "prec": args.prec, "sweeps": 1,
+                       "l2": "inputs (8.6 GB) larger than L2; no flush" if coeffs * 8 > 2e8 else
+                             "inputs smaller than L2: latency-bound, no flush",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "accuracy": {"max_abs_rho_L": rep["res_max_abs"], "rho_L_l1": rep["res_left_l1"],
+                         "rho_R_l1": rep["res_right_l1"]},
+            "fp64_path": fp64,
+            "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
+            "gpu_launches": int(launches),
+            "stage_ms": breakdown,
+            "roofline": roof,
+            "clocks": clocks,
+            "e2e": None if ms_e2e is None else {
+                "value": world * coeffs / (ms_e2e * 1e-3), "unit": "coefficients/s",
+                "h2d_bytes_per_step": coeffs * 8, "d2h_bytes_per_step": coeffs * 8, "ms_per_step": ms_e2e},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

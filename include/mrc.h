@@ -174,6 +174,35 @@ mrc_status mrc_first_entrance(mrc_ctx *ctx, int d, int64_t N, const double *q, c
 mrc_status mrc_occupation(mrc_ctx *ctx, int d, int64_t N, const double *P, const double *alpha,
                           const int *B, int nB, double *out, void *stream);
 
+/*
+ * Instrumentation (no counterpart in the paper; used to report the roofline
+ * of one kernel class measured inside a timed region).
+ *
+ * mrc_launch_count: number of CUDA kernel launches this library has issued
+ * since it was loaded (all contexts).
+ *
+ * mrc_profile_begin(kclass): from now on, record a CUDA event pair on the
+ * launching stream around every launch of kernel class `kclass`
+ * (MRC_K_* below; 0 switches recording off) and accumulate the algorithmic
+ * bytes and flops each launch is charged with (the per-unit figures in the
+ * design notes).  mrc_profile_end synchronises the recorded events and returns
+ * the summed device time (ms), the number of timed launches and the charged
+ * bytes and flops, then switches recording off.  At most 8192 launches are
+ * timed per begin/end; later launches are counted by mrc_launch_count only.
+ * Not thread safe.
+ */
+#define MRC_K_FFT_F64 1
+#define MRC_K_FFT_F32 2
+#define MRC_K_FFT_DD 3
+#define MRC_K_PAIR_F64 4
+#define MRC_K_PAIR_F32 5
+#define MRC_K_PAIR_DD 6
+#define MRC_K_MISC 7
+#define MRC_KCLASS_MAX 7
+unsigned long long mrc_launch_count(void);
+mrc_status mrc_profile_begin(int kclass);
+mrc_status mrc_profile_end(double *ms_total, long long *launches, double *bytes, double *flops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,6 +1,7 @@
 // launchers.cuh -- host-side launchers for one working precision T.  Each
 // k_<prec>.cu includes this file once with MRC_T / MRC_SUF defined.
 #pragma once
+#include <algorithm>
 #include "kernels.cuh"
 
 namespace {
@@ -11,6 +12,12 @@ inline int ilog2_i64(int64_t x)
     while (((int64_t)1 << l) < x) ++l;
     return l;
 }
+
+template <class T> constexpr int kclass_fft();
+template <> constexpr int kclass_fft<double>() { return 1; }
+template <> constexpr int kclass_fft<float>() { return 2; }
+template <> constexpr int kclass_fft<dd>() { return 3; }
+template <class T> constexpr int kclass_pair() { return kclass_fft<T>() + 3; }
 
 template <class T>
 constexpr int default_ec() { return sizeof(cx<T>) == 8 ? 16 : 8; }
@@ -67,7 +74,16 @@ cudaError_t fft_run(const FftSrc &src, const FftDst &dst, int64_t M, int E, int 
             a.dst_scale = 1.0; a.dst_eye_d = 0;
         }
         dim3 grid((unsigned)(M >> a.logR), (unsigned)((E + ec - 1) / ec));
+        // algorithmic charge: the valid source rows read once, the kept output written once,
+        // 5 M log2(R) real flops per entry (radix-2 convention)
+        double rd, wr;
+        if (a.src_mode == SRC_REAL64) rd = (double)std::min<int64_t>(a.src_nvalid, 2 * M) * E * 8.0;
+        else rd = (double)std::min<int64_t>(a.src_nvalid, M) * E * sizeof(cx<T>);
+        if (a.dst_mode == DST_CPLX) wr = (double)M * E * sizeof(cx<T>);
+        else wr = (double)(a.dst_hi - a.dst_lo) * E * 8.0 * (a.dst_mode == DST_REAL64_ADD ? 2.0 : 1.0);
+        mrc_prof_pre(kclass_fft<T>(), st);
         fft_pass_kernel<T><<<grid, 256, fft_smem_bytes<T>(a.logR, ec), st>>>(a);
+        mrc_prof_post(kclass_fft<T>(), st, rd + wr, 5.0 * (double)M * a.logR * E);
         logNs += a.logR;
     }
     return cudaGetLastError();
@@ -78,7 +94,11 @@ cudaError_t pairmul_launch(const PairArgs &a, cudaStream_t st)
 {
     const int tiles = ((a.r + BM - 1) / BM) * ((a.c + BN - 1) / BN);
     dim3 grid((unsigned)a.npairs, (unsigned)tiles);
+    const double bytes = (double)a.M * ((double)a.r * a.m + (double)a.m * a.c + (double)a.r * a.c) * sizeof(cx<T>);
+    const double flops = 8.0 * a.r * a.m * a.c * (double)(a.M + 1);
+    mrc_prof_pre(kclass_pair<T>(), st);
     pairmul_kernel<T, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(a);
+    mrc_prof_post(kclass_pair<T>(), st, bytes, flops);
     return cudaGetLastError();
 }
 
@@ -107,14 +127,19 @@ cudaError_t pairdiag_run(const void *zx, const void *zy, void *zc, int64_t M, in
     const int64_t total = a.npairs * (int64_t)r * c;
     int64_t blocks = (total + 255) / 256;
     if (blocks > 152 * 32) blocks = 152 * 32;
+    const double bytes = (double)M * (2.0 * r * c + c) * sizeof(cx<T>);
+    mrc_prof_pre(kclass_pair<T>(), st);
     pairdiag_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(a);
+    mrc_prof_post(kclass_pair<T>(), st, bytes, 6.0 * r * c * (double)(M + 1));
     return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t twiddles_run(void *tw, int tw_log, cudaStream_t st)
 {
+    mrc_prof_pre(7, st);
     twiddle_kernel<T><<<152 * 8, 256, 0, st>>>(reinterpret_cast<cx<T> *>(tw), tw_log);
+    mrc_prof_post(7, st, 0, 0);
     return cudaGetLastError();
 }
 

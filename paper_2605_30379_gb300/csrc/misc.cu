@@ -279,7 +279,9 @@ inline unsigned grid_for(int64_t n, int bs = 256)
 
 cudaError_t mrc_gauss_jordan(const double *A0, double *out, double *work, int d, int *status, cudaStream_t st)
 {
+    mrc_prof_pre(7, st);
     gj_kernel<<<1, 1024, sizeof(double) * d, st>>>(A0, out, work, d, status);
+    mrc_prof_post(7, st, 0, 0);
     return cudaGetLastError();
 }
 
@@ -287,22 +289,32 @@ cudaError_t mrc_base_case(const double *A, double *psi, int d, int64_t m0, cudaS
 {
     if (m0 <= 1) return cudaSuccess;
     int bs = d < 32 ? 32 : (d > 512 ? 512 : ((d + 31) / 32) * 32);
+    mrc_prof_pre(7, st);
     base_case_kernel<<<d, bs, sizeof(double) * d, st>>>(A, psi, d, (int)m0);
+    mrc_prof_post(7, st, 0, 0);
     return cudaGetLastError();
 }
 
 cudaError_t mrc_row_sums(const double *q, double *rs, int d, int64_t N, cudaStream_t st)
 {
+    mrc_prof_pre(7, st);
     row_sums_kernel<<<grid_for(N * d), 256, 0, st>>>(q, rs, d, N);
+    mrc_prof_post(7, st, 0, 0);
     return cudaGetLastError();
 }
 
 cudaError_t mrc_scan_cols(double *x, int ncol, int64_t N, double *work, double scale, double offset, cudaStream_t st)
 {
     const int64_t nch = (N + SCAN_CH - 1) / SCAN_CH;
+    mrc_prof_pre(7, st);
     scan_chunk_sums<<<grid_for(nch * ncol), 256, 0, st>>>(x, ncol, N, work);
+    mrc_prof_post(7, st, 0, 0);
+    mrc_prof_pre(7, st);
     scan_chunk_offsets<<<grid_for(ncol), 256, 0, st>>>(work, ncol, nch);
+    mrc_prof_post(7, st, 0, 0);
+    mrc_prof_pre(7, st);
     scan_apply<<<grid_for(nch * ncol), 256, 0, st>>>(x, ncol, N, work, scale, offset);
+    mrc_prof_post(7, st, 0, 0);
     return cudaGetLastError();
 }
 
@@ -310,7 +322,9 @@ cudaError_t mrc_norms(const double *rho, int E, int64_t N, double *acc, cudaStre
 {
     cudaError_t e = cudaMemsetAsync(acc, 0, 2 * sizeof(double), st);
     if (e != cudaSuccess) return e;
+    mrc_prof_pre(7, st);
     norms_kernel<<<grid_for(N * 32), 256, 0, st>>>(rho, E, N, acc);
+    mrc_prof_post(7, st, 0, 0);
     return cudaGetLastError();
 }
 
@@ -322,14 +336,18 @@ cudaError_t mrc_gather_blocks(const double *q, int d, int64_t N, const int *Cidx
     D.n = nD;
     for (int i = 0; i < nC; ++i) C.idx[i] = Cidx[i];
     for (int i = 0; i < nD; ++i) D.idx[i] = Didx[i];
+    mrc_prof_pre(7, st);
     gather_blocks_kernel<<<grid_for(N * nC * (nC + nD)), 256, 0, st>>>(q, d, N, C, D, ACC, QCD);
+    mrc_prof_post(7, st, 0, 0);
     return cudaGetLastError();
 }
 
 cudaError_t mrc_weighted_rowsum(const double *g, int nC, int nD, int64_t N, const double *alpha, double *out,
                                 cudaStream_t st)
 {
+    mrc_prof_pre(7, st);
     weighted_rowsum_kernel<<<grid_for(N), 256, 0, st>>>(g, nC, nD, N, alpha, out);
+    mrc_prof_post(7, st, 0, 0);
     return cudaGetLastError();
 }
 
@@ -340,12 +358,16 @@ cudaError_t mrc_occupation_k(const double *P, int d, int64_t N, const double *al
     B.n = 0;
     for (int j = 0; j < d; ++j)
         if (inB[j]) B.idx[B.n++] = j;
+    mrc_prof_pre(7, st);
     occupation_kernel<<<grid_for(N), 256, 0, st>>>(P, d, N, alpha, B, out);
+    mrc_prof_post(7, st, 0, 0);
     return cudaGetLastError();
 }
 
 cudaError_t mrc_one_minus(const double *x, double *y, int64_t n, cudaStream_t st)
 {
+    mrc_prof_pre(7, st);
     one_minus_kernel<<<grid_for(n), 256, 0, st>>>(x, y, n);
+    mrc_prof_post(7, st, 0, 0);
     return cudaGetLastError();
 }

@@ -63,6 +63,10 @@ struct FftDst {
     int eye_d;
 };
 
+// prof.cu: every launch is bracketed by these (launch counter, optional timing)
+void mrc_prof_pre(int kclass, cudaStream_t st);
+void mrc_prof_post(int kclass, cudaStream_t st, double bytes, double flops);
+
 // Per-precision launchers (k_f64.cu, k_f32.cu, k_dd.cu).
 #define MRC_DECLARE_PREC(SUF)                                                                         \
     cudaError_t mrc_fft_##SUF(const FftSrc &src, const FftDst &dst, int64_t M, int E, int dir,        \
