@@ -175,6 +175,31 @@ mrc_status mrc_occupation(mrc_ctx *ctx, int d, int64_t N, const double *P, const
                           const int *B, int nB, double *out, void *stream);
 
 /*
+ * mrc_inverse_noalloc -- the FP64 inverse of mrc_inverse (same kernels, same
+ * result) for callers that cannot let a library allocate device memory: a
+ * process whose device memory is already owned by another allocator's pool,
+ * code that forbids dynamic allocation after initialisation, or a plugin host
+ * that only hands out fixed buffers.  The paper has no counterpart; this is
+ * an interface variant only.
+ *   d, N, A, psi, stream : as mrc_inverse with prec = MRC_FP64.
+ * Scratch: one fixed 64 MiB device array inside the library (held on every
+ * GPU that loads the library until the process exits).  The call uses
+ * 256 B + 512 KiB (twiddles) + 16 d^2 + 4 * 16 d^2 * M bytes of it, M being
+ * the largest Newton level (< N); N must be <= 2^14.  Larger requests return
+ * MRC_ERR_NO_MEMORY at once, with the limit printed to stderr.
+ * No cudaMalloc/cudaFree or allocating library routine is called.
+ * The first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress) and fills the twiddle table, synchronously: make
+ * that first call before any stream capture.  Every call then clears the
+ * status word, enqueues the work on `stream`, synchronises `stream` and
+ * returns MRC_OK or MRC_ERR_SINGULAR_A0.  All calls share the array and it
+ * keeps the last call's contents: calls whose work overlaps on the GPU (two
+ * host threads, or two streams) race on it and must be serialised by the
+ * caller.
+ */
+mrc_status mrc_inverse_noalloc(int d, int64_t N, const double *A, double *psi, void *stream);
+
+/*
  * Instrumentation (no counterpart in the paper; used to report the roofline
  * of one kernel class measured inside a timed region).
  *
