@@ -16,16 +16,20 @@
 // exactly the L/2+1 frequencies of the half spectrum (Eq. (fft-convolution)
 // restricted to Hermitian spectra).
 #pragma once
+#include <utility>
+
 #include "arith.cuh"
 #include "mrc_internal.h"
 
 // ---------------------------------------------------------------------------
 // FFT pass: one radix-R Stockham step of a length-M transform (R = 2^logR,
 // Ns = product of the earlier radices).  CTA (j, chunk) loads the R elements
-// j + r*M/R of `ec` consecutive entries, applies the inter-pass twiddles
-// W_{Ns R}^{(j mod Ns) r}, runs the length-R DFT in shared memory (radix-2,
-// bit-reversed load), and writes element f to (j/Ns)*Ns*R + (j mod Ns) + f*Ns.
-// After the last pass the output is in natural frequency order.
+// j + r*M/R of EC consecutive entries, applies the inter-pass twiddles
+// W_{Ns R}^{(j mod Ns) r}, runs the length-R DFT as in-CTA Stockham stages of
+// radix 2/4 then 8 with the points of each butterfly in registers and one
+// shared-memory exchange per stage, and writes element f to
+// (j/Ns)*Ns*R + (j mod Ns) + f*Ns.  After the last pass the output is in
+// natural frequency order.
 template <class T>
 __device__ __forceinline__ cx<T> fft_load(const FftArgs &a, int64_t k, int e)
 {
@@ -68,74 +72,191 @@ __device__ __forceinline__ void fft_store(const FftArgs &a, int64_t k, int e, cx
     }
 }
 
-template <class T>
-__global__ void __launch_bounds__(256) fft_pass_kernel(FftArgs a)
+// Small DFTs in registers, natural order in and out.  INV selects the sign
+// of the exponent (+ for the inverse transform).
+template <class T, bool INV>
+__device__ __forceinline__ cx<T> mul_mi(cx<T> a)  // a * (-i) forward, a * (+i) inverse
 {
+    return INV ? cx<T>{Ar<T>::neg(a.im), a.re} : cx<T>{a.im, Ar<T>::neg(a.re)};
+}
+
+template <class T, bool INV>
+__device__ __forceinline__ void dft2(cx<T> *v)
+{
+    cx<T> t = v[0];
+    v[0] = c_add(t, v[1]);
+    v[1] = c_sub(t, v[1]);
+}
+
+template <class T, bool INV>
+__device__ __forceinline__ void dft4(cx<T> *v)
+{
+    cx<T> c0 = c_add(v[0], v[2]), c2 = c_sub(v[0], v[2]);
+    cx<T> c1 = c_add(v[1], v[3]), c3 = mul_mi<T, INV>(c_sub(v[1], v[3]));
+    v[0] = c_add(c0, c1);
+    v[2] = c_sub(c0, c1);
+    v[1] = c_add(c2, c3);
+    v[3] = c_sub(c2, c3);
+}
+
+// radix-8 = one radix-2 step (decimation in frequency) + two radix-4 DFTs
+template <class T, bool INV>
+__device__ __forceinline__ void dft8(cx<T> *v)
+{
+    const T s = Ar<T>::from_d(0.70710678118654752440);
+    cx<T> a[4], b[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        a[n] = c_add(v[n], v[n + 4]);
+        b[n] = c_sub(v[n], v[n + 4]);
+    }
+    // b_n *= W_8^{n} (forward) or W_8^{-n} (inverse)
+    {
+        cx<T> x = b[1];
+        b[1] = INV ? cx<T>{Ar<T>::mul(Ar<T>::sub(x.re, x.im), s), Ar<T>::mul(Ar<T>::add(x.re, x.im), s)}
+                   : cx<T>{Ar<T>::mul(Ar<T>::add(x.re, x.im), s), Ar<T>::mul(Ar<T>::sub(x.im, x.re), s)};
+        b[2] = mul_mi<T, INV>(b[2]);
+        x = b[3];
+        b[3] = INV ? cx<T>{Ar<T>::mul(Ar<T>::neg(Ar<T>::add(x.re, x.im)), s), Ar<T>::mul(Ar<T>::sub(x.re, x.im), s)}
+                   : cx<T>{Ar<T>::mul(Ar<T>::sub(x.im, x.re), s), Ar<T>::mul(Ar<T>::neg(Ar<T>::add(x.re, x.im)), s)};
+    }
+    dft4<T, INV>(a);
+    dft4<T, INV>(b);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[2 * k] = a[k];
+        v[2 * k + 1] = b[k];
+    }
+}
+
+template <class T, bool INV, int LR>
+__device__ __forceinline__ void dft_r(cx<T> *v)
+{
+    if constexpr (LR == 0) return;
+    else if constexpr (LR == 1) dft2<T, INV>(v);
+    else if constexpr (LR == 2) dft4<T, INV>(v);
+    else dft8<T, INV>(v);
+}
+
+// Compile-time plan of one pass: R = 2^LOGR points split into in-CTA stages
+// of radix 2^FIRST then 8, 8, ...; EC entries per CTA; NT threads, each
+// holding EPT points in registers.
+template <class T, int LOGR, int EC>
+struct FftPlan {
+    static constexpr int R = 1 << LOGR;
+    static constexpr int FIRST = (LOGR < 3) ? LOGR : ((LOGR % 3) == 0 ? 3 : (LOGR % 3));
+    static constexpr int NSTAGE = (LOGR < 3) ? 1 : 1 + (LOGR - FIRST) / 3;
+    static constexpr int LRMAX = (LOGR < 3) ? LOGR : 3;
+    static constexpr int UNITS = (R >> LRMAX) * EC;        // butterflies in a max-radix stage
+    static constexpr int UB = UNITS > 512 ? UNITS / 512 : 1;
+    static constexpr int NT = UNITS / UB;
+    static constexpr int EPT = UB << LRMAX;               // points per thread
+    static constexpr int LEC = EC == 1 ? 0 : EC == 2 ? 1 : EC == 4 ? 2 : EC == 8 ? 3 : 4;
+};
+
+template <class T, int LOGR, int EC, int S, bool INV>
+__device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<T> *stw, const cx<T> *spt,
+                                          int64_t j, int e0, int ecount, int64_t base_out)
+{
+    using P = FftPlan<T, LOGR, EC>;
+    constexpr int R = P::R, NT = P::NT;
+    constexpr int LR = (S == 0) ? P::FIRST : 3;
+    constexpr int r = 1 << LR;
+    constexpr int LNS = (S == 0) ? 0 : P::FIRST + 3 * (S - 1);
+    constexpr int Ns = 1 << LNS;
+    constexpr int UPT = P::EPT / r;
+    constexpr bool FIRST = (S == 0), LAST = (S == P::NSTAGE - 1);
+    const int tid = threadIdx.x;
+    cx<T> v[UPT][r];
+#pragma unroll
+    for (int u = 0; u < UPT; ++u) {
+        const int unit = tid + u * NT;
+        const int e = unit & (EC - 1), b = unit >> P::LEC;
+#pragma unroll
+        for (int q = 0; q < r; ++q) {
+            const int rho = b + q * (R / r);
+            if constexpr (FIRST) {
+                cx<T> x = c_zero<T>();
+                if (e < ecount) {
+                    x = fft_load<T>(a, j + (int64_t)rho * (a.M >> LOGR), e0 + e);
+                    if (a.Ns > 1) x = c_mul(x, spt[rho]);
+                }
+                v[u][q] = x;
+            } else {
+                v[u][q] = sm[rho * EC + e];
+            }
+        }
+    }
+    if constexpr (!FIRST) __syncthreads();
+#pragma unroll
+    for (int u = 0; u < UPT; ++u) {
+        const int b = (tid + u * NT) >> P::LEC;
+        if constexpr (Ns > 1) {
+            const int bm = b & (Ns - 1);
+#pragma unroll
+            for (int q = 1; q < r; ++q) v[u][q] = c_mul(v[u][q], stw[(bm * q) << (LOGR - LNS - LR)]);
+        }
+        dft_r<T, INV, LR>(v[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < UPT; ++u) {
+        const int unit = tid + u * NT;
+        const int e = unit & (EC - 1), b = unit >> P::LEC;
+        const int ob = ((b >> LNS) << (LNS + LR)) + (b & (Ns - 1));
+#pragma unroll
+        for (int q = 0; q < r; ++q) {
+            const int o = ob + q * Ns;
+            if constexpr (LAST) {
+                if (e < ecount) fft_store<T>(a, base_out + (int64_t)o * a.Ns, e0 + e, v[u][q]);
+            } else {
+                sm[o * EC + e] = v[u][q];
+            }
+        }
+    }
+    if constexpr (!LAST) __syncthreads();
+}
+
+template <class T, int LOGR, int EC, bool INV>
+__device__ __forceinline__ void fft_pass_body(const FftArgs &a)
+{
+    using P = FftPlan<T, LOGR, EC>;
+    constexpr int R = P::R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int logR = a.logR;
-    const int R = 1 << logR;
-    const int ec = a.ec;
-    cx<T> *s = reinterpret_cast<cx<T> *>(smem_raw);  // [R][ec]
-    cx<T> *stw = s + (size_t)R * ec;                  // [R/2]  W_R^t
-    cx<T> *spt = stw + (R >> 1);                      // [R]    inter-pass twiddle
+    cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);  // [R][EC]
+    cx<T> *stw = sm + R * EC;                         // [R]  W_R^t
+    cx<T> *spt = stw + R;                             // [R]  inter-pass twiddles
     const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x;
     const int64_t j = blockIdx.x;
-    const int e0 = blockIdx.y * ec;
-    const int ecount = min(ec, a.E - e0);
+    const int e0 = blockIdx.y * EC;
+    const int ecount = min(EC, a.E - e0);
     const int64_t jm = j & (a.Ns - 1);
-    const bool inv = a.dir > 0;
-
-    for (int t = tid; t < (R >> 1); t += nt) {
-        cx<T> w = tw[(int64_t)t << (a.tw_log - logR)];
-        stw[t] = inv ? c_conj(w) : w;
-    }
-    const bool has_pt = a.Ns > 1;
-    if (has_pt) {
-        // W_{Ns R}^{jm r} = table[(jm r) << (tw_log - log2(Ns R))]
-        const int sh = a.tw_log - (a.logNs + logR);
-        for (int r = tid; r < R; r += nt) {
-            cx<T> w = tw[(jm * r) << sh];
-            spt[r] = inv ? c_conj(w) : w;
+    if constexpr (P::NSTAGE > 1)
+        for (int t = tid; t < R; t += P::NT) {
+            cx<T> w = tw[(int64_t)t << (a.tw_log - LOGR)];
+            stw[t] = INV ? c_conj(w) : w;
+        }
+    if (a.Ns > 1) {
+        const int sh = a.tw_log - (a.logNs + LOGR);
+        for (int t = tid; t < R; t += P::NT) {
+            cx<T> w = tw[(jm * t) << sh];
+            spt[t] = INV ? c_conj(w) : w;
         }
     }
     __syncthreads();
+    const int64_t base_out = (j >> a.logNs << (a.logNs + LOGR)) + jm;
+    fft_stage<T, LOGR, EC, 0, INV>(a, sm, stw, spt, j, e0, ecount, base_out);
+    if constexpr (P::NSTAGE > 1) fft_stage<T, LOGR, EC, 1, INV>(a, sm, stw, spt, j, e0, ecount, base_out);
+    if constexpr (P::NSTAGE > 2) fft_stage<T, LOGR, EC, 2, INV>(a, sm, stw, spt, j, e0, ecount, base_out);
+    if constexpr (P::NSTAGE > 3) fft_stage<T, LOGR, EC, 3, INV>(a, sm, stw, spt, j, e0, ecount, base_out);
+}
 
-    const int64_t stride_in = a.M >> logR;
-    for (int idx = tid; idx < R * ec; idx += nt) {
-        int r = idx / ec, e = idx - r * ec;
-        cx<T> v = c_zero<T>();
-        if (e < ecount) {
-            v = fft_load<T>(a, j + (int64_t)r * stride_in, e0 + e);
-            if (has_pt) v = c_mul(v, spt[r]);
-        }
-        int rb = logR ? (int)(__brev((unsigned)r) >> (32 - logR)) : 0;
-        s[rb * ec + e] = v;
-    }
-    __syncthreads();
-
-    for (int lh = 0; lh < logR; ++lh) {
-        const int h = 1 << lh;
-        const int tsh = logR - 1 - lh;  // W_{2h}^pos = W_R^{pos * R/(2h)}
-        for (int idx = tid; idx < (R >> 1) * ec; idx += nt) {
-            int b = idx / ec, e = idx - b * ec;
-            int pos = b & (h - 1);
-            int i0 = ((b >> lh) << (lh + 1)) + pos;
-            int i1 = i0 + h;
-            cx<T> w = stw[pos << tsh];
-            cx<T> x0 = s[i0 * ec + e];
-            cx<T> x1 = c_mul(s[i1 * ec + e], w);
-            s[i0 * ec + e] = c_add(x0, x1);
-            s[i1 * ec + e] = c_sub(x0, x1);
-        }
-        __syncthreads();
-    }
-
-    const int64_t base = (j >> a.logNs << (a.logNs + logR)) + jm;
-    for (int idx = tid; idx < R * ec; idx += nt) {
-        int f = idx / ec, e = idx - f * ec;
-        if (e < ecount) fft_store<T>(a, base + (int64_t)f * a.Ns, e0 + e, s[f * ec + e]);
-    }
+// One Stockham pass of radix R = 2^LOGR over EC entries per CTA.
+template <class T, int LOGR, int EC>
+__global__ void __launch_bounds__(FftPlan<T, LOGR, EC>::NT) fft_pass_kernel(FftArgs a)
+{
+    if (a.dir > 0) fft_pass_body<T, LOGR, EC, true>(a);
+    else fft_pass_body<T, LOGR, EC, false>(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -296,4 +417,22 @@ __global__ void twiddle_kernel(cx<T> *tw, int log)
         sincospi(-2.0 * (double)t / (double)n, &s, &c);
         tw[t] = c_from_d<T>(c, s);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Launch table of the FFT pass instantiations: entry [ec_index][logR], where
+// ec_index 0 is the default entries per CTA (16 for 8-byte complex, 8 for
+// 16-byte) and 1 is 4 entries per CTA.
+using FftKernel = void (*)(FftArgs);
+struct FftEntry {
+    FftKernel fn;
+    int nt;
+};
+
+template <class T, int OFF, int... L>
+void fft_fill_shifted(FftEntry (*t)[11], std::integer_sequence<int, L...>)
+{
+    constexpr int ECD = sizeof(cx<T>) == 8 ? 16 : 8;
+    ((t[0][OFF + L] = FftEntry{fft_pass_kernel<T, OFF + L, ECD>, FftPlan<T, OFF + L, ECD>::NT}), ...);
+    ((t[1][OFF + L] = FftEntry{fft_pass_kernel<T, OFF + L, 4>, FftPlan<T, OFF + L, 4>::NT}), ...);
 }

@@ -2,7 +2,14 @@
 // k_<prec>.cu includes this file once with MRC_T / MRC_SUF defined.
 #pragma once
 #include <algorithm>
+#include <utility>
 #include "kernels.cuh"
+
+// table[ec_index][logR] (ec_index 0: default entries per CTA, 1: 4), filled by
+// the two FFT translation units of this precision (low and high radices);
+// specialised once per precision by MRC_DEFINE_PREC.
+template <class T>
+const FftEntry (&fft_table())[2][11];
 
 namespace {
 
@@ -22,17 +29,25 @@ template <class T> constexpr int kclass_pair() { return kclass_fft<T>() + 3; }
 template <class T>
 constexpr int default_ec() { return sizeof(cx<T>) == 8 ? 16 : 8; }
 
+// entries per CTA: the full default when E allows, else 4 (>= 32-byte row
+// segments; lanes beyond E idle)
+template <class T>
+int pick_ec(int E) { return E >= default_ec<T>() ? default_ec<T>() : 4; }
+
 template <class T>
 size_t fft_smem_bytes(int logR, int ec)
 {
     const size_t R = (size_t)1 << logR;
-    return (R * ec + (R >> 1) + R) * sizeof(cx<T>);
+    return (R * ec + 2 * R) * sizeof(cx<T>);
 }
 
-// Radix plan: one pass up to 2^9, else two passes of sizes 2^ceil(l/2), 2^floor(l/2).
+template <class T>
+int ec_index(int ec) { return ec == default_ec<T>() ? 0 : 1; }
+
+// Radix plan: one pass up to 2^10, else two passes of sizes 2^ceil(l/2), 2^floor(l/2).
 inline int fft_plan(int logM, int *logRs)
 {
-    if (logM <= 9) { logRs[0] = logM; return 1; }
+    if (logM <= 10) { logRs[0] = logM; return 1; }
     logRs[0] = (logM + 1) / 2;
     logRs[1] = logM / 2;
     return 2;
@@ -46,8 +61,7 @@ cudaError_t fft_run(const FftSrc &src, const FftDst &dst, int64_t M, int E, int 
     if (((int64_t)1 << logM) != M || logM > 20 || logM + 1 > tw_log) return cudaErrorInvalidValue;
     int logRs[2];
     const int np = fft_plan(logM, logRs);
-    int ec = default_ec<T>();
-    if (ec > E) ec = E;
+    const int ec = pick_ec<T>(E);
     int logNs = 0;
     for (int ps = 0; ps < np; ++ps) {
         FftArgs a{};
@@ -81,8 +95,9 @@ cudaError_t fft_run(const FftSrc &src, const FftDst &dst, int64_t M, int E, int 
         else rd = (double)std::min<int64_t>(a.src_nvalid, M) * E * sizeof(cx<T>);
         if (a.dst_mode == DST_CPLX) wr = (double)M * E * sizeof(cx<T>);
         else wr = (double)(a.dst_hi - a.dst_lo) * E * 8.0 * (a.dst_mode == DST_REAL64_ADD ? 2.0 : 1.0);
+        const FftEntry &k = fft_table<T>()[ec_index<T>(ec)][a.logR];
         mrc_prof_pre(kclass_fft<T>(), st);
-        fft_pass_kernel<T><<<grid, 256, fft_smem_bytes<T>(a.logR, ec), st>>>(a);
+        k.fn<<<grid, k.nt, fft_smem_bytes<T>(a.logR, ec), st>>>(a);
         mrc_prof_post(kclass_fft<T>(), st, rd + wr, 5.0 * (double)M * a.logR * E);
         logNs += a.logR;
     }
@@ -146,12 +161,32 @@ cudaError_t twiddles_run(void *tw, int tw_log, cudaStream_t st)
 template <class T>
 cudaError_t init_run()
 {
-    return cudaFuncSetAttribute(fft_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    const auto &t = fft_table<T>();
+    for (int i = 0; i < 2; ++i)
+        for (int l = 0; l < 11; ++l) {
+            cudaError_t e = cudaFuncSetAttribute(t[i][l].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
 }
 
 } // namespace
 
 #define MRC_DEFINE_PREC(T, SUF)                                                                             \
+    void mrc_fft_fill_##SUF##_lo(FftEntry (*t)[11]);                                                        \
+    void mrc_fft_fill_##SUF##_hi(FftEntry (*t)[11]);                                                        \
+    template <>                                                                                             \
+    const FftEntry (&fft_table<T>())[2][11]                                                                 \
+    {                                                                                                       \
+        static FftEntry t[2][11];                                                                           \
+        static bool init = false;                                                                           \
+        if (!init) {                                                                                        \
+            mrc_fft_fill_##SUF##_lo(t);                                                                     \
+            mrc_fft_fill_##SUF##_hi(t);                                                                     \
+            init = true;                                                                                    \
+        }                                                                                                   \
+        return t;                                                                                           \
+    }                                                                                                       \
     cudaError_t mrc_fft_##SUF(const FftSrc &src, const FftDst &dst, int64_t M, int E, int dir, void *scratch, \
                               const void *tw, int tw_log, cudaStream_t st)                                  \
     {                                                                                                       \
