@@ -43,6 +43,9 @@ WORKLOADS = {
     "weibull_d4_N1024": (4, 1024, "weibull", {}),
     "lognormal_d64_N65536": (64, 1 << 16, "lognormal", {}),
     "weibull_d256_N32768": (256, 1 << 15, "weibull", {"alpha": 0.5, "shape": (0.5, 3.0)}),
+    # 256 independent models, d ~ U{3..48}, N = round(2^U[10,16]), half discrete Weibull,
+    # half Lognormal mean-value (h = 0.05), one captured batch
+    "batch256": (0, 0, "batch", {"n": 256}),
 }
 DEFAULT_WORKLOAD = "lognormal_d64_N262144"
 
@@ -147,6 +150,8 @@ class ClockSampler:
 def make_input(name):
     from paper_2605_30379_gb300 import synth
     d, N, kind, extra = WORKLOADS[name]
+    if kind == "batch":
+        return [m["A"] for m in synth.batch_models(n=extra["n"], seed=0)]
     if kind == "lognormal":
         A, _ = synth.lognormal_model(d, N, seed=0, h=0.05)
     else:
@@ -181,7 +186,10 @@ def run_reference(args, rank, world):
     d, N, kind, _ = WORKLOADS[name]
     from paper_2605_30379_gb300 import synth
     # prefix of the same seeded workload (the generator is prefix-consistent)
-    if kind == "lognormal":
+    if kind == "batch":
+        A = synth.batch_models(n=1, seed=0)[0]["A"]
+        d, N = A.shape[1], A.shape[0]
+    elif kind == "lognormal":
         A, _ = synth.lognormal_model(d, min(N, 8192), seed=0, h=0.05)
     else:
         q, _ = synth.weibull_model(d, min(N, 8192), seed=0, **WORKLOADS[name][3])
@@ -250,12 +258,16 @@ def main():
         return float(t.item())
 
     d, N, kind, _ = WORKLOADS[args.workload]
-    coeffs = N * d * d
-    A_host_np = make_input(args.workload)
-    A_pin = torch.from_numpy(A_host_np).pin_memory()
-    A = A_pin.to("cuda", non_blocking=False)
-    psi = torch.empty_like(A)
-    psi_pin = torch.empty(A.shape, dtype=torch.float64).pin_memory()
+    hosts = make_input(args.workload)
+    batch = kind == "batch"
+    if not batch:
+        hosts = [hosts]
+    coeffs = sum(a.shape[0] * a.shape[1] * a.shape[2] for a in hosts)
+    A_pins = [torch.from_numpy(a).pin_memory() for a in hosts]
+    As = [p.to("cuda", non_blocking=False) for p in A_pins]
+    psis = [torch.empty_like(a) for a in As]
+    psi_pins = [torch.empty(a.shape, dtype=torch.float64).pin_memory() for a in As]
+    A_host_np = hosts[0]
     lib = mrc.load()
     import ctypes
     lib.mrc_launch_count.restype = ctypes.c_ulonglong
@@ -265,7 +277,10 @@ def main():
     stream = torch.cuda.current_stream()
 
     def step(prec=args.prec):
-        mrc.inverse(A, prec=prec, sweeps=1, out=psi)
+        if batch:
+            mrc.inverse_batched(As, prec=prec, sweeps=1, outs=psis)
+        else:
+            mrc.inverse(As[0], prec=prec, sweeps=1, out=psis[0])
 
     def prof(kclass, fn):
         lib.mrc_profile_begin(kclass)
@@ -274,13 +289,17 @@ def main():
         lib.mrc_profile_end(ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b), ctypes.byref(f))
         return ms.value, n.value, b.value, f.value
 
-    for _ in range(max(args.warmup, 3)):
+    lw = lib.mrc_launch_count()
+    step()  # first warm-up step (captures the batch graph)
+    torch.cuda.synchronize()
+    launches_per_step = lib.mrc_launch_count() - lw
+    for _ in range(max(args.warmup, 3) - 1):
         step()
     torch.cuda.synchronize()
 
     # per-class device time of one step (untimed), to pick the dominant kernel
     breakdown = {}
-    for kc in ([] if args.no_breakdown else KCLASS):
+    for kc in ([] if (args.no_breakdown or batch) else KCLASS):
         ms, n, b, f = prof(kc, step)
         if n:
             breakdown[KCLASS[kc]] = {"ms": ms, "launches": n}
@@ -301,6 +320,8 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     launches = lib.mrc_launch_count() - l0
+    if batch:  # graph replays: the kernels were counted once, at capture
+        launches = launches_per_step * args.steps
     pms, pn, pb, pf = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
     lib.mrc_profile_end(ctypes.byref(pms), ctypes.byref(pn), ctypes.byref(pb), ctypes.byref(pf))
     barrier()
@@ -324,8 +345,11 @@ def main():
         step()  # leave the mixed result in psi for the accuracy check
         torch.cuda.synchronize()
 
-    # ---- accuracy of the timed path: double-float residual of psi
-    _, _, rep = mrc.residual(A, psi, sides=3, prec="mixed", want_rho=False)
+    # ---- accuracy of the timed path: double-float residual of psi (worst model)
+    rep = {"res_max_abs": 0.0, "res_left_l1": 0.0, "res_right_l1": 0.0}
+    for a, p_ in zip(As, psis):
+        _, _, r = mrc.residual(a, p_, sides=3, prec="mixed", want_rho=False)
+        rep = {k: max(rep[k], r[k]) for k in rep}
 
     # ---- e2e through the public API with host buffers
     ms_e2e = None
@@ -334,9 +358,11 @@ def main():
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(args.steps):
-            A.copy_(A_pin, non_blocking=True)
+            for a, p_ in zip(As, A_pins):
+                a.copy_(p_, non_blocking=True)
             step()
-            psi_pin.copy_(psi, non_blocking=True)
+            for p_, q_ in zip(psi_pins, psis):
+                p_.copy_(q_, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
         ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps)
@@ -349,8 +375,9 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n, dt, cores = cpu_oracle_sample(A_host_np, d)
-        cpu = {"value": n * d * d / dt, "unit": "coefficients/s", "cores": cores, "kind": "oracle",
+        dc = A_host_np.shape[1]
+        n, dt, cores = cpu_oracle_sample(A_host_np, dc)
+        cpu = {"value": n * dc * dc / dt, "unit": "coefficients/s", "cores": cores, "kind": "oracle",
                "sample": f"one call on the prefix k < {n} of the same workload, {dt:.1f} s "
                          f"(direct recursion, cost d^3 n^2 / 2: its rate falls as 1/n)"}
 
@@ -360,9 +387,10 @@ def main():
             "value": value, "unit": "coefficients/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+dd" if args.prec == "mixed" else "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "d": d, "N": N, "prec": args.prec, "sweeps": 1,
-                       "l2": "inputs (8.6 GB) larger than L2; no flush" if coeffs * 8 > 2e8 else
-                             "inputs smaller than L2: latency-bound, no flush",
+            "config": {"workload": args.workload, "d": d if not batch else "3..48",
+                       "N": N if not batch else "round(2^U[10,16])", "models": len(As), "prec": args.prec, "sweeps": 1,
+                       "l2": (f"inputs ({coeffs * 8 / 1e9:.1f} GB) larger than L2; no flush" if coeffs * 8 > 2e8
+                              else "inputs smaller than L2: latency-bound, no flush"),
                        "parallelism": "replicas" if world > 1 else "single"},
             "accuracy": {"max_abs_rho_L": rep["res_max_abs"], "rho_L_l1": rep["res_left_l1"],
                          "rho_R_l1": rep["res_right_l1"]},

@@ -115,8 +115,18 @@ mrc_status mrc_inverse(mrc_ctx *ctx, int d, int64_t N, const double *A, double *
 /*
  * mrc_inverse_batched -- mrc_inverse over `nmodels` independent models with
  * their own d[b] and N[b] (host arrays), A[b]/psi[b] device pointers held in
- * HOST arrays of pointers.  All models are enqueued on `stream` in order.
- * report (nullable, host) receives one mrc_report per model.
+ * HOST arrays of pointers (no counterpart in the paper beyond applying
+ * Eq. (newton) to each model).
+ * Scheduling: models are placed longest-first on the least-loaded of up to 8
+ * internal streams (cost ~ N d^2 (log2 N + d)), each stream with its own slice
+ * of the workspace, and the whole batch is captured once into a CUDA graph.
+ * A later call with the same (d, N, A, psi, prec, sweeps) lists replays the
+ * graph with one launch on `stream`; the context keeps the 8 most recent
+ * graphs, and a workspace reallocation discards them.  The launch-count
+ * counter counts kernels at capture time only.
+ * report (nullable, host) receives one mrc_report per model (ms = the whole
+ * batch); with a report the call synchronises and returns the first nonzero
+ * per-model status (e.g. MRC_ERR_SINGULAR_A0).
  */
 mrc_status mrc_inverse_batched(mrc_ctx *ctx, int nmodels, const int *d, const int64_t *N,
                                const double *const *A, double *const *psi,

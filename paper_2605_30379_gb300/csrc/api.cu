@@ -16,6 +16,19 @@
 
 #define MRC_TW_LOG 21  // twiddle tables cover transform lengths up to 2^21
 
+// One captured batch: the CUDA graph of every model's kernels on the
+// context's internal streams, replayed while the configuration is unchanged.
+struct BatchGraph {
+    std::vector<int> d;
+    std::vector<int64_t> N;
+    std::vector<const double *> A;
+    std::vector<double *> psi;
+    int prec = 0, sweeps = 0;
+    cudaGraphExec_t exec = nullptr;
+};
+
+#define MRC_BATCH_STREAMS 8
+
 struct mrc_ctx {
     int device = 0;
     size_t cap = 0;        // 0 = unlimited
@@ -25,7 +38,13 @@ struct mrc_ctx {
     int *d_status = nullptr;
     double *d_acc = nullptr;  // [4] norm accumulators
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // batching
+    cudaStream_t bst[MRC_BATCH_STREAMS] = {};
+    cudaEvent_t bev[MRC_BATCH_STREAMS] = {};
+    std::vector<BatchGraph> graphs;  // most recent last
 };
+
+void mrc_prof_set_capturing(bool on);
 
 namespace {
 
@@ -88,6 +107,8 @@ mrc_status ensure_ws(mrc_ctx *c, size_t need)
 {
     if (need <= c->ws_size) return MRC_OK;
     if (c->cap && need > c->cap) return MRC_ERR_NO_MEMORY;
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);  // graphs hold workspace addresses
+    c->graphs.clear();
     if (c->ws) {
         cudaDeviceSynchronize();
         cudaFree(c->ws);
@@ -220,11 +241,11 @@ mrc_status newton_levels(mrc_ctx *c, Arena &ar, int prec, int d, int64_t N, cons
 bool valid_dN(int d, int64_t N) { return d >= 1 && d <= 512 && N >= 1 && N <= ((int64_t)1 << 20); }
 
 mrc_status inverse_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A, double *psi, int prec, int sweeps,
-                        int *levels, cudaStream_t st)
+                        int *levels, cudaStream_t st, int *status = nullptr)
 {
     const size_t E = (size_t)d * d;
     double *gjw = (double *)ar.take(sizeof(double) * 2 * E);
-    CK(mrc_gauss_jordan(A, psi, gjw, d, c->d_status, st));
+    CK(mrc_gauss_jordan(A, psi, gjw, d, status ? status : c->d_status, st));
     const int64_t m0 = base_size(d, N);
     CK(mrc_base_case(A, psi, d, m0, st));
     const size_t mark = ar.off;
@@ -357,6 +378,11 @@ mrc_status mrc_destroy(mrc_ctx *c)
     cudaFree(c->d_acc);
     cudaEventDestroy(c->ev0);
     cudaEventDestroy(c->ev1);
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
+    for (int k = 0; k < MRC_BATCH_STREAMS; ++k) {
+        if (c->bst[k]) cudaStreamDestroy(c->bst[k]);
+        if (c->bev[k]) cudaEventDestroy(c->bev[k]);
+    }
     delete c;
     return MRC_OK;
 }
@@ -423,17 +449,124 @@ mrc_status mrc_inverse_batched(mrc_ctx *c, int nmodels, const int *d, const int6
     if (!c || nmodels < 0 || (nmodels > 0 && (!d || !N || !A || !psi))) return MRC_ERR_INVALID_ARG;
     for (int b = 0; b < nmodels; ++b)
         if (!valid_dN(d[b], N[b]) || !A[b] || !psi[b]) return MRC_ERR_INVALID_ARG;
+    if (nmodels == 0) return MRC_OK;
     const int prec = opt ? opt->prec : MRC_FP64;
-    size_t need = 0;
-    for (int b = 0; b < nmodels; ++b) need = std::max(need, ws_inverse(d[b], N[b], prec));
-    mrc_status s;
+    if (prec != MRC_FP64 && prec != MRC_MIXED) return MRC_ERR_INVALID_ARG;
+    int sweeps = opt ? opt->refine_sweeps : 1;
+    if (prec == MRC_MIXED && sweeps <= 0) sweeps = 1;
+    if (prec == MRC_FP64) sweeps = 0;
+    if (sweeps > 4) return MRC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
     cudaSetDevice(c->device);
-    if ((s = ensure_ws(c, need)) != MRC_OK) return s;
-    for (int b = 0; b < nmodels; ++b) {
-        s = mrc_inverse(c, d[b], N[b], A[b], psi[b], opt, stream, report ? report + b : nullptr);
-        if (s != MRC_OK) return s;
+    mrc_status s;
+    if ((s = ensure_tw(c, prec == MRC_FP64 ? PREC_F64 : PREC_F32, st)) != MRC_OK) return s;
+    if (prec == MRC_MIXED && (s = ensure_tw(c, PREC_DD, st)) != MRC_OK) return s;
+
+    // Longest-first onto the least-loaded of up to MRC_BATCH_STREAMS streams;
+    // cost model ~ N d^2 (log2 N + d), the FFT and product terms of Prop 2.4.
+    const int S = std::min(nmodels, MRC_BATCH_STREAMS);
+    std::vector<int> order(nmodels), assign(nmodels);
+    for (int b = 0; b < nmodels; ++b) order[b] = b;
+    auto cost = [&](int b) {
+        double lg = 1.0;
+        for (int64_t x = 1; x < N[b]; x <<= 1) lg += 1.0;
+        return (double)N[b] * d[b] * d[b] * (lg + d[b]);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    std::vector<double> load(S, 0.0);
+    std::vector<size_t> wsz(S, 0);
+    for (int b : order) {
+        int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        assign[b] = k;
+        load[k] += cost(b);
+        wsz[k] = std::max(wsz[k], ws_inverse(d[b], N[b], prec));
     }
-    return MRC_OK;
+    std::vector<size_t> woff(S, 0);
+    size_t total = align_up(sizeof(int) * nmodels);
+    for (int k = 0; k < S; ++k) {
+        woff[k] = total;
+        total += align_up(wsz[k]);
+    }
+    if ((s = ensure_ws(c, total)) != MRC_OK) return s;
+    int *status = (int *)c->ws;
+
+    BatchGraph *hit = nullptr;
+    for (auto &g : c->graphs) {
+        if (g.prec != prec || g.sweeps != sweeps || (int)g.d.size() != nmodels) continue;
+        bool same = true;
+        for (int b = 0; b < nmodels && same; ++b)
+            same = g.d[b] == d[b] && g.N[b] == N[b] && g.A[b] == A[b] && g.psi[b] == psi[b];
+        if (same) { hit = &g; break; }
+    }
+    if (!hit) {
+        for (int k = 0; k < MRC_BATCH_STREAMS; ++k) {
+            if (!c->bst[k]) CK(cudaStreamCreateWithFlags(&c->bst[k], cudaStreamNonBlocking));
+            if (!c->bev[k]) CK(cudaEventCreateWithFlags(&c->bev[k], cudaEventDisableTiming));
+        }
+        cudaStream_t s0 = c->bst[0];
+        CK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+        mrc_prof_set_capturing(true);
+        mrc_status cs = MRC_OK;
+        cudaError_t ce = cudaMemsetAsync(status, 0, sizeof(int) * nmodels, s0);
+        if (ce == cudaSuccess) ce = cudaEventRecord(c->bev[0], s0);
+        for (int k = 1; k < S && ce == cudaSuccess; ++k) ce = cudaStreamWaitEvent(c->bst[k], c->bev[0], 0);
+        if (ce != cudaSuccess) cs = MRC_ERR_CUDA;
+        for (int b = 0; b < nmodels && cs == MRC_OK; ++b) {
+            Arena ar{(char *)c->ws + woff[assign[b]]};
+            cs = inverse_impl(c, ar, d[b], N[b], A[b], psi[b], prec, sweeps, nullptr, c->bst[assign[b]], status + b);
+        }
+        for (int k = 1; k < S && cs == MRC_OK; ++k) {
+            if (cudaEventRecord(c->bev[k], c->bst[k]) != cudaSuccess ||
+                cudaStreamWaitEvent(s0, c->bev[k], 0) != cudaSuccess)
+                cs = MRC_ERR_CUDA;
+        }
+        mrc_prof_set_capturing(false);
+        cudaGraph_t graph = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(s0, &graph);
+        if (cs != MRC_OK || ee != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return cs != MRC_OK ? cs : MRC_ERR_CUDA;
+        }
+        BatchGraph g;
+        g.d.assign(d, d + nmodels);
+        g.N.assign(N, N + nmodels);
+        g.A.assign(A, A + nmodels);
+        g.psi.assign(psi, psi + nmodels);
+        g.prec = prec;
+        g.sweeps = sweeps;
+        ce = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return MRC_ERR_CUDA;
+        if (c->graphs.size() >= 8) {
+            cudaGraphExecDestroy(c->graphs.front().exec);
+            c->graphs.erase(c->graphs.begin());
+        }
+        c->graphs.push_back(std::move(g));
+        hit = &c->graphs.back();
+    }
+    if (report) CK(cudaEventRecord(c->ev0, st));
+    CK(cudaGraphLaunch(hit->exec, st));
+    if (!report) return MRC_OK;
+    CK(cudaEventRecord(c->ev1, st));
+    CK(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    std::vector<int> hs(nmodels, 0);
+    CK(cudaMemcpy(hs.data(), status, sizeof(int) * nmodels, cudaMemcpyDeviceToHost));
+    mrc_status first = MRC_OK;
+    for (int b = 0; b < nmodels; ++b) {
+        mrc_report &r = report[b];
+        memset(&r, 0, sizeof(r));
+        r.res_left_l1 = r.res_right_l1 = r.res_max_abs = -1.0;
+        int lv = 0;
+        for (int64_t m = base_size(d[b], N[b]); m < N[b]; m <<= 1) ++lv;
+        r.levels = lv;
+        r.sweeps = sweeps;
+        r.ms = ms;
+        if (hs[b] && first == MRC_OK) first = (mrc_status)hs[b];
+    }
+    return first;
 }
 
 mrc_status mrc_residual(mrc_ctx *c, int d, int64_t N, const double *A, const double *psi, int sides, double *rho_left,

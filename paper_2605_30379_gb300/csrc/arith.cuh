@@ -71,14 +71,65 @@ __device__ __forceinline__ dd dd_fma(dd a, dd b, dd c)
     return dd_fast_two_sum(s.hi, t);
 }
 
-__device__ __forceinline__ dd dd_from_double(double x)
+// ---------------------------------------------------------------------------
+// Conversions between binary64 and the FP32-based formats done with integer
+// operations on the two 32-bit halves, so they stay off the (narrow) FP64
+// pipe.  Magnitudes below 2^-126 are flushed to a signed zero: every use here
+// compares absolute errors far above that.
+
+// binary64 -> nearest binary32 (ties to even); exponents outside the normal
+// binary32 range go through the hardware conversion.
+__device__ __forceinline__ float f64_to_f32_rn(double x)
 {
-    float hi = __double2float_rn(x);
-    float lo = __double2float_rn(x - (double)hi);
-    return {hi, lo};
+    const long long b = __double_as_longlong(x);
+    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+    const int ex = (int)((hw >> 20) & 0x7ffu);
+    if (ex < 897 || ex > 1150) return ex < 897 ? __int_as_float((int)(hw & 0x80000000u)) : __double2float_rn(x);
+    const unsigned m23 = ((hw & 0xfffffu) << 3) | (lw >> 29);
+    const unsigned rem = lw & 0x1fffffffu;
+    const unsigned up = (rem > 0x10000000u) | ((rem == 0x10000000u) & m23);
+    const unsigned fb = (hw & 0x80000000u) | ((((unsigned)(ex - 896)) << 23) + m23 + (up & 1u));
+    return __uint_as_float(fb);
 }
 
-__device__ __forceinline__ double dd_to_double(dd x) { return (double)x.hi + (double)x.lo; }
+// binary64 -> double-float (hi = nearest binary32, lo = the rest rounded to binary32)
+__device__ __forceinline__ dd dd_from_double(double x)
+{
+    const long long b = __double_as_longlong(x);
+    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+    const int ex = (int)((hw >> 20) & 0x7ffu);
+    if (ex < 897 || ex > 1150) {
+        if (ex < 897) return {__int_as_float((int)(hw & 0x80000000u)), 0.0f};
+        float hi = __double2float_rn(x);
+        return {hi, __double2float_rn(x - (double)hi)};
+    }
+    const unsigned m23 = ((hw & 0xfffffu) << 3) | (lw >> 29);
+    const unsigned rem = lw & 0x1fffffffu;
+    const unsigned up = ((rem > 0x10000000u) | ((rem == 0x10000000u) & m23)) & 1u;
+    const unsigned fb = (hw & 0x80000000u) | ((((unsigned)(ex - 896)) << 23) + m23 + up);
+    // x - hi = (rem - up 2^29) 2^(ex - 1075), sign of x
+    float lo = 0.0f;
+    if (ex >= 949) {
+        const int r = (int)rem - (int)(up << 29);
+        lo = __int2float_rn(r) * __uint_as_float(((unsigned)(ex - 948)) << 23);
+        if (hw & 0x80000000u) lo = -lo;
+    }
+    return {__uint_as_float(fb), lo};
+}
+
+// binary32 -> binary64, exact (binary32 subnormals flush to zero)
+__device__ __forceinline__ double f32_to_f64(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e8 = (u >> 23) & 0xffu;
+    if (e8 == 0u) return __longlong_as_double((long long)(u & 0x80000000u) << 32);
+    if (e8 == 0xffu) return (double)f;
+    const unsigned hw = (u & 0x80000000u) | ((e8 + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+    const unsigned lw = (u & 0x7fffffu) << 29;
+    return __longlong_as_double(((long long)hw << 32) | lw);
+}
+
+__device__ __forceinline__ double dd_to_double(dd x) { return f32_to_f64(x.hi) + f32_to_f64(x.lo); }
 
 // ---------------------------------------------------------------------------
 // Real arithmetic traits.  scal(a, s) multiplies by a host scalar s that is a
@@ -94,6 +145,7 @@ struct Ar<double> {
     static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
     static __device__ __forceinline__ double neg(double a) { return -a; }
     static __device__ __forceinline__ double scal(double a, double s) { return a * s; }
+    static __device__ __forceinline__ double scal_f(double a, float s) { return a * (double)s; }
     static __device__ __forceinline__ double from_d(double x) { return x; }
     static __device__ __forceinline__ double to_d(double x) { return x; }
     static __device__ __forceinline__ double zero() { return 0.0; }
@@ -107,8 +159,9 @@ struct Ar<float> {
     static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
     static __device__ __forceinline__ float neg(float a) { return -a; }
     static __device__ __forceinline__ float scal(float a, double s) { return a * (float)s; }
-    static __device__ __forceinline__ float from_d(double x) { return __double2float_rn(x); }
-    static __device__ __forceinline__ double to_d(float x) { return (double)x; }
+    static __device__ __forceinline__ float scal_f(float a, float s) { return a * s; }
+    static __device__ __forceinline__ float from_d(double x) { return f64_to_f32_rn(x); }
+    static __device__ __forceinline__ double to_d(float x) { return f32_to_f64(x); }
     static __device__ __forceinline__ float zero() { return 0.0f; }
 };
 
@@ -124,6 +177,7 @@ struct Ar<dd> {
         float f = (float)s;
         return {a.hi * f, a.lo * f};
     }
+    static __device__ __forceinline__ dd scal_f(dd a, float f) { return {a.hi * f, a.lo * f}; }
     static __device__ __forceinline__ dd from_d(double x) { return dd_from_double(x); }
     static __device__ __forceinline__ double to_d(dd x) { return dd_to_double(x); }
     static __device__ __forceinline__ dd zero() { return {0.0f, 0.0f}; }

@@ -44,8 +44,16 @@ __device__ __forceinline__ cx<T> fft_load(const FftArgs &a, int64_t k, int e)
     int64_t r0 = 2 * k, r1 = 2 * k + 1;
     double x0 = (r0 < a.src_nvalid) ? s[(a.src_row0 + r0) * (int64_t)a.src_ld + e] : 0.0;
     double x1 = (r1 < a.src_nvalid) ? s[(a.src_row0 + r1) * (int64_t)a.src_ld + e] : 0.0;
-    if (a.src_neg) { x0 = -x0; x1 = -x1; }
-    return c_from_d<T>(x0, x1);
+    cx<T> v = c_from_d<T>(x0, x1);
+    return a.src_neg ? c_neg(v) : v;
+}
+
+// multiply by the (signed power of two) output scale in the working precision
+template <class T>
+__device__ __forceinline__ cx<T> scale_out(const FftArgs &a, cx<T> v)
+{
+    if constexpr (sizeof(T) == 8 && sizeof(cx<T>) == 16 && !__is_same(T, dd)) return c_scal(v, a.dst_scale);
+    else return {Ar<T>::scal_f(v.re, a.dst_scale_f), Ar<T>::scal_f(v.im, a.dst_scale_f)};
 }
 
 template <class T>
@@ -53,18 +61,20 @@ __device__ __forceinline__ void fft_store(const FftArgs &a, int64_t k, int e, cx
 {
     if (a.dst_mode == DST_CPLX) {
         cx<T> *d = reinterpret_cast<cx<T> *>(a.dst);
-        if (a.dst_scale != 1.0) v = c_scal(v, a.dst_scale);
+        if (a.dst_scale != 1.0) v = scale_out(a, v);
         d[k * (int64_t)a.dst_ld + e] = v;
         return;
     }
-    // real rows 2k (re) and 2k+1 (im), window [lo, hi)
+    // real rows 2k (re) and 2k+1 (im), window [lo, hi); the power-of-two
+    // scale is applied in the working precision (exact) before conversion
     double *d = reinterpret_cast<double *>(a.dst);
-    double vals[2] = {Ar<T>::to_d(v.re), Ar<T>::to_d(v.im)};
+    v = scale_out(a, v);
+    const T vals[2] = {v.re, v.im};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         int64_t r = 2 * k + h;
         if (r < a.dst_lo || r >= a.dst_hi) continue;
-        double x = vals[h] * a.dst_scale;
+        double x = Ar<T>::to_d(vals[h]);
         if (a.dst_eye_d > 0 && r == 0 && (e % (a.dst_eye_d + 1)) == 0) x += 1.0;
         double *p = d + (a.dst_row0 + (r - a.dst_lo)) * (int64_t)a.dst_ld + e;
         if (a.dst_mode == DST_REAL64_ADD) *p += x;

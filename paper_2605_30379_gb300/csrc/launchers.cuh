@@ -87,6 +87,7 @@ cudaError_t fft_run(const FftSrc &src, const FftDst &dst, int64_t M, int E, int 
             a.dst_mode = DST_CPLX; a.dst = scratch; a.dst_ld = E; a.dst_lo = 0; a.dst_hi = 0; a.dst_row0 = 0;
             a.dst_scale = 1.0; a.dst_eye_d = 0;
         }
+        a.dst_scale_f = (float)a.dst_scale;
         dim3 grid((unsigned)(M >> a.logR), (unsigned)((E + ec - 1) / ec));
         // algorithmic charge: the valid source rows read once, the kept output written once,
         // 5 M log2(R) real flops per entry (radix-2 convention)

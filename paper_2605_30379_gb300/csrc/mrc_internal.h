@@ -32,6 +32,7 @@ struct FftArgs {
     int64_t dst_lo, dst_hi; // REAL64*: kept window of real rows
     int64_t dst_row0;       // REAL64*: destination row of real row dst_lo
     double dst_scale;       // signed power of two
+    float dst_scale_f;      // the same, for the FP32-based precisions
     int dst_eye_d;          // REAL64*: if > 0 add 1 to the diagonal of real row 0 (d = this)
 };
 

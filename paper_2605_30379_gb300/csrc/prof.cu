@@ -20,19 +20,24 @@ struct Prof {
     size_t used = 0;
     double bytes = 0, flops = 0;
     long long n = 0;
+    bool capturing = false;  // no event records while a stream capture is open
 } g_prof;
 constexpr size_t kPool = 16384;
 } // namespace
 
+void mrc_prof_set_capturing(bool on) { g_prof.capturing = on; }
+
 void mrc_prof_pre(int kclass, cudaStream_t st)
 {
     g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (g_prof.capturing) return;
     if (g_prof.kclass && kclass == g_prof.kclass && g_prof.used + 2 <= g_prof.pool.size())
         cudaEventRecord(g_prof.pool[g_prof.used], st);
 }
 
 void mrc_prof_post(int kclass, cudaStream_t st, double bytes, double flops)
 {
+    if (g_prof.capturing) return;
     if (g_prof.kclass && kclass == g_prof.kclass && g_prof.used + 2 <= g_prof.pool.size()) {
         cudaEventRecord(g_prof.pool[g_prof.used + 1], st);
         g_prof.used += 2;

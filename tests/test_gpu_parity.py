@@ -197,3 +197,33 @@ def test_batched_matches_single(mrc):
     for m, o in zip(models, outs):
         ref = oracle.inverse_left(m["A"])
         assert np.abs(o.cpu().numpy() - ref).max() <= TOL64
+
+
+def test_batched_mixed_and_graph_replay(mrc):
+    """Uneven d and non-power-of-two N in one captured batch; a second call
+    with the same configuration replays the graph and must give the same bits."""
+    models = synth.batch_models(n=10, seed=5, d_range=(3, 20), logN_range=(7.0, 10.5))
+    As = [dev(m["A"]) for m in models]
+    outs, reps = mrc.inverse_batched(As, prec="mixed", report=True)
+    first = [o.clone() for o in outs]
+    for m, o, r in zip(models, outs, reps):
+        ref = oracle.inverse_left(m["A"])
+        assert e_rel(o.cpu().numpy(), ref) <= TOL_REL
+        assert r["sweeps"] == 1 and r["levels"] >= 1
+    outs2 = mrc.inverse_batched(As, prec="mixed", outs=outs)
+    torch.cuda.synchronize()
+    for a, b in zip(first, outs2):
+        assert torch.equal(a, b)
+
+
+def test_batched_reports_singular_model(mrc):
+    q, _ = synth.weibull_model(3, 50, seed=1)
+    good = synth.identity_minus(q)
+    bad = np.zeros((40, 3, 3))
+    bad[0] = [[1, 2, 3], [2, 4, 6], [0, 0, 1.0]]
+    with pytest.raises(mrc.MrcError) as ei:
+        mrc.inverse_batched([dev(good), dev(bad), dev(good)], prec="fp64", report=True)
+    assert ei.value.status == 2
+    outs = mrc.inverse_batched([dev(good), dev(good)], prec="fp64")
+    for o in outs:
+        assert np.abs(o.cpu().numpy() - oracle.inverse_left(good)).max() <= TOL64
