@@ -165,6 +165,14 @@ size_t ws_inverse(int d, int64_t N, int prec)
     return std::max(a, b);
 }
 
+// Double-float square products with 32 <= d <= 64 run on the tensor cores
+// (ozaki.cu) unless MRC_DD_PRODUCT=simt selects the FP32-pipe kernel.
+bool use_tensor_dd()
+{
+    const char *v = getenv("MRC_DD_PRODUCT");
+    return !(v && strcmp(v, "simt") == 0);
+}
+
 // ---------------------------------------------------------------------------
 // C = X * Y truncated to rows [0, N) (linear convolution via L = 2 Mr,
 // Mr = pow2ceil(N)), X: [NX rows][r][m], Y: [NY rows][m][c] real FP64.
@@ -191,6 +199,8 @@ mrc_status conv_product(mrc_ctx *c, Arena &ar, int prec, const double *X, int64_
     CK(op.fft(sx, dx, Mr, (int)EX, -1, bT, tw, MRC_TW_LOG, st));
     CK(op.fft(sy, dy, Mr, (int)EY, -1, bT, tw, MRC_TW_LOG, st));
     if (diag) CK(op.pairdiag(bX, bY, bC, Mr, r, cc, tw, MRC_TW_LOG, st));
+    else if (prec == PREC_DD && use_tensor_dd() && mrc_ozaki_supported(r, m, cc))
+        CK(mrc_pairmul_dd_ozaki(bX, bY, bC, Mr, r, tw, MRC_TW_LOG, st));
     else CK(op.pairmul(bX, bY, bC, Mr, r, m, cc, tw, MRC_TW_LOG, st));
     FftSrc sc{SRC_CPLX, bC, 0, Mr, (int)EC, 0};
     FftDst dc{add ? DST_REAL64_ADD : DST_REAL64, out, (int)EC, 0, N, 0, sign / (double)Mr, eye_d};
@@ -353,6 +363,7 @@ mrc_status mrc_create(mrc_ctx **out, int device, size_t max_workspace_bytes)
     if (cudaSetDevice(device) != cudaSuccess) return MRC_ERR_CUDA;
     for (int p = 0; p < 3; ++p)
         if (OPS[p].init() != cudaSuccess) return MRC_ERR_CUDA;
+    if (mrc_ozaki_init() != cudaSuccess) return MRC_ERR_CUDA;
     mrc_ctx *c = new mrc_ctx();
     c->device = device;
     c->cap = max_workspace_bytes;

@@ -227,3 +227,35 @@ def test_batched_reports_singular_model(mrc):
     outs = mrc.inverse_batched([dev(good), dev(good)], prec="fp64")
     for o in outs:
         assert np.abs(o.cpu().numpy() - oracle.inverse_left(good)).max() <= TOL64
+
+
+@pytest.mark.parametrize("d,N", [(40, 300), (64, 200), (48, 513)])
+def test_tensor_core_dd_residual_matches_oracle(mrc, d, N):
+    """The double-float residual product for 32 <= d <= 64 runs on the BF16
+    tensor cores (exact digit products); it must match the oracle's residual
+    and the FP32-pipe double-float kernel to 1e-12."""
+    import os
+    rng = np.random.default_rng(d)
+    q, _ = synth.weibull_model(d, N, seed=d)
+    A = synth.identity_minus(q)
+    psi = oracle.inverse_left(A) + 1e-6 * rng.standard_normal(A.shape)
+    rl_ref, rr_ref = oracle.residuals(A, psi)
+    rl, rr, _ = mrc.residual(dev(A), dev(psi), sides=3, prec="mixed")
+    assert np.abs(rl.cpu().numpy() - rl_ref).max() <= 1e-12
+    assert np.abs(rr.cpu().numpy() - rr_ref).max() <= 1e-12
+    os.environ["MRC_DD_PRODUCT"] = "simt"
+    try:
+        rl2, _, _ = mrc.residual(dev(A), dev(psi), sides=1, prec="mixed")
+    finally:
+        del os.environ["MRC_DD_PRODUCT"]
+    assert (rl - rl2).abs().max().item() <= 1e-12
+
+
+def test_mixed_inverse_d64_lognormal_prefix(mrc):
+    """d = 64 mean-value Lognormal (the precision workload's shape) at a horizon
+    the oracle finishes quickly: e_rel and the residual bound."""
+    A, _ = synth.lognormal_model(64, 256, seed=0, h=0.05)
+    ref = oracle.inverse_left(A)
+    psi, rep = mrc.inverse(dev(A), prec="mixed", target_residual=1e-10, report=True)
+    assert e_rel(psi.cpu().numpy(), ref) <= TOL_REL
+    assert rep["res_max_abs"] <= TOL_REL
