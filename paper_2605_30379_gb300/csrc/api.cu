@@ -165,12 +165,29 @@ size_t ws_inverse(int d, int64_t N, int prec)
     return std::max(a, b);
 }
 
-// Double-float square products with 32 <= d <= 64 run on the tensor cores
-// (ozaki.cu) unless MRC_DD_PRODUCT=simt selects the FP32-pipe kernel.
-bool use_tensor_dd()
+// Square double-float products with 32 <= d <= 64 run on the tensor cores
+// (ozaki.cu) unless MRC_DD_PRODUCT=simt selects the FP32-pipe kernel;
+// MRC_F32_PRODUCT=tensor moves the FP32 products there too.
+bool env_is_simt(const char *name)
 {
-    const char *v = getenv("MRC_DD_PRODUCT");
-    return !(v && strcmp(v, "simt") == 0);
+    const char *v = getenv(name);
+    return v && strcmp(v, "simt") == 0;
+}
+
+cudaError_t pairmul_any(int prec, const void *zx, const void *zy, void *zc, int64_t M, int r, int m, int c,
+                        const void *tw, cudaStream_t st, bool newton_level = false)
+{
+    if (mrc_ozaki_supported(r, m, c)) {
+        if (prec == PREC_DD && !env_is_simt("MRC_DD_PRODUCT"))
+            return mrc_pairmul_dd_ozaki(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
+        // FP32 products stay on the FP32 pipes unless MRC_F32_PRODUCT=tensor: at
+        // d <= 64 the per-entry digit work outweighs the tensor-core savings
+        // (d = 64, N = 2^18: 118 ms on the tensor cores against 54.5 ms)
+        const char *fv = getenv("MRC_F32_PRODUCT");
+        if (prec == PREC_F32 && fv && strcmp(fv, "tensor") == 0)
+            return mrc_pairmul_f32_ozaki(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
+    }
+    return OPS[prec].pairmul(zx, zy, zc, M, r, m, c, tw, MRC_TW_LOG, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -199,9 +216,7 @@ mrc_status conv_product(mrc_ctx *c, Arena &ar, int prec, const double *X, int64_
     CK(op.fft(sx, dx, Mr, (int)EX, -1, bT, tw, MRC_TW_LOG, st));
     CK(op.fft(sy, dy, Mr, (int)EY, -1, bT, tw, MRC_TW_LOG, st));
     if (diag) CK(op.pairdiag(bX, bY, bC, Mr, r, cc, tw, MRC_TW_LOG, st));
-    else if (prec == PREC_DD && use_tensor_dd() && mrc_ozaki_supported(r, m, cc))
-        CK(mrc_pairmul_dd_ozaki(bX, bY, bC, Mr, r, tw, MRC_TW_LOG, st));
-    else CK(op.pairmul(bX, bY, bC, Mr, r, m, cc, tw, MRC_TW_LOG, st));
+    else CK(pairmul_any(prec, bX, bY, bC, Mr, r, m, cc, tw, st));
     FftSrc sc{SRC_CPLX, bC, 0, Mr, (int)EC, 0};
     FftDst dc{add ? DST_REAL64_ADD : DST_REAL64, out, (int)EC, 0, N, 0, sign / (double)Mr, eye_d};
     CK(op.fft(sc, dc, Mr, (int)EC, +1, bT, tw, MRC_TW_LOG, st));
@@ -232,14 +247,14 @@ mrc_status newton_levels(mrc_ctx *c, Arena &ar, int prec, int d, int64_t N, cons
         FftDst to1{DST_CPLX, b1, E, 0, 0, 0, 1.0, 0};
         CK(op.fft(sA, to0, M, E, -1, bt, tw, MRC_TW_LOG, st));               // A-hat
         CK(op.fft(sB, to1, M, E, -1, bt, tw, MRC_TW_LOG, st));               // B-hat
-        CK(op.pairmul(b0, b1, b2, M, d, d, d, tw, MRC_TW_LOG, st));          // (A B)-hat
+        CK(pairmul_any(prec, b0, b1, b2, M, d, d, d, tw, st, true));        // (A B)-hat
         FftSrc s2{SRC_CPLX, b2, 0, M, E, 0};
         FftDst t0s{DST_CPLX, b0, E, 0, 0, 0, 1.0 / (double)M, 0};
         CK(op.fft(s2, t0s, M, E, +1, bt, tw, MRC_TW_LOG, st));               // A*B, packed time
         FftSrc sR{SRC_CPLX, b0, M / 2, M / 2, E, 1};                          // R = -(A*B)[m, 2m)
         FftDst to2{DST_CPLX, b2, E, 0, 0, 0, 1.0, 0};
         CK(op.fft(sR, to2, M, E, -1, bt, tw, MRC_TW_LOG, st));               // R-hat
-        CK(op.pairmul(b1, b2, b0, M, d, d, d, tw, MRC_TW_LOG, st));          // (B R)-hat
+        CK(pairmul_any(prec, b1, b2, b0, M, d, d, d, tw, st, true));        // (B R)-hat
         FftSrc s0{SRC_CPLX, b0, 0, M, E, 0};
         FftDst toP{DST_REAL64, psi, E, 0, m2 - m, m, 1.0 / (double)M, 0};
         CK(op.fft(s0, toP, M, E, +1, bt, tw, MRC_TW_LOG, st));               // B[m, m2)

@@ -1,6 +1,8 @@
 // launchers.cuh -- host-side launchers for one working precision T.  Each
 // k_<prec>.cu includes this file once with MRC_T / MRC_SUF defined.
 #pragma once
+#include <stdlib.h>
+
 #include <algorithm>
 #include <utility>
 #include "kernels.cuh"

@@ -86,11 +86,13 @@ MRC_DECLARE_PREC(dd)
 // Element sizes of one complex value per precision.
 static inline size_t mrc_cx_bytes(int prec) { return prec == PREC_F32 ? 8 : 16; }
 
-// ozaki.cu: double-float square products (32 <= d <= 64) on BF16 tensor cores
+// ozaki.cu: double-float and FP32 square products (32 <= d <= 64) on BF16 tensor cores
 bool mrc_ozaki_supported(int r, int m, int c);
 cudaError_t mrc_ozaki_init(void);
 cudaError_t mrc_pairmul_dd_ozaki(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw,
                                  int tw_log, cudaStream_t st);
+cudaError_t mrc_pairmul_f32_ozaki(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw,
+                                  int tw_log, cudaStream_t st);
 
 // misc.cu
 cudaError_t mrc_gauss_jordan(const double *A0, double *out, double *work, int d, int *status, cudaStream_t st);

@@ -25,8 +25,8 @@
 // precision times |X||Y|.
 //
 // One CTA owns one frequency pair {f, M-f} (the real-FFT split and merge of
-// kernels.cuh), computes C(f) (stored unmerged in its output rows), then
-// C(M-f), then merges both into the packed output spectrum.
+// kernels.cuh), computes C(f) (kept in registers), then C(M-f), then merges
+// both into the packed output spectrum.
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
@@ -34,12 +34,25 @@
 namespace {
 
 constexpr int OZ_D = 64;       // padded matrix size
-constexpr int OZ_S = 6;        // digits per value
 constexpr int OZ_LD = 72;      // shared-memory row length (bf16), padded against bank conflicts
-constexpr int OZ_GMIN = 5;     // smallest digit-pair weight group kept
-constexpr int OZ_THREADS = 256;
+constexpr int OZ_THREADS = 512;
 constexpr int OZ_SLICE = OZ_D * OZ_LD;
-constexpr size_t OZ_SMEM = (size_t)4 * OZ_S * OZ_SLICE * sizeof(unsigned short) + 4 * OZ_D * sizeof(int);
+
+// Digits per value and smallest digit-pair weight group kept, per precision:
+// double-float 6 digits (48 bits), groups s + t >= 5; FP32 5 digits (40 bits
+// relative to the row/column maximum), groups s + t >= 5.  Fewer FP32 digits
+// are not enough: the level products cancel heavily (A*B = e0 + small), and
+// with 3 or 4 digits the error relative to the row maximum left max|rho_L|
+// at 1e-5 and 5e-10 after one refinement sweep at d = 33..64, against
+// 3e-14 with 5 digits (8.7e-14 with FP32 SIMT products).
+#ifndef MRC_OZ_F32_DIGITS
+#define MRC_OZ_F32_DIGITS 5
+#endif
+template <class T> struct OzP;
+template <> struct OzP<dd> { static constexpr int S = 6, GMIN = 5; };
+template <> struct OzP<float> { static constexpr int S = MRC_OZ_F32_DIGITS, GMIN = MRC_OZ_F32_DIGITS; };
+template <class T>
+constexpr size_t oz_smem() { return (size_t)4 * OzP<T>::S * OZ_SLICE * sizeof(unsigned short) + 4 * OZ_D * sizeof(int); }
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1)
 {
@@ -57,7 +70,7 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
 // 2^-17 + 2^-26, |e| <= 2^-41); e joins after four digits, where the rest is
 // <= 2^-33.  Each digit therefore stays within 128 (+ at most 1/2 before
 // rounding to an integer).
-__device__ __forceinline__ void digits6(float hi, float lo, float (&q)[OZ_S])
+__device__ __forceinline__ void digits6(float hi, float lo, float (&q)[6])
 {
     float x = hi, t;
     t = __fsub_rn(__fadd_rn(x, 49152.0f), 49152.0f);            // grid 2^-8
@@ -79,6 +92,55 @@ __device__ __forceinline__ void digits6(float hi, float lo, float (&q)[OZ_S])
     x = __fsub_rn(x, t);
     t = __fsub_rn(__fadd_rn(x, 0x1.8p-25f), 0x1.8p-25f);        // grid 2^-48
     q[0] = t * 0x1p48f;
+}
+
+// Three balanced base-256 digits of an FP32 value |x| <= 1/2 (weights 2^-8,
+// 2^-16, 2^-24; the rest, below 2^-25, is dropped as FP32 rounding).
+__device__ __forceinline__ void digits3(float x, float (&q)[3])
+{
+    float t;
+    t = __fsub_rn(__fadd_rn(x, 49152.0f), 49152.0f);
+    q[2] = t * 256.0f;
+    x = __fsub_rn(x, t);
+    t = __fsub_rn(__fadd_rn(x, 192.0f), 192.0f);
+    q[1] = t * 65536.0f;
+    x = __fsub_rn(x, t);
+    t = __fsub_rn(__fadd_rn(x, 0.75f), 0.75f);
+    q[0] = t * 16777216.0f;
+}
+
+__device__ __forceinline__ float hi_part(float x) { return x; }
+__device__ __forceinline__ float hi_part(dd x) { return x.hi; }
+
+__device__ __forceinline__ void split_digits(dd v, float sc, float (&q)[6]) { digits6(v.hi * sc, v.lo * sc, q); }
+__device__ __forceinline__ void split_digits(float v, float sc, float (&q)[3]) { digits3(v * sc, q); }
+__device__ __forceinline__ void split_digits(float v, float sc, float (&q)[5])
+{
+    float r[3];
+    float x = v * sc;
+    digits3(x, r);
+    float rest = __fsub_rn(__fsub_rn(__fsub_rn(x, r[2] * 0x1p-8f), r[1] * 0x1p-16f), r[0] * 0x1p-24f);
+    float t = __fsub_rn(__fadd_rn(rest, 0x1.8p-9f), 0x1.8p-9f);  // grid 2^-32
+    q[1] = t * 0x1p32f;
+    rest = __fsub_rn(rest, t);
+    t = __fsub_rn(__fadd_rn(rest, 0x1.8p-17f), 0x1.8p-17f);      // grid 2^-40
+    q[0] = t * 0x1p40f;
+    q[2] = r[0];
+    q[3] = r[1];
+    q[4] = r[2];
+}
+__device__ __forceinline__ void split_digits(float v, float sc, float (&q)[4])
+{
+    float r[3];
+    float x = v * sc;
+    digits3(x, r);
+    // fourth digit from the rest below 2^-24
+    const float rest = __fsub_rn(__fsub_rn(__fsub_rn(x, r[2] * 0x1p-8f), r[1] * 0x1p-16f), r[0] * 0x1p-24f);
+    const float t = __fsub_rn(__fadd_rn(rest, 0x1.8p-9f), 0x1.8p-9f);
+    q[0] = t * 0x1p32f;
+    q[1] = r[0];
+    q[2] = r[1];
+    q[3] = r[2];
 }
 
 __device__ __forceinline__ unsigned short bf16_bits(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
@@ -104,41 +166,85 @@ __device__ __forceinline__ int scale_exp(float b)
     return e + 1;
 }
 
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void *p)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(unsigned (&r)[4], const void *p)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+}
+
+// 16 warps: warp w owns rows 16 (w & 3) .. +16 and columns 16 (w >> 2) .. +16
+// of both C_r and C_i (two n-tiles of 8 each).  Digit tiles are row-major
+// [row][k] for X and [k][j] for Y (72-element rows: the 8 rows an ldmatrix
+// phase touches fall in distinct banks).
+template <class T>
+__device__ __forceinline__ T from_int(long long v, int ex);
+template <>
+__device__ __forceinline__ dd from_int<dd>(long long v, int ex)
+{
+    const float h = __ll2float_rn(v);
+    const float l = __ll2float_rn(v - __float2ll_rn(h));
+    return dd_fast_two_sum(scale2(h, ex), scale2(l, ex));
+}
+template <>
+__device__ __forceinline__ float from_int<float>(long long v, int ex) { return scale2(__ll2float_rn(v), ex); }
+
+template <class T>
 __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pairmul_kernel(PairArgs a)
 {
+    constexpr int OZ_S = OzP<T>::S, OZ_GMIN = OzP<T>::GMIN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned short *Xr = reinterpret_cast<unsigned short *>(smem_raw);  // [S][64][72]
+    unsigned short *Xr = reinterpret_cast<unsigned short *>(smem_raw);  // [S][64][72]  X_r digits [i][k]
     unsigned short *Xi = Xr + OZ_S * OZ_SLICE;
-    unsigned short *YrT = Xi + OZ_S * OZ_SLICE;  // transposed: [S][j][k]
-    unsigned short *YiT = YrT + OZ_S * OZ_SLICE;
-    unsigned *bx = reinterpret_cast<unsigned *>(YiT + OZ_S * OZ_SLICE);  // [64] row bounds (float bits)
+    unsigned short *Yr = Xi + OZ_S * OZ_SLICE;  // [S][64][72]  Y_r digits [k][j]
+    unsigned short *Yi = Yr + OZ_S * OZ_SLICE;
+    unsigned *bx = reinterpret_cast<unsigned *>(Yi + OZ_S * OZ_SLICE);  // [64] row bounds (float bits)
     unsigned *by = bx + OZ_D;
     int *sig = reinterpret_cast<int *>(by + OZ_D);
     int *tau = sig + OZ_D;
 
-    const cx<dd> *ZX = reinterpret_cast<const cx<dd> *>(a.zx);
-    const cx<dd> *ZY = reinterpret_cast<const cx<dd> *>(a.zy);
-    cx<dd> *ZC = reinterpret_cast<cx<dd> *>(a.zc);
-    const cx<dd> *tw = reinterpret_cast<const cx<dd> *>(a.tw);
+    const cx<T> *ZX = reinterpret_cast<const cx<T> *>(a.zx);
+    const cx<T> *ZY = reinterpret_cast<const cx<T> *>(a.zy);
+    cx<T> *ZC = reinterpret_cast<cx<T> *>(a.zc);
+    const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
     const int d = a.r;  // square: r = m = c = d <= 64
     const int64_t E = (int64_t)d * d;
     const int64_t p = blockIdx.x, M = a.M;
     const int64_t f = p, gL = M - p, gZ = gL & (M - 1);
-    const cx<dd> wf = tw[f << (a.tw_log - a.logM - 1)];
-    const cx<dd> wg = c_neg(c_conj(wf));
-    const int tid = threadIdx.x;
+    const cx<T> wf = tw[f << (a.tw_log - a.logM - 1)];
+    const cx<T> wg = c_neg(c_conj(wf));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    // ---- row (X) and column (Y) magnitude bounds: |Xh(f)|, |Xh(g)| <= |Z(f)| + |Z(g)|
-    for (int t = tid; t < 2 * OZ_D; t += OZ_THREADS) bx[t] = 0u;  // bx and by
+    // ---- magnitude bounds: |Xh(f)|, |Xh(g)| <= |Z(f)| + |Z(g)| entrywise.
+    // The 64 x 64 (padded) grid is walked as t = tid + 512 n: a thread keeps
+    // one column k = tid & 63, a warp one row per step.
+    for (int t = tid; t < 2 * OZ_D; t += OZ_THREADS) bx[t] = 0u;
     __syncthreads();
-    for (int t = tid; t < d * d; t += OZ_THREADS) {
-        const int i = t / d, k = t - i * d;
-        const cx<dd> xa = ZX[f * E + t], xb = ZX[gZ * E + t];
-        const cx<dd> ya = ZY[f * E + t], yb = ZY[gZ * E + t];
-        const float mx = fabsf(xa.re.hi) + fabsf(xa.im.hi) + fabsf(xb.re.hi) + fabsf(xb.im.hi);
-        const float my = fabsf(ya.re.hi) + fabsf(ya.im.hi) + fabsf(yb.re.hi) + fabsf(yb.im.hi);
-        atomicMax(&bx[i], __float_as_uint(mx));  // X row i
-        atomicMax(&by[k], __float_as_uint(my));  // Y entry (i=k row, k=column): column index is k here
+    {
+        const int k = tid & 63;
+        float my = 0.0f;
+        for (int t = tid; t < OZ_D * OZ_D; t += OZ_THREADS) {
+            const int i = t >> 6;
+            float mx = 0.0f;
+            if (i < d && k < d) {
+                const int64_t e = (int64_t)i * d + k;
+                const cx<T> xa = ZX[f * E + e], xb = ZX[gZ * E + e];
+                const cx<T> ya = ZY[f * E + e], yb = ZY[gZ * E + e];
+                mx = fabsf(hi_part(xa.re)) + fabsf(hi_part(xa.im)) + fabsf(hi_part(xb.re)) + fabsf(hi_part(xb.im));
+                my = fmaxf(my, fabsf(hi_part(ya.re)) + fabsf(hi_part(ya.im)) + fabsf(hi_part(yb.re)) +
+                                   fabsf(hi_part(yb.im)));
+            }
+            const unsigned wmx = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));  // one row per warp
+            if (lane == 0) atomicMax(&bx[i], wmx);
+        }
+        atomicMax(&by[k], __float_as_uint(my));
     }
     __syncthreads();
     for (int t = tid; t < OZ_D; t += OZ_THREADS) {
@@ -147,27 +253,29 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pairmul_kernel(PairArgs a
     }
     __syncthreads();
 
-    const int lane = tid & 31, warp = tid >> 5;
     const int gid = lane >> 2, tig = lane & 3;
-    const int i0 = (warp & 3) * 16, j0 = (warp >> 2) * 32;
+    const int i0 = (warp & 3) * 16, j0 = (warp >> 2) * 16;
     const bool two = (gZ != f);
     const int nfreq = (gL == f) ? 1 : 2;  // p = M/2 pairs with itself
+    // ldmatrix lane addresses (element offsets inside one digit tile)
+    const int a_off = (i0 + (lane & 15)) * OZ_LD + ((lane >> 4) << 3);               // + k0
+    const int b_off = ((lane & 7) + (((lane >> 3) & 1) << 3)) * OZ_LD + j0 + ((lane >> 4) << 3);  // + k0 * OZ_LD
 
-    cx<dd> keep[16];  // C(f) of this thread's outputs while C(g) is formed
+    cx<T> keep[8];  // C(f) of this thread's outputs while C(g) is formed
     for (int phase = 0; phase < nfreq; ++phase) {
-        // ---- split, scale and slice X(phi), Y(phi) into digit matrices
+        // ---- split, scale and slice X(phi), Y(phi) into digit tiles
         const int64_t ra = phase == 0 ? f : gZ, rb = phase == 0 ? gZ : f;
-        const cx<dd> w = phase == 0 ? wf : wg;
+        const cx<T> w = phase == 0 ? wf : wg;
         for (int t = tid; t < OZ_D * OZ_D; t += OZ_THREADS) {
             const int i = t >> 6, k = t & 63;
             float qr[OZ_S], qi[OZ_S];
-            // X entry (i, k)
-            if (i < d && k < d) {
-                const int64_t e = (int64_t)i * d + k;
-                cx<dd> x = split_real(ZX[ra * E + e], ZX[rb * E + e], w);
+            const bool in = i < d && k < d;
+            const int64_t e = (int64_t)i * d + k;
+            if (in) {
+                const cx<T> x = split_real(ZX[ra * E + e], ZX[rb * E + e], w);
                 const float sc = pow2f(-sig[i]);
-                digits6(x.re.hi * sc, x.re.lo * sc, qr);
-                digits6(x.im.hi * sc, x.im.lo * sc, qi);
+                split_digits(x.re, sc, qr);
+                split_digits(x.im, sc, qi);
             } else {
 #pragma unroll
                 for (int s = 0; s < OZ_S; ++s) qr[s] = qi[s] = 0.0f;
@@ -177,102 +285,85 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pairmul_kernel(PairArgs a
                 Xr[s * OZ_SLICE + i * OZ_LD + k] = bf16_bits(qr[s]);
                 Xi[s * OZ_SLICE + i * OZ_LD + k] = bf16_bits(qi[s]);
             }
-            // Y entry (row i -> k index of the product, column k -> j); stored transposed [j][k]
-            if (i < d && k < d) {
-                const int64_t e = (int64_t)i * d + k;
-                cx<dd> y = split_real(ZY[ra * E + e], ZY[rb * E + e], w);
+            // Y entry: row i is the product's k index, column k is j
+            if (in) {
+                const cx<T> y = split_real(ZY[ra * E + e], ZY[rb * E + e], w);
                 const float sc = pow2f(-tau[k]);
-                digits6(y.re.hi * sc, y.re.lo * sc, qr);
-                digits6(y.im.hi * sc, y.im.lo * sc, qi);
+                split_digits(y.re, sc, qr);
+                split_digits(y.im, sc, qi);
             } else {
 #pragma unroll
                 for (int s = 0; s < OZ_S; ++s) qr[s] = qi[s] = 0.0f;
             }
 #pragma unroll
             for (int s = 0; s < OZ_S; ++s) {
-                YrT[s * OZ_SLICE + k * OZ_LD + i] = bf16_bits(qr[s]);
-                YiT[s * OZ_SLICE + k * OZ_LD + i] = bf16_bits(qi[s]);
+                Yr[s * OZ_SLICE + i * OZ_LD + k] = bf16_bits(qr[s]);
+                Yi[s * OZ_SLICE + i * OZ_LD + k] = bf16_bits(qi[s]);
             }
         }
         __syncthreads();
 
         // ---- exact digit-pair products, grouped by weight
-        long long acc64[8][4];
+        long long acc64[4][4];
 #pragma unroll
-        for (int n = 0; n < 8; ++n)
+        for (int n = 0; n < 4; ++n)
 #pragma unroll
             for (int r = 0; r < 4; ++r) acc64[n][r] = 0;
         for (int g = 2 * (OZ_S - 1); g >= OZ_GMIN; --g) {
-            float acc[8][4];
+            float acc[4][4];  // [0..1]: C_r n-tiles, [2..3]: C_i n-tiles
 #pragma unroll
-            for (int n = 0; n < 8; ++n)
+            for (int n = 0; n < 4; ++n)
 #pragma unroll
                 for (int r = 0; r < 4; ++r) acc[n][r] = 0.0f;
             for (int s = max(0, g - (OZ_S - 1)); s <= min(OZ_S - 1, g); ++s) {
                 const int tt = g - s;
-                const unsigned short *xr = Xr + s * OZ_SLICE, *xi = Xi + s * OZ_SLICE;
-                const unsigned short *yr = YrT + tt * OZ_SLICE, *yi = YiT + tt * OZ_SLICE;
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
-                    const unsigned short *xa = half == 0 ? xr : xi;
+                    // half 0: X_r with (Y_r -> C_r, Y_i -> C_i); half 1: X_i with (-Y_i -> C_r, Y_r -> C_i)
+                    const unsigned short *xa = (half == 0 ? Xr : Xi) + s * OZ_SLICE + a_off;
+                    const unsigned short *ybr = (half == 0 ? Yr : Yi) + tt * OZ_SLICE + b_off;
+                    const unsigned short *ybi = (half == 0 ? Yi : Yr) + tt * OZ_SLICE + b_off;
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks) {
-                        const int k0 = ks * 16 + tig * 2;
-                        unsigned af[4];
-                        af[0] = *reinterpret_cast<const unsigned *>(xa + (i0 + gid) * OZ_LD + k0);
-                        af[1] = *reinterpret_cast<const unsigned *>(xa + (i0 + gid + 8) * OZ_LD + k0);
-                        af[2] = *reinterpret_cast<const unsigned *>(xa + (i0 + gid) * OZ_LD + k0 + 8);
-                        af[3] = *reinterpret_cast<const unsigned *>(xa + (i0 + gid + 8) * OZ_LD + k0 + 8);
+                        unsigned af[4], br[4], bi[4];
+                        ldsm_x4(af, xa + ks * 16);
+                        ldsm_x4_t(br, ybr + ks * 16 * OZ_LD);
+                        ldsm_x4_t(bi, ybi + ks * 16 * OZ_LD);
+                        if (half == 1) {
 #pragma unroll
-                        for (int nt = 0; nt < 4; ++nt) {
-                            const int jn = j0 + nt * 8 + gid;
-                            // C_r: X_r Y_r (half 0) + X_i (-Y_i) (half 1)
-                            const unsigned short *br = half == 0 ? yr : yi;
-                            unsigned b0 = *reinterpret_cast<const unsigned *>(br + jn * OZ_LD + k0);
-                            unsigned b1 = *reinterpret_cast<const unsigned *>(br + jn * OZ_LD + k0 + 8);
-                            if (half == 1) { b0 ^= 0x80008000u; b1 ^= 0x80008000u; }
-                            mma_bf16(acc[nt], af, b0, b1);
-                            // C_i: X_r Y_i (half 0) + X_i Y_r (half 1)
-                            const unsigned short *bi = half == 0 ? yi : yr;
-                            b0 = *reinterpret_cast<const unsigned *>(bi + jn * OZ_LD + k0);
-                            b1 = *reinterpret_cast<const unsigned *>(bi + jn * OZ_LD + k0 + 8);
-                            mma_bf16(acc[4 + nt], af, b0, b1);
+                            for (int u = 0; u < 4; ++u) br[u] ^= 0x80008000u;
                         }
+                        mma_bf16(acc[0], af, br[0], br[1]);
+                        mma_bf16(acc[1], af, br[2], br[3]);
+                        mma_bf16(acc[2], af, bi[0], bi[1]);
+                        mma_bf16(acc[3], af, bi[2], bi[3]);
                     }
                 }
             }
             const int sh = 8 * (g - OZ_GMIN);
 #pragma unroll
-            for (int n = 0; n < 8; ++n)
+            for (int n = 0; n < 4; ++n)
 #pragma unroll
                 for (int r = 0; r < 4; ++r) acc64[n][r] += (long long)__float2ll_rn(acc[n][r]) << sh;
         }
-        __syncthreads();  // digit matrices are rewritten by the next phase
+        __syncthreads();  // digit tiles are rewritten by the next phase
 
-        // ---- back to double-float, scaled by 2^(sigma_i + tau_j - 56)
+        // ---- back to the working precision, scaled by 2^(sigma_i + tau_j + 8 GMIN - 16 S)
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
+        for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int i = i0 + gid + ((r >> 1) << 3), j = j0 + nt * 8 + tig * 2 + (r & 1);
-                const int ex = sig[i] + tau[j] - 56;
-                cx<dd> v;
-                const long long sr = acc64[nt][r], si = acc64[4 + nt][r];
-                float h = __ll2float_rn(sr);
-                float l = __ll2float_rn(sr - __float2ll_rn(h));
-                v.re = dd_fast_two_sum(scale2(h, ex), scale2(l, ex));
-                h = __ll2float_rn(si);
-                l = __ll2float_rn(si - __float2ll_rn(h));
-                v.im = dd_fast_two_sum(scale2(h, ex), scale2(l, ex));
+                const int ex = sig[i] + tau[j] + 8 * OZ_GMIN - 16 * OZ_S;
+                const cx<T> v = {from_int<T>(acc64[nt][r], ex), from_int<T>(acc64[2 + nt][r], ex)};
                 const int o = nt * 4 + r;
                 if (phase == 0) keep[o] = v;
                 if (i >= d || j >= d) continue;
                 const int64_t e = (int64_t)i * d + j;
                 if (nfreq == 1) {
-                    // p = M/2: C(g) = C(f)
-                    ZC[f * E + e] = merge_real(v, v, c_conj(wf));
+                    ZC[f * E + e] = merge_real(v, v, c_conj(wf));  // p = M/2: C(g) = C(f)
                 } else if (phase == 1) {
-                    const cx<dd> cf = keep[o];
+                    const cx<T> cf = keep[o];
                     ZC[f * E + e] = merge_real(cf, v, c_conj(wf));
                     if (two) ZC[gZ * E + e] = merge_real(v, cf, c_conj(wg));
                 }
@@ -286,11 +377,16 @@ bool mrc_ozaki_supported(int r, int m, int c) { return r == m && m == c && r >= 
 
 cudaError_t mrc_ozaki_init(void)
 {
-    return cudaFuncSetAttribute(ozaki_pairmul_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(ozaki_pairmul_kernel<dd>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)oz_smem<dd>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(ozaki_pairmul_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)oz_smem<float>());
 }
 
-cudaError_t mrc_pairmul_dd_ozaki(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
-                                 cudaStream_t st)
+template <class T>
+cudaError_t ozaki_run(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
+                      cudaStream_t st, int kclass)
 {
     PairArgs a{};
     a.zx = zx; a.zy = zy; a.zc = zc; a.tw = tw; a.tw_log = tw_log; a.M = M;
@@ -299,10 +395,22 @@ cudaError_t mrc_pairmul_dd_ozaki(const void *zx, const void *zy, void *zc, int64
     a.logM = l;
     a.npairs = M >= 2 ? M / 2 + 1 : 1;
     a.r = a.m = a.c = d;
-    const double bytes = (double)M * 3.0 * d * d * sizeof(cx<dd>);
+    const double bytes = (double)M * 3.0 * d * d * sizeof(cx<T>);
     const double flops = 8.0 * d * d * d * (double)(M + 1);
-    mrc_prof_pre(6, st);
-    ozaki_pairmul_kernel<<<(unsigned)a.npairs, OZ_THREADS, OZ_SMEM, st>>>(a);
-    mrc_prof_post(6, st, bytes, flops);
+    mrc_prof_pre(kclass, st);
+    ozaki_pairmul_kernel<T><<<(unsigned)a.npairs, OZ_THREADS, oz_smem<T>(), st>>>(a);
+    mrc_prof_post(kclass, st, bytes, flops);
     return cudaGetLastError();
+}
+
+cudaError_t mrc_pairmul_dd_ozaki(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
+                                 cudaStream_t st)
+{
+    return ozaki_run<dd>(zx, zy, zc, M, d, tw, tw_log, st, 6);
+}
+
+cudaError_t mrc_pairmul_f32_ozaki(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw,
+                                  int tw_log, cudaStream_t st)
+{
+    return ozaki_run<float>(zx, zy, zc, M, d, tw, tw_log, st, 5);
 }
