@@ -165,9 +165,11 @@ size_t ws_inverse(int d, int64_t N, int prec)
     return std::max(a, b);
 }
 
-// Square double-float products with 32 <= d <= 64 run on the tensor cores
-// (ozaki.cu) unless MRC_DD_PRODUCT=simt selects the FP32-pipe kernel;
-// MRC_F32_PRODUCT=tensor moves the FP32 products there too.
+// Square products on the tensor cores: double-float with 32 <= d <= 64 as
+// exact digit products (ozaki.cu; MRC_DD_PRODUCT=simt selects the FP32-pipe
+// kernel).  Opt-in: MRC_F32_PRODUCT=tf32x3 (Newton-level FP32 products as
+// three TF32 products, tf32x3.cu) or =tensor (every FP32 product as digit
+// products).
 bool env_is_simt(const char *name)
 {
     const char *v = getenv(name);
@@ -177,6 +179,16 @@ bool env_is_simt(const char *name)
 cudaError_t pairmul_any(int prec, const void *zx, const void *zy, void *zc, int64_t M, int r, int m, int c,
                         const void *tw, cudaStream_t st, bool newton_level = false)
 {
+    // MRC_F32_PRODUCT=tf32x3 runs the Newton-level FP32 products as three TF32
+    // tensor-core products.  Off by default: its psi_0 is a few times less
+    // accurate than with FP32 dot products, and after one sweep e_rel reached
+    // 1.4e-10 at d = 16 (gate 1e-10); the correction psi * rho always keeps
+    // FP32 dot products (with TF32x3 there max|rho_L| stayed near 1e-11).
+    if (prec == PREC_F32 && newton_level && mrc_tf32x3_supported(r, m, c)) {
+        const char *fv = getenv("MRC_F32_PRODUCT");
+        if (fv && strcmp(fv, "tf32x3") == 0)
+            return mrc_pairmul_f32_tf32x3(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
+    }
     if (mrc_ozaki_supported(r, m, c)) {
         if (prec == PREC_DD && !env_is_simt("MRC_DD_PRODUCT"))
             return mrc_pairmul_dd_ozaki(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
@@ -379,6 +391,7 @@ mrc_status mrc_create(mrc_ctx **out, int device, size_t max_workspace_bytes)
     for (int p = 0; p < 3; ++p)
         if (OPS[p].init() != cudaSuccess) return MRC_ERR_CUDA;
     if (mrc_ozaki_init() != cudaSuccess) return MRC_ERR_CUDA;
+    if (mrc_tf32x3_init() != cudaSuccess) return MRC_ERR_CUDA;
     mrc_ctx *c = new mrc_ctx();
     c->device = device;
     c->cap = max_workspace_bytes;

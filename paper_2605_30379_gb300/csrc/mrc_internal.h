@@ -94,6 +94,12 @@ cudaError_t mrc_pairmul_dd_ozaki(const void *zx, const void *zy, void *zc, int64
 cudaError_t mrc_pairmul_f32_ozaki(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw,
                                   int tw_log, cudaStream_t st);
 
+// tf32x3.cu: FP32 square products (16 <= d <= 64) as three TF32 tensor-core products
+bool mrc_tf32x3_supported(int r, int m, int c);
+cudaError_t mrc_tf32x3_init(void);
+cudaError_t mrc_pairmul_f32_tf32x3(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw,
+                                   int tw_log, cudaStream_t st);
+
 // misc.cu
 cudaError_t mrc_gauss_jordan(const double *A0, double *out, double *work, int d, int *status, cudaStream_t st);
 cudaError_t mrc_base_case(const double *A, double *psi, int d, int64_t m0, cudaStream_t st);
