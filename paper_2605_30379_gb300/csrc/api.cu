@@ -143,7 +143,7 @@ size_t ws_newton(int d, int64_t N, int prec)
     const size_t E = (size_t)d * d;
     size_t b = align_up(sizeof(double) * 2 * E);  // Gauss-Jordan work
     const int64_t M = newton_maxM(d, N);
-    b += 4 * align_up((size_t)M * E * OPS[prec].cxb);
+    b += 3 * align_up((size_t)M * E * OPS[prec].cxb) + align_up(mrc_fft_scratch_elems(M, (int)E) * OPS[prec].cxb);
     return b;
 }
 
@@ -151,7 +151,8 @@ size_t ws_product(int64_t Mr, size_t EX, size_t EY, size_t EC, int prec)
 {
     size_t cxb = OPS[prec].cxb;
     size_t emax = std::max(EX, std::max(EY, EC));
-    return align_up(Mr * EX * cxb) + align_up(Mr * EY * cxb) + align_up(Mr * EC * cxb) + align_up(Mr * emax * cxb);
+    return align_up(Mr * EX * cxb) + align_up(Mr * EY * cxb) + align_up(Mr * EC * cxb) +
+           align_up(mrc_fft_scratch_elems(Mr, (int)emax) * cxb);
 }
 
 size_t ws_inverse(int d, int64_t N, int prec)
@@ -219,7 +220,7 @@ mrc_status conv_product(mrc_ctx *c, Arena &ar, int prec, const double *X, int64_
     void *bX = ar.take(Mr * EX * op.cxb);
     void *bY = ar.take(Mr * EY * op.cxb);
     void *bC = ar.take(Mr * EC * op.cxb);
-    void *bT = ar.take(Mr * emax * op.cxb);
+    void *bT = ar.take(mrc_fft_scratch_elems(Mr, (int)emax) * op.cxb);
     const void *tw = c->tw[prec];
     FftSrc sx{SRC_REAL64, X, 0, std::min(NX, N), (int)EX, 0};
     FftSrc sy{SRC_REAL64, Y, 0, std::min(NY, N), (int)EY, 0};
@@ -248,7 +249,7 @@ mrc_status newton_levels(mrc_ctx *c, Arena &ar, int prec, int d, int64_t N, cons
     void *b0 = ar.take((size_t)Mmax * E * op.cxb);
     void *b1 = ar.take((size_t)Mmax * E * op.cxb);
     void *b2 = ar.take((size_t)Mmax * E * op.cxb);
-    void *bt = ar.take((size_t)Mmax * E * op.cxb);
+    void *bt = ar.take(mrc_fft_scratch_elems(Mmax, E) * op.cxb);
     const void *tw = c->tw[prec];
     int lv = 0;
     for (int64_t m = m0; m < N; m <<= 1, ++lv) {
@@ -400,6 +401,7 @@ mrc_status mrc_create(mrc_ctx **out, int device, size_t max_workspace_bytes)
         return MRC_ERR_NO_MEMORY;
     }
     cudaMemset(c->d_status, 0, sizeof(int));
+    mrc_set_status_word(c->d_status);
     cudaEventCreate(&c->ev0);
     cudaEventCreate(&c->ev1);
     *out = c;
@@ -413,6 +415,7 @@ mrc_status mrc_destroy(mrc_ctx *c)
     cudaDeviceSynchronize();
     cudaFree(c->ws);
     for (int p = 0; p < 3; ++p) cudaFree(c->tw[p]);
+    if (mrc_status_word() == c->d_status) mrc_set_status_word(nullptr);
     cudaFree(c->d_status);
     cudaFree(c->d_acc);
     cudaEventDestroy(c->ev0);

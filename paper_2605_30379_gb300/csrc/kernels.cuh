@@ -167,7 +167,7 @@ struct FftPlan {
 
 template <class T, int LOGR, int EC, int S, bool INV>
 __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<T> *stw, const cx<T> *spt,
-                                          int64_t j, int e0, int ecount, int64_t base_out)
+                                          int64_t j, int e0, int ecount, int64_t base_out, bool staged)
 {
     using P = FftPlan<T, LOGR, EC>;
     constexpr int R = P::R, NT = P::NT;
@@ -188,17 +188,20 @@ __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<
             const int rho = b + q * (R / r);
             if constexpr (FIRST) {
                 cx<T> x = c_zero<T>();
-                if (e < ecount) {
+                if (staged) {
+                    x = sm[rho * EC + e];  // rows past the valid range were zero-filled
+                    if (a.src_neg) x = c_neg(x);
+                } else if (e < ecount) {
                     x = fft_load<T>(a, j + (int64_t)rho * (a.M >> LOGR), e0 + e);
-                    if (a.Ns > 1) x = c_mul(x, spt[rho]);
                 }
+                if (a.Ns > 1) x = c_mul(x, spt[rho]);
                 v[u][q] = x;
             } else {
                 v[u][q] = sm[rho * EC + e];
             }
         }
     }
-    if constexpr (!FIRST) __syncthreads();
+    if (!FIRST || staged) __syncthreads();  // every read of sm done before the in-place writes
 #pragma unroll
     for (int u = 0; u < UPT; ++u) {
         const int b = (tid + u * NT) >> P::LEC;
@@ -225,6 +228,65 @@ __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<
         }
     }
     if constexpr (!LAST) __syncthreads();
+}
+
+// Bulk-copy staging of a complex source (TMA, cp.async.bulk): warp 0 copies
+// the R row segments j + rho M/R (EC entries each, EC * sizeof(cx<T>) bytes,
+// 16-byte aligned: checked on the host) into sm[rho][*], completing on one
+// mbarrier; the other warps zero-fill the segments of rows past the valid
+// range.  The wait is bounded: if it gives up, the status word is set to
+// MRC_ERR_TIMEOUT and a second bounded wait lets copies in flight land before
+// the CTA moves on.
+__device__ __forceinline__ bool mbar_try_wait(unsigned addr, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(addr), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+template <class T, int LOGR, int EC>
+__device__ __forceinline__ void fft_stage_in_tma(const FftArgs &a, cx<T> *sm, int64_t j, int e0)
+{
+    using P = FftPlan<T, LOGR, EC>;
+    constexpr int R = P::R;
+    __shared__ alignas(8) unsigned long long mbar;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const unsigned mb = (unsigned)__cvta_generic_to_shared(&mbar);
+    const int64_t stride = a.M >> LOGR;
+    // valid rows: k = j + rho * stride < nvalid
+    const int64_t nv64 = a.src_nvalid > j ? (a.src_nvalid - j + stride - 1) / stride : 0;
+    const int nv = (int)(nv64 < R ? nv64 : R);
+    constexpr unsigned SEG = EC * sizeof(cx<T>);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (tid < 32) {
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mb), "r"(SEG * nv)
+                         : "memory");
+        __syncwarp();
+        const cx<T> *src = reinterpret_cast<const cx<T> *>(a.src);
+        for (int rho = lane; rho < nv; rho += 32) {
+            const cx<T> *g = src + (a.src_row0 + j + (int64_t)rho * stride) * (int64_t)a.src_ld + e0;
+            const unsigned s = (unsigned)__cvta_generic_to_shared(sm + rho * EC);
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(s),
+                "l"(g), "r"(SEG), "r"(mb)
+                : "memory");
+        }
+    } else {
+        for (int idx = nv * EC + (tid - 32); idx < R * EC; idx += P::NT - 32) sm[idx] = c_zero<T>();
+    }
+    bool done = false;
+    for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(mb, 0);
+    if (!done) {
+        if (a.status) atomicExch(a.status, 6);
+        for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(mb, 0);
+    }
 }
 
 template <class T, int LOGR, int EC, bool INV>
@@ -254,12 +316,14 @@ __device__ __forceinline__ void fft_pass_body(const FftArgs &a)
             spt[t] = INV ? c_conj(w) : w;
         }
     }
+    const bool staged = a.tma != 0;
+    if (staged) fft_stage_in_tma<T, LOGR, EC>(a, sm, j, e0);
     __syncthreads();
     const int64_t base_out = (j >> a.logNs << (a.logNs + LOGR)) + jm;
-    fft_stage<T, LOGR, EC, 0, INV>(a, sm, stw, spt, j, e0, ecount, base_out);
-    if constexpr (P::NSTAGE > 1) fft_stage<T, LOGR, EC, 1, INV>(a, sm, stw, spt, j, e0, ecount, base_out);
-    if constexpr (P::NSTAGE > 2) fft_stage<T, LOGR, EC, 2, INV>(a, sm, stw, spt, j, e0, ecount, base_out);
-    if constexpr (P::NSTAGE > 3) fft_stage<T, LOGR, EC, 3, INV>(a, sm, stw, spt, j, e0, ecount, base_out);
+    fft_stage<T, LOGR, EC, 0, INV>(a, sm, stw, spt, j, e0, ecount, base_out, staged);
+    if constexpr (P::NSTAGE > 1) fft_stage<T, LOGR, EC, 1, INV>(a, sm, stw, spt, j, e0, ecount, base_out, staged);
+    if constexpr (P::NSTAGE > 2) fft_stage<T, LOGR, EC, 2, INV>(a, sm, stw, spt, j, e0, ecount, base_out, staged);
+    if constexpr (P::NSTAGE > 3) fft_stage<T, LOGR, EC, 3, INV>(a, sm, stw, spt, j, e0, ecount, base_out, staged);
 }
 
 // One Stockham pass of radix R = 2^LOGR over EC entries per CTA.

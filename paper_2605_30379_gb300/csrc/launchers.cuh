@@ -1,6 +1,7 @@
 // launchers.cuh -- host-side launchers for one working precision T.  Each
 // k_<prec>.cu includes this file once with MRC_T / MRC_SUF defined.
 #pragma once
+#include <stdint.h>
 #include <stdlib.h>
 
 #include <algorithm>
@@ -64,6 +65,7 @@ cudaError_t fft_run(const FftSrc &src, const FftDst &dst, int64_t M, int E, int 
     int logRs[2];
     const int np = fft_plan(logM, logRs);
     const int ec = pick_ec<T>(E);
+    const int sld = E;  // scratch row length (complex elements)
     int logNs = 0;
     for (int ps = 0; ps < np; ++ps) {
         FftArgs a{};
@@ -80,16 +82,25 @@ cudaError_t fft_run(const FftSrc &src, const FftDst &dst, int64_t M, int E, int 
             a.src_mode = src.mode; a.src = src.ptr; a.src_row0 = src.row0; a.src_nvalid = src.nvalid;
             a.src_ld = src.ld; a.src_neg = src.neg;
         } else {
-            a.src_mode = SRC_CPLX; a.src = scratch; a.src_row0 = 0; a.src_nvalid = M; a.src_ld = E; a.src_neg = 0;
+            a.src_mode = SRC_CPLX; a.src = scratch; a.src_row0 = 0; a.src_nvalid = M; a.src_ld = sld; a.src_neg = 0;
         }
         if (ps == np - 1) {
             a.dst_mode = dst.mode; a.dst = dst.ptr; a.dst_ld = dst.ld; a.dst_lo = dst.lo; a.dst_hi = dst.hi;
             a.dst_row0 = dst.row0; a.dst_scale = dst.scale; a.dst_eye_d = dst.eye_d;
         } else {
-            a.dst_mode = DST_CPLX; a.dst = scratch; a.dst_ld = E; a.dst_lo = 0; a.dst_hi = 0; a.dst_row0 = 0;
+            a.dst_mode = DST_CPLX; a.dst = scratch; a.dst_ld = sld; a.dst_lo = 0; a.dst_hi = 0; a.dst_row0 = 0;
             a.dst_scale = 1.0; a.dst_eye_d = 0;
         }
         a.dst_scale_f = (float)a.dst_scale;
+        // bulk-copy staging of a complex source: 16-byte aligned row segments
+        // of whole chunks, and at least one warp besides the copying warp
+        {
+            const FftEntry &kk = fft_table<T>()[ec_index<T>(ec)][a.logR];
+            const size_t rowb = (size_t)a.src_ld * sizeof(cx<T>);
+            a.tma = a.src_mode == SRC_CPLX && kk.nt >= 64 && (E % ec) == 0 && (rowb % 16) == 0 &&
+                    (((uintptr_t)a.src) % 16) == 0 && ((ec * sizeof(cx<T>)) % 16) == 0 && mrc_fft_tma_enabled();
+            a.status = mrc_status_word();
+        }
         dim3 grid((unsigned)(M >> a.logR), (unsigned)((E + ec - 1) / ec));
         // algorithmic charge: the valid source rows read once, the kept output written once,
         // 5 M log2(R) real flops per entry (radix-2 convention)

@@ -34,6 +34,8 @@ struct FftArgs {
     double dst_scale;       // signed power of two
     float dst_scale_f;      // the same, for the FP32-based precisions
     int dst_eye_d;          // REAL64*: if > 0 add 1 to the diagonal of real row 0 (d = this)
+    int tma;                // CPLX source staged into shared memory by bulk copies (first stage)
+    int *status;            // device status word: MRC_ERR_TIMEOUT (6) if a bounded wait gives up
 };
 
 struct PairArgs {
@@ -63,6 +65,16 @@ struct FftDst {
     double scale;
     int eye_d;
 };
+
+// prof.cu: device status word that bounded in-kernel waits report timeouts to
+// (the most recently created context's), and the FFT staging switch
+// (MRC_FFT_TMA=1 turns bulk-copy staging of complex sources on; measured
+// slower on the d = 64 workload, so off by default)
+int *mrc_status_word(void);
+void mrc_set_status_word(int *p);
+bool mrc_fft_tma_enabled(void);
+// elements of FFT scratch a transform of M points over E entries needs
+static inline size_t mrc_fft_scratch_elems(int64_t M, int E) { return (size_t)M * (size_t)E; }
 
 // prof.cu: every launch is bracketed by these (launch counter, optional timing)
 void mrc_prof_pre(int kclass, cudaStream_t st);

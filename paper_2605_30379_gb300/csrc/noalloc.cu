@@ -56,7 +56,8 @@ int64_t max_level(int d, int64_t N)
 size_t need_bytes(int d, int64_t N)
 {
     const size_t E = (size_t)d * d;
-    return kWorkOff + up256(sizeof(double) * 2 * E) + 4 * up256((size_t)max_level(d, N) * E * 16);
+    return kWorkOff + up256(sizeof(double) * 2 * E) + 3 * up256((size_t)max_level(d, N) * E * 16) +
+           up256(mrc_fft_scratch_elems(max_level(d, N), (int)E) * 16);
 }
 
 // Once per device, with that device current: resolve the array's device

@@ -6,6 +6,8 @@
 // on its own stream, together with the algorithmic bytes and flops the launch
 // is charged with; mrc_profile_end sums them.  Not thread safe: profile one
 // host thread at a time.
+#include <stdlib.h>
+
 #include <atomic>
 #include <vector>
 
@@ -26,6 +28,18 @@ constexpr size_t kPool = 16384;
 } // namespace
 
 void mrc_prof_set_capturing(bool on) { g_prof.capturing = on; }
+
+namespace {
+int *g_status_word = nullptr;
+}
+int *mrc_status_word(void) { return g_status_word; }
+void mrc_set_status_word(int *p) { g_status_word = p; }
+bool mrc_fft_tma_enabled(void)
+{
+    const char *v = getenv("MRC_FFT_TMA");
+    return v && v[0] == '1';
+}
+
 
 void mrc_prof_pre(int kclass, cudaStream_t st)
 {

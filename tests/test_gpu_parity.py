@@ -277,3 +277,22 @@ def test_mixed_inverse_with_fp32_tensor_products(mrc, mode):
         del os.environ["MRC_F32_PRODUCT"]
     assert e_rel(psi.cpu().numpy(), ref) <= 1e-9
     assert rep["res_max_abs"] <= TOL_REL
+
+
+def test_fft_bulk_copy_staging_matches_oracle(mrc):
+    """MRC_FFT_TMA=1 stages complex FFT inputs into shared memory with
+    cp.async.bulk (off by default: slower on the d = 64 workload); both
+    precisions must still match the oracle."""
+    import os
+    q, _ = synth.weibull_model(16, 3000, seed=41)
+    A = synth.identity_minus(q)
+    ref = oracle.inverse_left(A)
+    os.environ["MRC_FFT_TMA"] = "1"
+    try:
+        p64 = mrc.inverse(dev(A), prec="fp64").cpu().numpy()
+        pmx = mrc.inverse(dev(A), prec="mixed").cpu().numpy()
+        mrc.sync_status()
+    finally:
+        del os.environ["MRC_FFT_TMA"]
+    assert np.abs(p64 - ref).max() <= TOL64
+    assert e_rel(pmx, ref) <= TOL_REL
