@@ -160,6 +160,23 @@ def make_input(name):
     return A
 
 
+def max_over_ranks_on(x, world, device):
+    """The slowest rank's time (all ranks receive it); identity at world size 1."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, ms_step, world):
+    """Whole-job rate: the units every rank processed per second of the
+    slowest rank's step time (replicas: each rank processes units_per_rank)."""
+    return world * units_per_rank / (ms_step * 1e-3)
+
+
 def cpu_oracle_sample(A_host, d, budget_s=15.0):
     """Time the FP64 oracle (direct recursion) on a prefix of the same input,
     doubling the prefix until one call takes >= budget_s / 4 (then one timed call)."""
@@ -251,11 +268,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_on(x, world, "cuda")
 
     d, N, kind, _ = WORKLOADS[args.workload]
     hosts = make_input(args.workload)
@@ -327,7 +340,7 @@ def main():
     barrier()
     clocks = sampler.stop()
     ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps)
-    value = world * coeffs / (ms_step * 1e-3)
+    value = job_throughput(coeffs, ms_step, world)
 
     # ---- the plain FP64 path on the same inputs
     fp64 = None
@@ -341,7 +354,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ms64 = max_over_ranks(e0.elapsed_time(e1) / args.fp64_steps)
-        fp64 = {"value": world * coeffs / (ms64 * 1e-3), "ms_per_step": ms64, "steps": args.fp64_steps}
+        fp64 = {"value": job_throughput(coeffs, ms64, world), "ms_per_step": ms64, "steps": args.fp64_steps}
         step()  # leave the mixed result in psi for the accuracy check
         torch.cuda.synchronize()
 
@@ -401,7 +414,7 @@ def main():
             "roofline": roof,
             "clocks": clocks,
             "e2e": None if ms_e2e is None else {
-                "value": world * coeffs / (ms_e2e * 1e-3), "unit": "coefficients/s",
+                "value": job_throughput(coeffs, ms_e2e, world), "unit": "coefficients/s",
                 "h2d_bytes_per_step": coeffs * 8, "d2h_bytes_per_step": coeffs * 8, "ms_per_step": ms_e2e},
             "cpu_baseline": cpu,
         }

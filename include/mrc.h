@@ -60,7 +60,11 @@ typedef struct {
     int prec;               /* mrc_precision */
     int refine_sweeps;      /* MRC_MIXED: residual/correction sweeps (default 1, max 4) */
     double target_residual; /* MRC_MIXED with a report: max|rho_L| bound checked after refinement (0 = no check) */
-    int autotune;           /* reserved; 0 */
+    int autotune;           /* 1: pick the per-frequency product kernel (FP32-pipe tile 16/32/64, or the
+                               tensor-core kernel for double-float) by timing each candidate once per
+                               (precision, shape, transform size) on the call's own stream; choices are
+                               kept in the context and, if MRC_AUTOTUNE_CACHE names a file, loaded at
+                               mrc_create and written at mrc_destroy.  Batched calls tune before capture. */
 } mrc_options;
 
 typedef struct {
@@ -183,6 +187,26 @@ mrc_status mrc_first_entrance(mrc_ctx *ctx, int d, int64_t N, const double *q, c
  */
 mrc_status mrc_occupation(mrc_ctx *ctx, int d, int64_t N, const double *P, const double *alpha,
                           const int *B, int nB, double *out, void *stream);
+
+/*
+ * mrc_reward -- reward-type functional V = psi * r (Eq. (reward)): the
+ * solution of V = r + q * V with a rectangular right-hand side.
+ *   psi : device [N][d][d], the Markov renewal sequence.
+ *   r   : device [N][d][c] reward sequence (c >= 1 columns).
+ *   V   : device [N][d][c] output.
+ *   prec: MRC_FP64 or MRC_MIXED (double-float convolution).
+ */
+mrc_status mrc_reward(mrc_ctx *ctx, int d, int c, int64_t N, const double *psi, const double *r, double *V,
+                      int prec, void *stream);
+
+/*
+ * mrc_renewal_visits -- expected renewal visits to B counted from time 0,
+ * Eq. (renewal-visits): out(k) = alpha sum_{l<=k} psi(l) I_B 1_s.
+ *   psi   : device [N][d][d];  alpha : device [d];
+ *   B, nB : HOST list of states in B;  out : device [N].
+ */
+mrc_status mrc_renewal_visits(mrc_ctx *ctx, int d, int64_t N, const double *psi, const double *alpha,
+                              const int *B, int nB, double *out, void *stream);
 
 /*
  * mrc_inverse_noalloc -- the FP64 inverse of mrc_inverse (same kernels, same

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <vector>
 
 #include "../../include/mrc.h"
@@ -42,6 +43,12 @@ struct mrc_ctx {
     cudaStream_t bst[MRC_BATCH_STREAMS] = {};
     cudaEvent_t bev[MRC_BATCH_STREAMS] = {};
     std::vector<BatchGraph> graphs;  // most recent last
+    // autotuner of the per-frequency product kernel: key -> choice
+    // (0..2: FP32-pipe tile configuration 16/32/64, 3: tensor-core kernel)
+    std::map<uint64_t, int> tune;
+    bool autotune = false;   // the current call asked for it
+    bool capturing = false;  // a batch graph is being captured: no timing
+    bool tune_dirty = false;
 };
 
 void mrc_prof_set_capturing(bool on);
@@ -51,6 +58,8 @@ namespace {
 struct PrecOps {
     cudaError_t (*fft)(const FftSrc &, const FftDst &, int64_t, int, int, void *, const void *, int, cudaStream_t);
     cudaError_t (*pairmul)(const void *, const void *, void *, int64_t, int, int, int, const void *, int, cudaStream_t);
+    cudaError_t (*pairmul_cfg)(const void *, const void *, void *, int64_t, int, int, int, int, const void *, int,
+                               cudaStream_t);
     cudaError_t (*pairdiag)(const void *, const void *, void *, int64_t, int, int, const void *, int, cudaStream_t);
     cudaError_t (*twiddles)(void *, int, cudaStream_t);
     cudaError_t (*init)(void);
@@ -58,9 +67,9 @@ struct PrecOps {
 };
 
 const PrecOps OPS[3] = {
-    {mrc_fft_f64, mrc_pairmul_f64, mrc_pairdiag_f64, mrc_twiddles_f64, mrc_init_f64, 16},
-    {mrc_fft_f32, mrc_pairmul_f32, mrc_pairdiag_f32, mrc_twiddles_f32, mrc_init_f32, 8},
-    {mrc_fft_dd, mrc_pairmul_dd, mrc_pairdiag_dd, mrc_twiddles_dd, mrc_init_dd, 16},
+    {mrc_fft_f64, mrc_pairmul_f64, mrc_pairmul_cfg_f64, mrc_pairdiag_f64, mrc_twiddles_f64, mrc_init_f64, 16},
+    {mrc_fft_f32, mrc_pairmul_f32, mrc_pairmul_cfg_f32, mrc_pairdiag_f32, mrc_twiddles_f32, mrc_init_f32, 8},
+    {mrc_fft_dd, mrc_pairmul_dd, mrc_pairmul_cfg_dd, mrc_pairdiag_dd, mrc_twiddles_dd, mrc_init_dd, 16},
 };
 
 int64_t pow2ceil(int64_t x)
@@ -177,29 +186,81 @@ bool env_is_simt(const char *name)
     return v && strcmp(v, "simt") == 0;
 }
 
-cudaError_t pairmul_any(int prec, const void *zx, const void *zy, void *zc, int64_t M, int r, int m, int c,
-                        const void *tw, cudaStream_t st, bool newton_level = false)
+cudaError_t launch_choice(int prec, int choice, const void *zx, const void *zy, void *zc, int64_t M, int r, int m,
+                          int c, const void *tw, cudaStream_t st)
+{
+    if (choice == 3) return mrc_pairmul_dd_ozaki(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
+    return OPS[prec].pairmul_cfg(zx, zy, zc, M, r, m, c, choice, tw, MRC_TW_LOG, st);
+}
+
+uint64_t tune_key(int prec, int r, int m, int c, int64_t M)
+{
+    int l = 0;
+    while (((int64_t)1 << l) < M) ++l;
+    return ((uint64_t)prec << 40) | ((uint64_t)r << 30) | ((uint64_t)m << 20) | ((uint64_t)c << 10) | (uint64_t)l;
+}
+
+// Autotuned product kernel for (precision, r, m, c, log2 M): every candidate
+// runs once to warm up and twice under CUDA events on the call's own buffers
+// and stream; the fastest is cached in the context.  Candidates compute the
+// same product (the tensor-core kernel only for double-float, where its
+// accuracy matches), so whichever ran last leaves a valid result behind.
+// Returns -1 (use the built-in choice) when tuning is off or a graph is being
+// captured.
+int tuned_choice(mrc_ctx *cx, int prec, const void *zx, const void *zy, void *zc, int64_t M, int r, int m, int c,
+                 const void *tw, cudaStream_t st)
+{
+    if (!cx || !cx->autotune) return -1;
+    const uint64_t key = tune_key(prec, r, m, c, M);
+    auto it = cx->tune.find(key);
+    if (it != cx->tune.end()) return it->second;
+    if (cx->capturing) return -1;
+    int cands[4] = {0, 1, 2, 3};
+    const int nc = (prec == PREC_DD && mrc_ozaki_supported(r, m, c)) ? 4 : 3;
+    float best = 1e30f;
+    int pick = -1;
+    for (int k = 0; k < nc; ++k) {
+        if (launch_choice(prec, cands[k], zx, zy, zc, M, r, m, c, tw, st) != cudaSuccess) continue;
+        cudaEventRecord(cx->ev0, st);
+        launch_choice(prec, cands[k], zx, zy, zc, M, r, m, c, tw, st);
+        launch_choice(prec, cands[k], zx, zy, zc, M, r, m, c, tw, st);
+        cudaEventRecord(cx->ev1, st);
+        if (cudaEventSynchronize(cx->ev1) != cudaSuccess) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, cx->ev0, cx->ev1);
+        if (ms < best) { best = ms; pick = cands[k]; }
+    }
+    cudaGetLastError();
+    if (pick >= 0) {
+        cx->tune[key] = pick;
+        cx->tune_dirty = true;
+    }
+    return pick;
+}
+
+cudaError_t pairmul_any(mrc_ctx *cx, int prec, const void *zx, const void *zy, void *zc, int64_t M, int r, int m,
+                        int c, const void *tw, cudaStream_t st, bool newton_level = false)
 {
     // MRC_F32_PRODUCT=tf32x3 runs the Newton-level FP32 products as three TF32
     // tensor-core products.  Off by default: its psi_0 is a few times less
     // accurate than with FP32 dot products, and after one sweep e_rel reached
     // 1.4e-10 at d = 16 (gate 1e-10); the correction psi * rho always keeps
     // FP32 dot products (with TF32x3 there max|rho_L| stayed near 1e-11).
-    if (prec == PREC_F32 && newton_level && mrc_tf32x3_supported(r, m, c)) {
-        const char *fv = getenv("MRC_F32_PRODUCT");
-        if (fv && strcmp(fv, "tf32x3") == 0)
-            return mrc_pairmul_f32_tf32x3(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
+    const char *fv = getenv("MRC_F32_PRODUCT");
+    if (prec == PREC_F32 && newton_level && mrc_tf32x3_supported(r, m, c) && fv && strcmp(fv, "tf32x3") == 0)
+        return mrc_pairmul_f32_tf32x3(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
+    // FP32 products stay on the FP32 pipes unless MRC_F32_PRODUCT=tensor: at
+    // d <= 64 the per-entry digit work outweighs the tensor-core savings
+    // (d = 64, N = 2^18: 118 ms on the tensor cores against 54.5 ms)
+    if (prec == PREC_F32 && mrc_ozaki_supported(r, m, c) && fv && strcmp(fv, "tensor") == 0)
+        return mrc_pairmul_f32_ozaki(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
+    const bool dd_env = prec == PREC_DD && getenv("MRC_DD_PRODUCT");
+    if (!dd_env) {
+        const int ch = tuned_choice(cx, prec, zx, zy, zc, M, r, m, c, tw, st);
+        if (ch >= 0) return launch_choice(prec, ch, zx, zy, zc, M, r, m, c, tw, st);
     }
-    if (mrc_ozaki_supported(r, m, c)) {
-        if (prec == PREC_DD && !env_is_simt("MRC_DD_PRODUCT"))
-            return mrc_pairmul_dd_ozaki(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
-        // FP32 products stay on the FP32 pipes unless MRC_F32_PRODUCT=tensor: at
-        // d <= 64 the per-entry digit work outweighs the tensor-core savings
-        // (d = 64, N = 2^18: 118 ms on the tensor cores against 54.5 ms)
-        const char *fv = getenv("MRC_F32_PRODUCT");
-        if (prec == PREC_F32 && fv && strcmp(fv, "tensor") == 0)
-            return mrc_pairmul_f32_ozaki(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
-    }
+    if (prec == PREC_DD && mrc_ozaki_supported(r, m, c) && !env_is_simt("MRC_DD_PRODUCT"))
+        return mrc_pairmul_dd_ozaki(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
     return OPS[prec].pairmul(zx, zy, zc, M, r, m, c, tw, MRC_TW_LOG, st);
 }
 
@@ -229,7 +290,7 @@ mrc_status conv_product(mrc_ctx *c, Arena &ar, int prec, const double *X, int64_
     CK(op.fft(sx, dx, Mr, (int)EX, -1, bT, tw, MRC_TW_LOG, st));
     CK(op.fft(sy, dy, Mr, (int)EY, -1, bT, tw, MRC_TW_LOG, st));
     if (diag) CK(op.pairdiag(bX, bY, bC, Mr, r, cc, tw, MRC_TW_LOG, st));
-    else CK(pairmul_any(prec, bX, bY, bC, Mr, r, m, cc, tw, st));
+    else CK(pairmul_any(c, prec, bX, bY, bC, Mr, r, m, cc, tw, st));
     FftSrc sc{SRC_CPLX, bC, 0, Mr, (int)EC, 0};
     FftDst dc{add ? DST_REAL64_ADD : DST_REAL64, out, (int)EC, 0, N, 0, sign / (double)Mr, eye_d};
     CK(op.fft(sc, dc, Mr, (int)EC, +1, bT, tw, MRC_TW_LOG, st));
@@ -260,14 +321,14 @@ mrc_status newton_levels(mrc_ctx *c, Arena &ar, int prec, int d, int64_t N, cons
         FftDst to1{DST_CPLX, b1, E, 0, 0, 0, 1.0, 0};
         CK(op.fft(sA, to0, M, E, -1, bt, tw, MRC_TW_LOG, st));               // A-hat
         CK(op.fft(sB, to1, M, E, -1, bt, tw, MRC_TW_LOG, st));               // B-hat
-        CK(pairmul_any(prec, b0, b1, b2, M, d, d, d, tw, st, true));        // (A B)-hat
+        CK(pairmul_any(c, prec, b0, b1, b2, M, d, d, d, tw, st, true));     // (A B)-hat
         FftSrc s2{SRC_CPLX, b2, 0, M, E, 0};
         FftDst t0s{DST_CPLX, b0, E, 0, 0, 0, 1.0 / (double)M, 0};
         CK(op.fft(s2, t0s, M, E, +1, bt, tw, MRC_TW_LOG, st));               // A*B, packed time
         FftSrc sR{SRC_CPLX, b0, M / 2, M / 2, E, 1};                          // R = -(A*B)[m, 2m)
         FftDst to2{DST_CPLX, b2, E, 0, 0, 0, 1.0, 0};
         CK(op.fft(sR, to2, M, E, -1, bt, tw, MRC_TW_LOG, st));               // R-hat
-        CK(pairmul_any(prec, b1, b2, b0, M, d, d, d, tw, st, true));        // (B R)-hat
+        CK(pairmul_any(c, prec, b1, b2, b0, M, d, d, d, tw, st, true));     // (B R)-hat
         FftSrc s0{SRC_CPLX, b0, 0, M, E, 0};
         FftDst toP{DST_REAL64, psi, E, 0, m2 - m, m, 1.0 / (double)M, 0};
         CK(op.fft(s0, toP, M, E, +1, bt, tw, MRC_TW_LOG, st));               // B[m, m2)
@@ -362,6 +423,55 @@ size_t ws_residual(int d, int64_t N, int prec, bool need_tmp)
     return ws_product(pow2ceil(N), E, E, E, p) + (need_tmp ? align_up(sizeof(double) * N * E) : 0);
 }
 
+// The options' autotune flag holds for one API call.
+struct TuneScope {
+    mrc_ctx *cx;
+    TuneScope(mrc_ctx *c, const mrc_options *o) : cx(c) { cx->autotune = o && o->autotune; }
+    ~TuneScope() { cx->autotune = false; }
+};
+
+// Tune every product shape one model's inverse uses, on workspace buffers,
+// before a batch graph is captured (timing is impossible during capture).
+void pretune_model(mrc_ctx *cx, int prec, int d, int64_t N, char *buf, size_t bytes, cudaStream_t st)
+{
+    const size_t E = (size_t)d * d;
+    auto one = [&](int p, int64_t M) {
+        const size_t sz = align_up((size_t)M * E * OPS[p].cxb);
+        if (3 * sz > bytes) return;
+        tuned_choice(cx, p, buf, buf + sz, buf + 2 * sz, M, d, d, d, cx->tw[p], st);
+    };
+    const int pl = prec == MRC_FP64 ? PREC_F64 : PREC_F32;
+    for (int64_t m = base_size(d, N); m < N; m <<= 1) one(pl, m);
+    if (prec == MRC_MIXED) {
+        one(PREC_DD, pow2ceil(N));
+        one(PREC_F32, pow2ceil(N));
+    }
+}
+
+void tune_load(mrc_ctx *cx)
+{
+    const char *path = getenv("MRC_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    unsigned long long k;
+    int ch;
+    while (fscanf(f, "%llu %d", &k, &ch) == 2)
+        if (ch >= 0 && ch <= 3) cx->tune[(uint64_t)k] = ch;
+    fclose(f);
+}
+
+void tune_save(mrc_ctx *cx)
+{
+    const char *path = getenv("MRC_AUTOTUNE_CACHE");
+    if (!path || !cx->tune_dirty) return;
+    FILE *f = fopen(path, "w");
+    if (!f) return;
+    for (auto &kv : cx->tune) fprintf(f, "%llu %d\n", (unsigned long long)kv.first, kv.second);
+    fclose(f);
+    cx->tune_dirty = false;
+}
+
 } // namespace
 
 // ===========================================================================
@@ -402,6 +512,7 @@ mrc_status mrc_create(mrc_ctx **out, int device, size_t max_workspace_bytes)
     }
     cudaMemset(c->d_status, 0, sizeof(int));
     mrc_set_status_word(c->d_status);
+    tune_load(c);
     cudaEventCreate(&c->ev0);
     cudaEventCreate(&c->ev1);
     *out = c;
@@ -413,6 +524,7 @@ mrc_status mrc_destroy(mrc_ctx *c)
     if (!c) return MRC_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
+    tune_save(c);
     cudaFree(c->ws);
     for (int p = 0; p < 3; ++p) cudaFree(c->tw[p]);
     if (mrc_status_word() == c->d_status) mrc_set_status_word(nullptr);
@@ -445,6 +557,7 @@ mrc_status mrc_inverse(mrc_ctx *c, int d, int64_t N, const double *A, double *ps
                        void *stream, mrc_report *report)
 {
     if (!c || !A || !psi || !valid_dN(d, N)) return MRC_ERR_INVALID_ARG;
+    TuneScope tscope(c, opt);
     const int prec = opt ? opt->prec : MRC_FP64;
     if (prec != MRC_FP64 && prec != MRC_MIXED) return MRC_ERR_INVALID_ARG;
     int sweeps = opt ? opt->refine_sweeps : 1;
@@ -492,6 +605,7 @@ mrc_status mrc_inverse_batched(mrc_ctx *c, int nmodels, const int *d, const int6
     for (int b = 0; b < nmodels; ++b)
         if (!valid_dN(d[b], N[b]) || !A[b] || !psi[b]) return MRC_ERR_INVALID_ARG;
     if (nmodels == 0) return MRC_OK;
+    TuneScope tscope(c, opt);
     const int prec = opt ? opt->prec : MRC_FP64;
     if (prec != MRC_FP64 && prec != MRC_MIXED) return MRC_ERR_INVALID_ARG;
     int sweeps = opt ? opt->refine_sweeps : 1;
@@ -541,6 +655,17 @@ mrc_status mrc_inverse_batched(mrc_ctx *c, int nmodels, const int *d, const int6
         if (same) { hit = &g; break; }
     }
     if (!hit) {
+        if (c->autotune) {
+            // tune each distinct shape now: the graph capture below cannot time kernels
+            const size_t off = align_up(sizeof(int) * nmodels);
+            std::vector<std::pair<int, int64_t>> seen;
+            for (int b = 0; b < nmodels; ++b) {
+                std::pair<int, int64_t> key{d[b], N[b]};
+                if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
+                seen.push_back(key);
+                pretune_model(c, prec, d[b], N[b], (char *)c->ws + off, total - off, st);
+            }
+        }
         for (int k = 0; k < MRC_BATCH_STREAMS; ++k) {
             if (!c->bst[k]) CK(cudaStreamCreateWithFlags(&c->bst[k], cudaStreamNonBlocking));
             if (!c->bev[k]) CK(cudaEventCreateWithFlags(&c->bev[k], cudaEventDisableTiming));
@@ -548,6 +673,7 @@ mrc_status mrc_inverse_batched(mrc_ctx *c, int nmodels, const int *d, const int6
         cudaStream_t s0 = c->bst[0];
         CK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
         mrc_prof_set_capturing(true);
+        c->capturing = true;
         mrc_status cs = MRC_OK;
         cudaError_t ce = cudaMemsetAsync(status, 0, sizeof(int) * nmodels, s0);
         if (ce == cudaSuccess) ce = cudaEventRecord(c->bev[0], s0);
@@ -563,6 +689,7 @@ mrc_status mrc_inverse_batched(mrc_ctx *c, int nmodels, const int *d, const int6
                 cs = MRC_ERR_CUDA;
         }
         mrc_prof_set_capturing(false);
+        c->capturing = false;
         cudaGraph_t graph = nullptr;
         cudaError_t ee = cudaStreamEndCapture(s0, &graph);
         if (cs != MRC_OK || ee != cudaSuccess) {
@@ -659,6 +786,7 @@ mrc_status mrc_first_entrance(mrc_ctx *c, int d, int64_t N, const double *q, con
                               void *stream)
 {
     if (!c || !q || !D || !alpha_C || !valid_dN(d, N) || nD < 1 || nD >= d) return MRC_ERR_INVALID_ARG;
+    TuneScope tscope(c, opt);
     std::vector<int> inD(d, 0), Ci, Di;
     for (int t = 0; t < nD; ++t) {
         if (D[t] < 0 || D[t] >= d || inD[D[t]]) return MRC_ERR_INVALID_ARG;
@@ -717,6 +845,43 @@ mrc_status mrc_occupation(mrc_ctx *c, int d, int64_t N, const double *P, const d
     }
     cudaSetDevice(c->device);
     CK(mrc_occupation_k(P, d, N, alpha, inB.data(), out, (cudaStream_t)stream));
+    return MRC_OK;
+}
+
+mrc_status mrc_reward(mrc_ctx *c, int d, int cc, int64_t N, const double *psi, const double *r, double *V, int prec,
+                      void *stream)
+{
+    if (!c || !psi || !r || !V || !valid_dN(d, N) || cc < 1 || cc > 512) return MRC_ERR_INVALID_ARG;
+    if (prec != MRC_FP64 && prec != MRC_MIXED) return MRC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaSetDevice(c->device);
+    const int p = prec == MRC_FP64 ? PREC_F64 : PREC_DD;
+    mrc_status s;
+    if ((s = ensure_tw(c, p, st)) != MRC_OK) return s;
+    const size_t E = (size_t)d * d, EV = (size_t)d * cc;
+    if ((s = ensure_ws(c, ws_product(pow2ceil(N), E, EV, EV, p))) != MRC_OK) return s;
+    Arena ar{(char *)c->ws};
+    // V = psi * r: d x d times d x c at every frequency (Eq. (reward))
+    return conv_product(c, ar, p, psi, N, r, N, d, d, cc, N, V, 1.0, 0, 0, false, st);
+}
+
+mrc_status mrc_renewal_visits(mrc_ctx *c, int d, int64_t N, const double *psi, const double *alpha, const int *B,
+                              int nB, double *out, void *stream)
+{
+    if (!c || !psi || !alpha || !B || !out || !valid_dN(d, N) || nB < 0 || nB > d) return MRC_ERR_INVALID_ARG;
+    std::vector<int> inB(d, 0);
+    for (int t = 0; t < nB; ++t) {
+        if (B[t] < 0 || B[t] >= d) return MRC_ERR_INVALID_ARG;
+        inB[B[t]] = 1;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaSetDevice(c->device);
+    const int64_t nch = (N + 1023) / 1024;
+    mrc_status s;
+    if ((s = ensure_ws(c, align_up(sizeof(double) * nch))) != MRC_OK) return s;
+    // alpha psi(k) 1_B per k, then the running sum over k (Eq. (renewal-visits))
+    CK(mrc_occupation_k(psi, d, N, alpha, inB.data(), out, st));
+    CK(mrc_scan_cols(out, 1, N, (double *)c->ws, 1.0, 0.0, st));
     return MRC_OK;
 }
 

@@ -132,16 +132,19 @@ cudaError_t pairmul_launch(const PairArgs &a, cudaStream_t st)
 }
 
 template <class T>
-cudaError_t pairmul_run(const void *zx, const void *zy, void *zc, int64_t M, int r, int m, int c, const void *tw,
+cudaError_t pairmul_run(const void *zx, const void *zy, void *zc, int64_t M, int r, int m, int c, int cfg, const void *tw,
                         int tw_log, cudaStream_t st)
 {
     PairArgs a{};
     a.zx = zx; a.zy = zy; a.zc = zc; a.tw = tw; a.tw_log = tw_log; a.M = M; a.logM = ilog2_i64(M);
     a.npairs = M >= 2 ? M / 2 + 1 : 1;
     a.r = r; a.m = m; a.c = c;
+    // tile configuration: 0 = 16x16 (64 threads), 1 = 32x32 (256), 2 = 64x64 (256);
+    // cfg < 0 picks by the larger output dimension
     const int mx = r > c ? r : c;
-    if (mx <= 16) return pairmul_launch<T, 16, 16, 16, 2, 2>(a, st);
-    if (mx <= 32) return pairmul_launch<T, 32, 32, 16, 2, 2>(a, st);
+    if (cfg < 0) cfg = mx <= 16 ? 0 : (mx <= 32 ? 1 : 2);
+    if (cfg == 0) return pairmul_launch<T, 16, 16, 16, 2, 2>(a, st);
+    if (cfg == 1) return pairmul_launch<T, 32, 32, 16, 2, 2>(a, st);
     return pairmul_launch<T, 64, 64, 8, 4, 4>(a, st);
 }
 
@@ -209,7 +212,12 @@ cudaError_t init_run()
     cudaError_t mrc_pairmul_##SUF(const void *zx, const void *zy, void *zc, int64_t M, int r, int m, int c,   \
                                   const void *tw, int tw_log, cudaStream_t st)                              \
     {                                                                                                       \
-        return pairmul_run<T>(zx, zy, zc, M, r, m, c, tw, tw_log, st);                                      \
+        return pairmul_run<T>(zx, zy, zc, M, r, m, c, -1, tw, tw_log, st);                                  \
+    }                                                                                                       \
+    cudaError_t mrc_pairmul_cfg_##SUF(const void *zx, const void *zy, void *zc, int64_t M, int r, int m,      \
+                                      int c, int cfg, const void *tw, int tw_log, cudaStream_t st)          \
+    {                                                                                                       \
+        return pairmul_run<T>(zx, zy, zc, M, r, m, c, cfg, tw, tw_log, st);                                 \
     }                                                                                                       \
     cudaError_t mrc_pairdiag_##SUF(const void *zx, const void *zy, void *zc, int64_t M, int r, int c,         \
                                    const void *tw, int tw_log, cudaStream_t st)                             \

@@ -86,6 +86,9 @@ void mrc_prof_post(int kclass, cudaStream_t st, double bytes, double flops);
                               void *scratch, const void *tw, int tw_log, cudaStream_t st);            \
     cudaError_t mrc_pairmul_##SUF(const void *zx, const void *zy, void *zc, int64_t M, int r, int m,  \
                                   int c, const void *tw, int tw_log, cudaStream_t st);                \
+    cudaError_t mrc_pairmul_cfg_##SUF(const void *zx, const void *zy, void *zc, int64_t M, int r,     \
+                                      int m, int c, int cfg, const void *tw, int tw_log,              \
+                                      cudaStream_t st);                                               \
     cudaError_t mrc_pairdiag_##SUF(const void *zx, const void *zy, void *zc, int64_t M, int r, int c, \
                                    const void *tw, int tw_log, cudaStream_t st);                      \
     cudaError_t mrc_twiddles_##SUF(void *tw, int tw_log, cudaStream_t st);                            \

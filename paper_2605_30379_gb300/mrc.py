@@ -7,7 +7,8 @@ first call fails loudly if libmrc.so has not been built
 (``python -c "import __graft_entry__ as g; g.build()"``).
 
 Names follow the C ABI: ``inverse``, ``inverse_batched``, ``residual``,
-``transition``, ``first_entrance``, ``occupation``.
+``transition``, ``first_entrance``, ``occupation``, ``reward``,
+``renewal_visits``.
 """
 from __future__ import annotations
 
@@ -75,8 +76,11 @@ def load():
         lib.mrc_transition.argtypes = [P, I, I64, P, P, P, I, P]
         lib.mrc_first_entrance.argtypes = [P, I, I64, P, P, I, P, P, P, P, ctypes.POINTER(_Options), P]
         lib.mrc_occupation.argtypes = [P, I, I64, P, P, P, I, P, P]
+        lib.mrc_reward.argtypes = [P, I, I, I64, P, P, P, I, P]
+        lib.mrc_renewal_visits.argtypes = [P, I, I64, P, P, P, I, P, P]
         for name in ("mrc_create", "mrc_destroy", "mrc_sync_status", "mrc_inverse", "mrc_inverse_batched",
-                     "mrc_residual", "mrc_transition", "mrc_first_entrance", "mrc_occupation"):
+                     "mrc_residual", "mrc_transition", "mrc_first_entrance", "mrc_occupation", "mrc_reward",
+                     "mrc_renewal_visits"):
             getattr(lib, name).restype = I
         _lib = lib
         return lib
@@ -99,6 +103,17 @@ def context(device=None):
         return _ctx[dev]
 
 
+def release():
+    """Destroy the per-device default contexts (frees their workspace and writes
+    the autotuning cache when MRC_AUTOTUNE_CACHE is set); later calls create
+    new ones."""
+    lib = load()
+    with _lock:
+        for dev, h in list(_ctx.items()):
+            lib.mrc_destroy(h)
+            del _ctx[dev]
+
+
 def _stream(stream):
     s = torch.cuda.current_stream() if stream is None else stream
     return ctypes.c_void_p(s.cuda_stream)
@@ -116,11 +131,11 @@ def _ptr(x):
     return ctypes.c_void_p(x.data_ptr()) if x is not None else ctypes.c_void_p(0)
 
 
-def _opts(prec, sweeps, target):
-    return _Options(_PREC[prec], int(sweeps), float(target), 0)
+def _opts(prec, sweeps, target, autotune=False):
+    return _Options(_PREC[prec], int(sweeps), float(target), 1 if autotune else 0)
 
 
-def inverse(A, prec="fp64", sweeps=1, target_residual=0.0, report=False, out=None, stream=None):
+def inverse(A, prec="fp64", sweeps=1, target_residual=0.0, report=False, out=None, stream=None, autotune=False):
     """psi = A^{(-1)} mod x^N (mrc_inverse).  A: CUDA float64 [N, d, d]."""
     A = _seq(A, "A")
     N, d, d2 = A.shape
@@ -129,13 +144,13 @@ def inverse(A, prec="fp64", sweeps=1, target_residual=0.0, report=False, out=Non
     psi = torch.empty_like(A) if out is None else out
     rep = _Report()
     st = load().mrc_inverse(context(A.device.index), d, N, _ptr(A), _ptr(psi),
-                            ctypes.byref(_opts(prec, sweeps, target_residual)), _stream(stream),
+                            ctypes.byref(_opts(prec, sweeps, target_residual, autotune)), _stream(stream),
                             ctypes.byref(rep) if report else None)
     _check(st, "mrc_inverse")
     return (psi, rep.as_dict()) if report else psi
 
 
-def inverse_batched(As, prec="fp64", sweeps=1, outs=None, report=False, stream=None):
+def inverse_batched(As, prec="fp64", sweeps=1, outs=None, report=False, stream=None, autotune=False):
     """mrc_inverse over a list of independent models (one stream, in order)."""
     As = [_seq(a, "A") for a in As]
     outs = [torch.empty_like(a) for a in As] if outs is None else outs
@@ -146,7 +161,7 @@ def inverse_batched(As, prec="fp64", sweeps=1, outs=None, report=False, stream=N
     Pp = (ctypes.c_void_p * n)(*[p.data_ptr() for p in outs])
     reps = (_Report * n)() if report else None
     dev = As[0].device.index if n else None
-    st = load().mrc_inverse_batched(context(dev), n, dv, Nv, Ap, Pp, ctypes.byref(_opts(prec, sweeps, 0.0)),
+    st = load().mrc_inverse_batched(context(dev), n, dv, Nv, Ap, Pp, ctypes.byref(_opts(prec, sweeps, 0.0, autotune)),
                                     _stream(stream), reps)
     _check(st, "mrc_inverse_batched")
     return (outs, [r.as_dict() for r in reps]) if report else outs
@@ -203,6 +218,31 @@ def occupation(P, alpha, B, stream=None):
     Bv = (ctypes.c_int * max(1, len(B)))(*B)
     _check(load().mrc_occupation(context(P.device.index), d, N, _ptr(P), _ptr(alpha), Bv, len(B), _ptr(out),
                                  _stream(stream)), "mrc_occupation")
+    return out
+
+
+def reward(psi, r, prec="fp64", stream=None):
+    """V = psi * r (mrc_reward); r: CUDA float64 [N, d, c]."""
+    psi, r = _seq(psi, "psi"), _seq(r, "r")
+    N, d, _ = psi.shape
+    if r.shape[0] != N or r.shape[1] != d:
+        raise ValueError("r must have shape [N, d, c]")
+    V = torch.empty_like(r)
+    _check(load().mrc_reward(context(psi.device.index), d, r.shape[2], N, _ptr(psi), _ptr(r), _ptr(V), _PREC[prec],
+                             _stream(stream)), "mrc_reward")
+    return V
+
+
+def renewal_visits(psi, alpha, B, stream=None):
+    """N_B(k) = alpha sum_{l<=k} psi(l) I_B 1 (mrc_renewal_visits)."""
+    psi = _seq(psi, "psi")
+    N, d, _ = psi.shape
+    alpha = alpha.to(device=psi.device, dtype=torch.float64).contiguous()
+    out = torch.empty(N, dtype=torch.float64, device=psi.device)
+    B = [int(x) for x in B]
+    Bv = (ctypes.c_int * max(1, len(B)))(*B)
+    _check(load().mrc_renewal_visits(context(psi.device.index), d, N, _ptr(psi), _ptr(alpha), Bv, len(B), _ptr(out),
+                                     _stream(stream)), "mrc_renewal_visits")
     return out
 
 

@@ -296,3 +296,54 @@ def test_fft_bulk_copy_staging_matches_oracle(mrc):
         del os.environ["MRC_FFT_TMA"]
     assert np.abs(p64 - ref).max() <= TOL64
     assert e_rel(pmx, ref) <= TOL_REL
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_reward_matches_oracle(mrc, prec):
+    """V = psi * r with a rectangular reward sequence (Eq. (reward)); the oracle
+    side is its direct convolution, and V must solve V = r + q * V."""
+    rng = np.random.default_rng(42)
+    d, c, N = 6, 3, 700
+    q, _ = synth.weibull_model(d, N, seed=42)
+    psi = oracle.inverse_left(synth.identity_minus(q))
+    r = rng.uniform(0, 1, (N, d, c))
+    ref = oracle.convolve(psi, r)
+    V = mrc.reward(dev(psi), dev(r), prec=prec).cpu().numpy()
+    assert np.abs(V - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max())
+    np.testing.assert_allclose(V, r + oracle.convolve(q, V), atol=1e-9)
+
+
+def test_renewal_visits_matches_oracle(mrc):
+    d, N = 5, 900
+    q, _ = synth.weibull_model(d, N, seed=43)
+    psi = oracle.inverse_left(synth.identity_minus(q))
+    alpha = np.array([0.4, 0.1, 0.1, 0.2, 0.2])
+    ref = oracle.renewal_visits(psi, alpha, [1, 3])
+    got = mrc.renewal_visits(dev(psi), torch.tensor(alpha), [1, 3]).cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+
+
+def test_autotuned_inverse_and_batch(mrc, tmp_path):
+    """autotune=1 times the product-kernel candidates per shape on the call's
+    stream; results stay within the parity gates and the choices are written
+    to MRC_AUTOTUNE_CACHE when the context is destroyed."""
+    import os
+    cache = tmp_path / "tune.txt"
+    os.environ["MRC_AUTOTUNE_CACHE"] = str(cache)
+    try:
+        q, _ = synth.weibull_model(40, 1500, seed=51)
+        A = synth.identity_minus(q)
+        ref = oracle.inverse_left(A)
+        p64 = mrc.inverse(dev(A), prec="fp64", autotune=True).cpu().numpy()
+        pmx = mrc.inverse(dev(A), prec="mixed", autotune=True).cpu().numpy()
+        assert np.abs(p64 - ref).max() <= TOL64
+        assert e_rel(pmx, ref) <= TOL_REL
+        models = synth.batch_models(n=5, seed=52, d_range=(3, 40), logN_range=(7.0, 9.5))
+        outs = mrc.inverse_batched([dev(m["A"]) for m in models], prec="mixed", autotune=True)
+        for m, o in zip(models, outs):
+            assert e_rel(o.cpu().numpy(), oracle.inverse_left(m["A"])) <= TOL_REL
+        mrc.release()
+        lines = cache.read_text().split()
+        assert len(lines) >= 2 and all(int(c) in (0, 1, 2, 3) for c in lines[1::2])
+    finally:
+        del os.environ["MRC_AUTOTUNE_CACHE"]
