@@ -245,6 +245,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-breakdown", action="store_true", help="skip the per-kernel-class timing steps")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="built-in product-kernel choices instead of tuning them during warm-up")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
@@ -289,11 +291,13 @@ def main():
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     stream = torch.cuda.current_stream()
 
+    tune = not args.no_autotune
+
     def step(prec=args.prec):
         if batch:
-            mrc.inverse_batched(As, prec=prec, sweeps=1, outs=psis)
+            mrc.inverse_batched(As, prec=prec, sweeps=1, outs=psis, autotune=tune)
         else:
-            mrc.inverse(As[0], prec=prec, sweeps=1, out=psis[0])
+            mrc.inverse(As[0], prec=prec, sweeps=1, out=psis[0], autotune=tune)
 
     def prof(kclass, fn):
         lib.mrc_profile_begin(kclass)
@@ -400,7 +404,7 @@ def main():
             "value": value, "unit": "coefficients/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+dd" if args.prec == "mixed" else "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "d": d if not batch else "3..48",
+            "config": {"workload": args.workload, "autotune": tune, "d": d if not batch else "3..48",
                        "N": N if not batch else "round(2^U[10,16])", "models": len(As), "prec": args.prec, "sweeps": 1,
                        "l2": (f"inputs ({coeffs * 8 / 1e9:.1f} GB) larger than L2; no flush" if coeffs * 8 > 2e8
                               else "inputs smaller than L2: latency-bound, no flush"),
