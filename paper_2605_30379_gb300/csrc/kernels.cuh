@@ -510,7 +510,10 @@ struct FftEntry {
 template <class T, int OFF, int... L>
 void fft_fill_shifted(FftEntry (*t)[11], std::integer_sequence<int, L...>)
 {
-    constexpr int ECD = sizeof(cx<T>) == 8 ? 16 : 8;
+    #ifndef MRC_F32_EC
+#define MRC_F32_EC 8
+#endif
+    constexpr int ECD = sizeof(cx<T>) == 8 ? MRC_F32_EC : 8;
     ((t[0][OFF + L] = FftEntry{fft_pass_kernel<T, OFF + L, ECD>, FftPlan<T, OFF + L, ECD>::NT}), ...);
     ((t[1][OFF + L] = FftEntry{fft_pass_kernel<T, OFF + L, 4>, FftPlan<T, OFF + L, 4>::NT}), ...);
 }

@@ -29,8 +29,14 @@ template <> constexpr int kclass_fft<float>() { return 2; }
 template <> constexpr int kclass_fft<dd>() { return 3; }
 template <class T> constexpr int kclass_pair() { return kclass_fft<T>() + 3; }
 
+// Entries per CTA of FP32 passes: 8 (64-byte row segments) measured best at
+// d = 64, N = 2^18 -- FP32 FFT 103.5 ms against 111.6 (16) and 163 (4): the
+// smaller CTAs let more of them overlap loads with compute on each SM.
+#ifndef MRC_F32_EC
+#define MRC_F32_EC 8
+#endif
 template <class T>
-constexpr int default_ec() { return sizeof(cx<T>) == 8 ? 16 : 8; }
+constexpr int default_ec() { return sizeof(cx<T>) == 8 ? MRC_F32_EC : 8; }
 
 // entries per CTA: the full default when E allows, else 4 (>= 32-byte row
 // segments; lanes beyond E idle)

@@ -48,8 +48,13 @@ constexpr int OZ_SLICE = OZ_D * OZ_LD;
 #ifndef MRC_OZ_F32_DIGITS
 #define MRC_OZ_F32_DIGITS 5
 #endif
+// (Five double-float digits, 15 pairs, were measured: pairmul_dd 70 -> 62 ms
+// at d = 64, N = 2^18, but the residual error rose from ~1e-13 to ~2e-11.)
+#ifndef MRC_OZ_DD_DIGITS
+#define MRC_OZ_DD_DIGITS 6
+#endif
 template <class T> struct OzP;
-template <> struct OzP<dd> { static constexpr int S = 6, GMIN = 5; };
+template <> struct OzP<dd> { static constexpr int S = MRC_OZ_DD_DIGITS, GMIN = MRC_OZ_DD_DIGITS - 1; };
 template <> struct OzP<float> { static constexpr int S = MRC_OZ_F32_DIGITS, GMIN = MRC_OZ_F32_DIGITS; };
 template <class T>
 constexpr size_t oz_smem() { return (size_t)4 * OzP<T>::S * OZ_SLICE * sizeof(unsigned short) + 4 * OZ_D * sizeof(int); }
@@ -113,6 +118,29 @@ __device__ __forceinline__ float hi_part(float x) { return x; }
 __device__ __forceinline__ float hi_part(dd x) { return x.hi; }
 
 __device__ __forceinline__ void split_digits(dd v, float sc, float (&q)[6]) { digits6(v.hi * sc, v.lo * sc, q); }
+
+// Five digits of a double-float value (weights 2^-8 .. 2^-40), same folding
+// of lo and of the TwoSum error as digits6.
+__device__ __forceinline__ void split_digits(dd v, float sc, float (&q)[5])
+{
+    float x = v.hi * sc, t;
+    t = __fsub_rn(__fadd_rn(x, 49152.0f), 49152.0f);
+    q[4] = t * 256.0f;
+    x = __fsub_rn(x, t);
+    t = __fsub_rn(__fadd_rn(x, 192.0f), 192.0f);
+    q[3] = t * 65536.0f;
+    x = __fsub_rn(x, t);
+    const dd ye = dd_two_sum(x, v.lo * sc);
+    x = ye.hi;
+    t = __fsub_rn(__fadd_rn(x, 0.75f), 0.75f);
+    q[2] = t * 16777216.0f;
+    x = __fsub_rn(x, t);
+    t = __fsub_rn(__fadd_rn(x, 0x1.8p-9f), 0x1.8p-9f);
+    q[1] = t * 0x1p32f;
+    x = __fadd_rn(__fsub_rn(x, t), ye.lo);
+    t = __fsub_rn(__fadd_rn(x, 0x1.8p-17f), 0x1.8p-17f);
+    q[0] = t * 0x1p40f;
+}
 __device__ __forceinline__ void split_digits(float v, float sc, float (&q)[3]) { digits3(v * sc, q); }
 __device__ __forceinline__ void split_digits(float v, float sc, float (&q)[5])
 {
