@@ -39,6 +39,11 @@ struct mrc_ctx {
     int *d_status = nullptr;
     double *d_acc = nullptr;  // [4] norm accumulators
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // streams of the single-model mixed inverse, created on first use: the
+    // FP32 Newton levels on `hi` (highest priority) while the double-float
+    // spectrum of A is computed on `aux` (lowest priority)
+    cudaStream_t aux = nullptr, hi = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     // batching
     cudaStream_t bst[MRC_BATCH_STREAMS] = {};
     cudaEvent_t bev[MRC_BATCH_STREAMS] = {};
@@ -164,15 +169,25 @@ size_t ws_product(int64_t Mr, size_t EX, size_t EY, size_t EC, int prec)
            align_up(mrc_fft_scratch_elems(Mr, (int)emax) * cxb);
 }
 
+// Mixed inverse layout: [Gauss-Jordan work | double-float spectrum of A |
+// its FFT scratch | then either the FP32 Newton buffers or, afterwards,
+// rho_L followed by the residual's two other double-float spectra or the
+// FP32 correction's product buffers].
 size_t ws_inverse(int d, int64_t N, int prec)
 {
     const size_t E = (size_t)d * d;
     if (prec == MRC_FP64) return ws_newton(d, N, PREC_F64);
-    size_t a = ws_newton(d, N, PREC_F32);
-    // Gauss-Jordan scratch stays reserved below the refinement buffers
-    size_t b = align_up(sizeof(double) * 2 * E) + ws_product(pow2ceil(N), E, E, E, PREC_DD) +
-               align_up((size_t)N * E * sizeof(double));
-    return std::max(a, b);
+    const int64_t Mr = pow2ceil(N);
+    const size_t gj = align_up(sizeof(double) * 2 * E);
+    const size_t ahat = align_up((size_t)Mr * E * 16) + align_up(mrc_fft_scratch_elems(Mr, (int)E) * 16);
+    const size_t newton = ws_newton(d, N, PREC_F32) - gj;
+    // rho_L, the FP32 spectrum of psi_0 (hi parts of its double-float one),
+    // then the residual's spectra of psi_0 and of the product (double-float)
+    // or the correction's FP32 spectrum of rho, product and FFT scratch
+    const size_t refine = align_up((size_t)N * E * sizeof(double)) + align_up((size_t)Mr * E * 8) +
+                          std::max(2 * align_up((size_t)Mr * E * 16),
+                                   2 * align_up((size_t)Mr * E * 8) + align_up(mrc_fft_scratch_elems(Mr, (int)E) * 8));
+    return gj + ahat + std::max(newton, refine);
 }
 
 // Square products on the tensor cores: double-float with 32 <= d <= 64 as
@@ -268,9 +283,14 @@ cudaError_t pairmul_any(mrc_ctx *cx, int prec, const void *zx, const void *zy, v
 // C = X * Y truncated to rows [0, N) (linear convolution via L = 2 Mr,
 // Mr = pow2ceil(N)), X: [NX rows][r][m], Y: [NY rows][m][c] real FP64.
 // Output: REAL64 rows [0, N) into `out` with scale s (and +I at row 0 if eye).
+// preX / preT (optional): the spectrum of X already computed into preX (length
+// Mr, EX entries, this precision) and the FFT scratch to use instead of a new
+// one; y_hi (double-float only, optional): also write the hi parts of Y's
+// spectrum there as FP32 complex values.
 mrc_status conv_product(mrc_ctx *c, Arena &ar, int prec, const double *X, int64_t NX, const double *Y, int64_t NY,
                         int r, int m, int cc, int64_t N, double *out, double sign, int eye_d, int add,
-                        bool diag, cudaStream_t st)
+                        bool diag, cudaStream_t st, void *preX = nullptr, void *preT = nullptr,
+                        void *y_hi = nullptr)
 {
     const PrecOps &op = OPS[prec];
     const int64_t Mr = pow2ceil(N);
@@ -278,16 +298,16 @@ mrc_status conv_product(mrc_ctx *c, Arena &ar, int prec, const double *X, int64_
     const size_t EX = diag ? (size_t)r * cc : (size_t)r * m, EY = diag ? (size_t)cc : (size_t)m * cc;
     const size_t EC = (size_t)r * cc;
     const size_t emax = std::max(EX, std::max(EY, EC));
-    void *bX = ar.take(Mr * EX * op.cxb);
+    void *bX = preX ? preX : ar.take(Mr * EX * op.cxb);
     void *bY = ar.take(Mr * EY * op.cxb);
     void *bC = ar.take(Mr * EC * op.cxb);
-    void *bT = ar.take(mrc_fft_scratch_elems(Mr, (int)emax) * op.cxb);
+    void *bT = preT ? preT : ar.take(mrc_fft_scratch_elems(Mr, (int)emax) * op.cxb);
     const void *tw = c->tw[prec];
     FftSrc sx{SRC_REAL64, X, 0, std::min(NX, N), (int)EX, 0};
     FftSrc sy{SRC_REAL64, Y, 0, std::min(NY, N), (int)EY, 0};
     FftDst dx{DST_CPLX, bX, (int)EX, 0, 0, 0, 1.0, 0};
-    FftDst dy{DST_CPLX, bY, (int)EY, 0, 0, 0, 1.0, 0};
-    CK(op.fft(sx, dx, Mr, (int)EX, -1, bT, tw, MRC_TW_LOG, st));
+    FftDst dy{DST_CPLX, bY, (int)EY, 0, 0, 0, 1.0, 0, y_hi};
+    if (!preX) CK(op.fft(sx, dx, Mr, (int)EX, -1, bT, tw, MRC_TW_LOG, st));
     CK(op.fft(sy, dy, Mr, (int)EY, -1, bT, tw, MRC_TW_LOG, st));
     if (diag) CK(op.pairdiag(bX, bY, bC, Mr, r, cc, tw, MRC_TW_LOG, st));
     else CK(pairmul_any(c, prec, bX, bY, bC, Mr, r, m, cc, tw, st));
@@ -339,29 +359,64 @@ mrc_status newton_levels(mrc_ctx *c, Arena &ar, int prec, int d, int64_t N, cons
 
 bool valid_dN(int d, int64_t N) { return d >= 1 && d <= 512 && N >= 1 && N <= ((int64_t)1 << 20); }
 
+// Mixed precision: the double-float spectrum of A that every residual sweep
+// uses depends on A alone.  With `split` (single-model calls) it is computed
+// on the context's low-priority stream while the FP32 Newton levels run on
+// its high-priority one -- the double-float FFT keeps the FP32 pipes busy,
+// the FP32 passes mostly wait on memory, and the priorities let each Newton
+// kernel's CTAs go first instead of queueing behind the FFT's -- and `st`
+// waits for both before the first residual.  Without `split` (batched calls,
+// whose models already overlap on several streams) everything runs on `st`.
 mrc_status inverse_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A, double *psi, int prec, int sweeps,
-                        int *levels, cudaStream_t st, int *status = nullptr)
+                        int *levels, cudaStream_t st, int *status = nullptr, bool split = false)
 {
     const size_t E = (size_t)d * d;
     double *gjw = (double *)ar.take(sizeof(double) * 2 * E);
-    CK(mrc_gauss_jordan(A, psi, gjw, d, status ? status : c->d_status, st));
+    void *ahat = nullptr, *ascr = nullptr;
+    cudaStream_t sn = st;  // Newton levels
+    if (prec == MRC_MIXED) {
+        const int64_t Mr = pow2ceil(N);
+        ahat = ar.take((size_t)Mr * E * 16);
+        ascr = ar.take(mrc_fft_scratch_elems(Mr, (int)E) * 16);
+        cudaStream_t sa = st;
+        if (split) {
+            CK(cudaEventRecord(c->ev_fork, st));
+            CK(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+            CK(cudaStreamWaitEvent(c->hi, c->ev_fork, 0));
+            sa = c->aux;
+            sn = c->hi;
+        }
+        FftSrc sx{SRC_REAL64, A, 0, N, (int)E, 0};
+        FftDst dx{DST_CPLX, ahat, (int)E, 0, 0, 0, 1.0, 0};
+        CK(OPS[PREC_DD].fft(sx, dx, Mr, (int)E, -1, ascr, c->tw[PREC_DD], MRC_TW_LOG, sa));
+        if (split) CK(cudaEventRecord(c->ev_join, c->aux));
+    }
+    CK(mrc_gauss_jordan(A, psi, gjw, d, status ? status : c->d_status, sn));
     const int64_t m0 = base_size(d, N);
-    CK(mrc_base_case(A, psi, d, m0, st));
+    CK(mrc_base_case(A, psi, d, m0, sn));
     const size_t mark = ar.off;
-    mrc_status s = newton_levels(c, ar, prec == MRC_FP64 ? PREC_F64 : PREC_F32, d, N, A, psi, m0, levels, st);
+    mrc_status s = newton_levels(c, ar, prec == MRC_FP64 ? PREC_F64 : PREC_F32, d, N, A, psi, m0, levels, sn);
     if (s != MRC_OK) return s;
     ar.off = mark;
     if (prec == MRC_MIXED) {
+        if (split) {
+            CK(cudaEventRecord(c->ev_join2, c->hi));
+            CK(cudaStreamWaitEvent(st, c->ev_join2, 0));
+            CK(cudaStreamWaitEvent(st, c->ev_join, 0));
+        }
         double *rho = (double *)ar.take(sizeof(double) * (size_t)N * E);
+        void *psi_hat32 = ar.take((size_t)pow2ceil(N) * E * 8);
         const size_t mark2 = ar.off;
         for (int sw = 0; sw < sweeps; ++sw) {
             ar.off = mark2;
-            // rho_L = e0 - A * psi in double-float (Proposition 2.6)
-            s = conv_product(c, ar, PREC_DD, A, N, psi, N, d, d, d, N, rho, -1.0, d, 0, false, st);
+            // rho_L = e0 - A * psi in double-float (Proposition 2.6); the FFT
+            // of psi also leaves the FP32 spectrum the correction needs
+            s = conv_product(c, ar, PREC_DD, A, N, psi, N, d, d, d, N, rho, -1.0, d, 0, false, st, ahat, ascr,
+                             psi_hat32);
             if (s != MRC_OK) return s;
             ar.off = mark2;
             // psi <- psi + psi * rho_L (Eq. (newton) from a full-length approximation), FP32 product
-            s = conv_product(c, ar, PREC_F32, psi, N, rho, N, d, d, d, N, psi, 1.0, 0, 1, false, st);
+            s = conv_product(c, ar, PREC_F32, psi, N, rho, N, d, d, d, N, psi, 1.0, 0, 1, false, st, psi_hat32);
             if (s != MRC_OK) return s;
         }
     }
@@ -532,6 +587,11 @@ mrc_status mrc_destroy(mrc_ctx *c)
     cudaFree(c->d_acc);
     cudaEventDestroy(c->ev0);
     cudaEventDestroy(c->ev1);
+    if (c->aux) cudaStreamDestroy(c->aux);
+    if (c->hi) cudaStreamDestroy(c->hi);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_join2) cudaEventDestroy(c->ev_join2);
     for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
     for (int k = 0; k < MRC_BATCH_STREAMS; ++k) {
         if (c->bst[k]) cudaStreamDestroy(c->bst[k]);
@@ -575,7 +635,16 @@ mrc_status mrc_inverse(mrc_ctx *c, int d, int64_t N, const double *A, double *ps
     Arena ar{(char *)c->ws};
     int levels = 0;
     if (report) CK(cudaEventRecord(c->ev0, st));
-    s = inverse_impl(c, ar, d, N, A, psi, prec, sweeps, &levels, st);
+    if (prec == MRC_MIXED && !c->aux) {
+        int least = 0, greatest = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        CK(cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, least));
+        CK(cudaStreamCreateWithPriority(&c->hi, cudaStreamNonBlocking, greatest));
+        CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming));
+    }
+    s = inverse_impl(c, ar, d, N, A, psi, prec, sweeps, &levels, st, nullptr, prec == MRC_MIXED);
     if (s != MRC_OK) return s;
     if (report) {
         CK(cudaEventRecord(c->ev1, st));

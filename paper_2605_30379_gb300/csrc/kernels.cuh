@@ -63,6 +63,8 @@ __device__ __forceinline__ void fft_store(const FftArgs &a, int64_t k, int e, cx
         cx<T> *d = reinterpret_cast<cx<T> *>(a.dst);
         if (a.dst_scale != 1.0) v = scale_out(a, v);
         d[k * (int64_t)a.dst_ld + e] = v;
+        if constexpr (__is_same(T, dd))
+            if (a.dst2) reinterpret_cast<cx<float> *>(a.dst2)[k * (int64_t)a.dst_ld + e] = {v.re.hi, v.im.hi};
         return;
     }
     // real rows 2k (re) and 2k+1 (im), window [lo, hi); the power-of-two
@@ -148,6 +150,17 @@ __device__ __forceinline__ void dft_r(cx<T> *v)
     else dft8<T, INV>(v);
 }
 
+// Entries per CTA of the passes: for 8-byte complex values (FP32) 8, i.e.
+// 64-byte row segments -- at d = 64, N = 2^18 the FP32 FFT took 103.5 ms
+// with 8, 111.6 ms with 16 and 163 ms with 4 (smaller CTAs overlap loads
+// and compute better; 32-byte segments halve the useful bytes per request);
+// for 16-byte values (FP64, double-float) 8.
+#ifndef MRC_F32_EC
+#define MRC_F32_EC 8
+#endif
+template <class T>
+constexpr int fft_default_ec() { return sizeof(cx<T>) == 8 ? MRC_F32_EC : 8; }
+
 // Compile-time plan of one pass: R = 2^LOGR points split into in-CTA stages
 // of radix 2^FIRST then 8, 8, ...; EC entries per CTA; NT threads, each
 // holding EPT points in registers.
@@ -165,9 +178,15 @@ struct FftPlan {
     static constexpr int LEC = EC == 1 ? 0 : EC == 2 ? 1 : EC == 4 ? 2 : EC == 8 ? 3 : 4;
 };
 
-template <class T, int LOGR, int EC, int S, bool INV>
+// One in-CTA stage S.  Stage 0 reads its points from global memory, from sm
+// (bulk-copy staging) or, with PIPE, from the staging buffer stg filled by
+// fft_pipe_prefetch (complex rows [R][EC], or for a real source the two real
+// rows of each packed point, [R][2][EC] doubles; inter-pass twiddles in spt
+// not yet conjugated).
+template <class T, int LOGR, int EC, int S, bool INV, bool PIPE = false>
 __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<T> *stw, const cx<T> *spt,
-                                          int64_t j, int e0, int ecount, int64_t base_out, bool staged)
+                                          int64_t j, int e0, int ecount, int64_t base_out, bool staged,
+                                          const void *stg = nullptr)
 {
     using P = FftPlan<T, LOGR, EC>;
     constexpr int R = P::R, NT = P::NT;
@@ -186,7 +205,18 @@ __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<
 #pragma unroll
         for (int q = 0; q < r; ++q) {
             const int rho = b + q * (R / r);
-            if constexpr (FIRST) {
+            if constexpr (FIRST && PIPE) {
+                cx<T> x;
+                if (a.src_mode == SRC_CPLX) {
+                    x = reinterpret_cast<const cx<T> *>(stg)[rho * EC + e];
+                } else {
+                    const double *s2 = reinterpret_cast<const double *>(stg) + rho * 2 * EC;
+                    x = c_from_d<T>(s2[e], s2[EC + e]);
+                }
+                if (a.src_neg) x = c_neg(x);
+                if (a.Ns > 1) x = c_mul(x, INV ? c_conj(spt[rho]) : spt[rho]);
+                v[u][q] = x;
+            } else if constexpr (FIRST) {
                 cx<T> x = c_zero<T>();
                 if (staged) {
                     x = sm[rho * EC + e];  // rows past the valid range were zero-filled
@@ -201,7 +231,7 @@ __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<
             }
         }
     }
-    if (!FIRST || staged) __syncthreads();  // every read of sm done before the in-place writes
+    if (!FIRST || (staged && !PIPE)) __syncthreads();  // every read of sm done before the in-place writes
 #pragma unroll
     for (int u = 0; u < UPT; ++u) {
         const int b = (tid + u * NT) >> P::LEC;
@@ -335,6 +365,125 @@ __global__ void __launch_bounds__(FftPlan<T, LOGR, EC>::NT) fft_pass_kernel(FftA
 {
     if (a.dir > 0) fft_pass_body<T, LOGR, EC, true>(a);
     else fft_pass_body<T, LOGR, EC, false>(a);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent pipelined pass.  The same Stockham pass as fft_pass_kernel, but
+// each CTA loops over tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... with
+// the entry chunk fastest (CTAs running together read and write whole rows),
+// and while it computes tile t the row segments and inter-pass twiddles of
+// its next tile are already on their way into a staging buffer (cp.async,
+// 16-byte pieces; rows past the valid range are zero-filled by a copy of
+// source size 0).  Requires E % EC == 0, a 16-byte aligned source with a
+// row stride that is a multiple of 16 bytes, and two passes or more
+// (NSTAGE > 1: stage 0 ends with a barrier, after which the staging buffer is
+// free for the next tile).
+__device__ __forceinline__ void cp_async16(unsigned dst, const void *src, unsigned src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(unsigned dst, const void *src)
+{
+    static_assert(BYTES == 8 || BYTES == 16, "cp.async size");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(dst), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// staging bytes per tile: complex source R*EC values, real source 2*R*EC doubles
+template <class T, int LOGR, int EC>
+struct FftPipeSmem {
+    static constexpr size_t R = (size_t)1 << LOGR;
+    static constexpr size_t head = (R * EC + 2 * R) * sizeof(cx<T>);  // sm, stw, spt
+    static constexpr size_t stg_cplx = R * EC * sizeof(cx<T>);
+    static constexpr size_t stg_real = 2 * R * EC * sizeof(double);
+};
+
+template <class T, int LOGR, int EC>
+__device__ __forceinline__ void fft_pipe_prefetch(const FftArgs &a, unsigned char *stg, cx<T> *spt, int64_t t,
+                                                  int nchunk)
+{
+    using P = FftPlan<T, LOGR, EC>;
+    constexpr int R = P::R, NT = P::NT;
+    const int tid = threadIdx.x;
+    const int64_t j = t / nchunk;
+    const int e0 = (int)(t - j * nchunk) * EC;
+    const int64_t stride = a.M >> LOGR;
+    const unsigned sb = (unsigned)__cvta_generic_to_shared(stg);
+    const char *g = reinterpret_cast<const char *>(a.src);
+    if (a.src_mode == SRC_CPLX) {
+        constexpr int CPR = EC * (int)sizeof(cx<T>) / 16;  // 16-byte pieces per row segment
+        static_assert(CPR >= 1, "row segment below 16 bytes");
+        for (int c = tid; c < R * CPR; c += NT) {
+            const int rho = c / CPR, q = c - (c / CPR) * CPR;
+            const int64_t k = j + (int64_t)rho * stride;
+            const bool ok = k < a.src_nvalid;
+            const char *src = ok ? g + ((a.src_row0 + k) * (int64_t)a.src_ld + e0) * (int64_t)sizeof(cx<T>) + q * 16 : g;
+            cp_async16(sb + 16u * c, src, ok ? 16u : 0u);
+        }
+    } else {
+        constexpr int CPR = EC * 8 / 16;  // pieces per real row segment
+        static_assert(CPR >= 1, "row segment below 16 bytes");
+        for (int c = tid; c < 2 * R * CPR; c += NT) {
+            const int rh = c / CPR, q = c - (c / CPR) * CPR;  // rh = 2 rho + h
+            const int64_t r = 2 * (j + (int64_t)(rh >> 1) * stride) + (rh & 1);
+            const bool ok = r < a.src_nvalid;
+            const char *src = ok ? g + ((a.src_row0 + r) * (int64_t)a.src_ld + e0) * 8 + q * 16 : g;
+            cp_async16(sb + 16u * c, src, ok ? 16u : 0u);
+        }
+    }
+    if (a.Ns > 1) {
+        const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
+        const int sh = a.tw_log - (a.logNs + LOGR);
+        const int64_t jm = j & (a.Ns - 1);
+        for (int k = tid; k < R; k += NT)
+            cp_async_small<(int)sizeof(cx<T>)>((unsigned)__cvta_generic_to_shared(spt + k), tw + ((jm * k) << sh));
+    }
+    cp_async_commit();
+}
+
+template <class T, int LOGR, int EC, bool INV>
+__device__ __forceinline__ void fft_pipe_body(const FftArgs &a)
+{
+    using P = FftPlan<T, LOGR, EC>;
+    static_assert(P::NSTAGE > 1, "pipelined pass needs a barrier after stage 0");
+    constexpr int R = P::R;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);  // [R][EC] exchange
+    cx<T> *stw = sm + R * EC;                         // [R]  W_R^t
+    cx<T> *spt = stw + R;                             // [R]  inter-pass twiddles of the staged tile
+    unsigned char *stg = smem_raw + FftPipeSmem<T, LOGR, EC>::head;
+    const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
+    const int tid = threadIdx.x;
+    const int nchunk = a.E / EC;
+    const int64_t ntiles = (a.M >> LOGR) * nchunk;
+    for (int k = tid; k < R; k += P::NT) {
+        cx<T> w = tw[(int64_t)k << (a.tw_log - LOGR)];
+        stw[k] = INV ? c_conj(w) : w;
+    }
+    int64_t t = blockIdx.x;
+    if (t < ntiles) fft_pipe_prefetch<T, LOGR, EC>(a, stg, spt, t, nchunk);
+    for (; t < ntiles; t += gridDim.x) {
+        cp_async_wait_all();
+        __syncthreads();
+        const int64_t j = t / nchunk;
+        const int e0 = (int)(t - j * nchunk) * EC;
+        const int64_t jm = j & (a.Ns - 1);
+        const int64_t base_out = (j >> a.logNs << (a.logNs + LOGR)) + jm;
+        fft_stage<T, LOGR, EC, 0, INV, true>(a, sm, stw, spt, j, e0, EC, base_out, false, stg);
+        if (t + gridDim.x < ntiles) fft_pipe_prefetch<T, LOGR, EC>(a, stg, spt, t + gridDim.x, nchunk);
+        fft_stage<T, LOGR, EC, 1, INV>(a, sm, stw, spt, j, e0, EC, base_out, false);
+        if constexpr (P::NSTAGE > 2) fft_stage<T, LOGR, EC, 2, INV>(a, sm, stw, spt, j, e0, EC, base_out, false);
+        if constexpr (P::NSTAGE > 3) fft_stage<T, LOGR, EC, 3, INV>(a, sm, stw, spt, j, e0, EC, base_out, false);
+    }
+}
+
+template <class T, int LOGR, int EC>
+__global__ void __launch_bounds__(FftPlan<T, LOGR, EC>::NT) fft_pipe_kernel(FftArgs a)
+{
+    if (a.dir > 0) fft_pipe_body<T, LOGR, EC, true>(a);
+    else fft_pipe_body<T, LOGR, EC, false>(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -499,21 +648,29 @@ __global__ void twiddle_kernel(cx<T> *tw, int log)
 
 // ---------------------------------------------------------------------------
 // Launch table of the FFT pass instantiations: entry [ec_index][logR], where
-// ec_index 0 is the default entries per CTA (16 for 8-byte complex, 8 for
-// 16-byte) and 1 is 4 entries per CTA.
+// ec_index 0 is the default entries per CTA (MRC_F32_EC for 8-byte complex
+// values, 8 for 16-byte ones) and 1 is 4 entries per CTA.  Default entries of
+// radix 2^5 .. 2^10 in the FP32 and double-float precisions also carry the
+// persistent pipelined pass (pipe; null elsewhere).
 using FftKernel = void (*)(FftArgs);
 struct FftEntry {
     FftKernel fn;
     int nt;
+    FftKernel pipe;
 };
+
+template <class T, int L, int EC>
+constexpr FftKernel fft_pipe_or_null()
+{
+    if constexpr (L >= 5 && !__is_same(T, double)) return fft_pipe_kernel<T, L, EC>;
+    else return nullptr;
+}
 
 template <class T, int OFF, int... L>
 void fft_fill_shifted(FftEntry (*t)[11], std::integer_sequence<int, L...>)
 {
-    #ifndef MRC_F32_EC
-#define MRC_F32_EC 8
-#endif
-    constexpr int ECD = sizeof(cx<T>) == 8 ? MRC_F32_EC : 8;
-    ((t[0][OFF + L] = FftEntry{fft_pass_kernel<T, OFF + L, ECD>, FftPlan<T, OFF + L, ECD>::NT}), ...);
-    ((t[1][OFF + L] = FftEntry{fft_pass_kernel<T, OFF + L, 4>, FftPlan<T, OFF + L, 4>::NT}), ...);
+    constexpr int ECD = fft_default_ec<T>();
+    ((t[0][OFF + L] = FftEntry{fft_pass_kernel<T, OFF + L, ECD>, FftPlan<T, OFF + L, ECD>::NT,
+                               fft_pipe_or_null<T, OFF + L, ECD>()}), ...);
+    ((t[1][OFF + L] = FftEntry{fft_pass_kernel<T, OFF + L, 4>, FftPlan<T, OFF + L, 4>::NT, nullptr}), ...);
 }

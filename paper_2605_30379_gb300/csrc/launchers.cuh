@@ -5,6 +5,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <utility>
 #include "kernels.cuh"
 
@@ -29,14 +30,8 @@ template <> constexpr int kclass_fft<float>() { return 2; }
 template <> constexpr int kclass_fft<dd>() { return 3; }
 template <class T> constexpr int kclass_pair() { return kclass_fft<T>() + 3; }
 
-// Entries per CTA of FP32 passes: 8 (64-byte row segments) measured best at
-// d = 64, N = 2^18 -- FP32 FFT 103.5 ms against 111.6 (16) and 163 (4): the
-// smaller CTAs let more of them overlap loads with compute on each SM.
-#ifndef MRC_F32_EC
-#define MRC_F32_EC 8
-#endif
 template <class T>
-constexpr int default_ec() { return sizeof(cx<T>) == 8 ? MRC_F32_EC : 8; }
+constexpr int default_ec() { return fft_default_ec<T>(); }
 
 // entries per CTA: the full default when E allows, else 4 (>= 32-byte row
 // segments; lanes beyond E idle)
@@ -52,6 +47,50 @@ size_t fft_smem_bytes(int logR, int ec)
 
 template <class T>
 int ec_index(int ec) { return ec == default_ec<T>() ? 0 : 1; }
+
+template <class T>
+size_t fft_pipe_smem_bytes(int logR, int ec, int src_mode)
+{
+    const size_t R = (size_t)1 << logR;
+    const size_t stg = src_mode == SRC_CPLX ? R * ec * sizeof(cx<T>) : 2 * R * ec * sizeof(double);
+    return (R * ec + 2 * R) * sizeof(cx<T>) + stg;
+}
+
+// The persistent pipelined pass (fft_pipe_kernel) runs a pass of a two-pass
+// transform when its instantiation exists, whole chunks cover E, the source
+// rows are 16-byte aligned for cp.async, and MRC_FFT_PIPE allows this
+// precision: "1" = FP32, "all" = FP32 and double-float, unset or "0" = never.
+// Off by default: at d = 64, N = 2^18 it measured slower than one tile per
+// CTA (FP32 FFT 104 -> 109 ms, double-float 113 -> 125 ms).
+template <class T>
+bool pipe_eligible(const FftArgs &a, const FftEntry &k, int np)
+{
+    const char *v = getenv("MRC_FFT_PIPE");
+    const int mode = (!v || !v[0] || v[0] == '0') ? 0 : v[0] == 'a' ? 2 : 1;
+    if (!k.pipe || np < 2 || a.tma || mode == 0) return false;
+    if (sizeof(cx<T>) != 8 && mode < 2) return false;
+    if (a.ec != default_ec<T>() || (a.E % a.ec) != 0) return false;
+    if (fft_pipe_smem_bytes<T>(a.logR, a.ec, a.src_mode) > 200 * 1024) return false;
+    const size_t rowb = (size_t)a.src_ld * (a.src_mode == SRC_CPLX ? sizeof(cx<T>) : sizeof(double));
+    return (rowb % 16) == 0 && (((uintptr_t)a.src) % 16) == 0;
+}
+
+// CTAs of the pipelined pass resident on the whole device (occupancy x SMs),
+// cached per radix and source kind for the current device.
+template <class T>
+int64_t pipe_resident_ctas(const FftEntry &k, int logR, int src_mode, size_t smem)
+{
+    static int cache[11][2] = {};
+    int &c = cache[logR][src_mode == SRC_CPLX ? 0 : 1];
+    if (c == 0) {
+        int dev = 0, nsm = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k.pipe, k.nt, smem);
+        c = std::max(1, nsm * std::max(per, 1));
+    }
+    return c;
+}
 
 // Radix plan: one pass up to 2^10, else two passes of sizes 2^ceil(l/2), 2^floor(l/2).
 inline int fft_plan(int logM, int *logRs)
@@ -93,6 +132,7 @@ cudaError_t fft_run(const FftSrc &src, const FftDst &dst, int64_t M, int E, int 
         if (ps == np - 1) {
             a.dst_mode = dst.mode; a.dst = dst.ptr; a.dst_ld = dst.ld; a.dst_lo = dst.lo; a.dst_hi = dst.hi;
             a.dst_row0 = dst.row0; a.dst_scale = dst.scale; a.dst_eye_d = dst.eye_d;
+            a.dst2 = (std::is_same<T, dd>::value && dst.mode == DST_CPLX) ? dst.ptr2 : nullptr;
         } else {
             a.dst_mode = DST_CPLX; a.dst = scratch; a.dst_ld = sld; a.dst_lo = 0; a.dst_hi = 0; a.dst_row0 = 0;
             a.dst_scale = 1.0; a.dst_eye_d = 0;
@@ -113,11 +153,18 @@ cudaError_t fft_run(const FftSrc &src, const FftDst &dst, int64_t M, int E, int 
         double rd, wr;
         if (a.src_mode == SRC_REAL64) rd = (double)std::min<int64_t>(a.src_nvalid, 2 * M) * E * 8.0;
         else rd = (double)std::min<int64_t>(a.src_nvalid, M) * E * sizeof(cx<T>);
-        if (a.dst_mode == DST_CPLX) wr = (double)M * E * sizeof(cx<T>);
+        if (a.dst_mode == DST_CPLX) wr = (double)M * E * (sizeof(cx<T>) + (a.dst2 ? 8 : 0));
         else wr = (double)(a.dst_hi - a.dst_lo) * E * 8.0 * (a.dst_mode == DST_REAL64_ADD ? 2.0 : 1.0);
         const FftEntry &k = fft_table<T>()[ec_index<T>(ec)][a.logR];
         mrc_prof_pre(kclass_fft<T>(), st);
-        k.fn<<<grid, k.nt, fft_smem_bytes<T>(a.logR, ec), st>>>(a);
+        if (pipe_eligible<T>(a, k, np)) {
+            const size_t smem = fft_pipe_smem_bytes<T>(a.logR, ec, a.src_mode);
+            const int64_t ntiles = (M >> a.logR) * (int64_t)(E / ec);
+            const int64_t g = std::min<int64_t>(ntiles, pipe_resident_ctas<T>(k, a.logR, a.src_mode, smem));
+            k.pipe<<<(unsigned)g, k.nt, smem, st>>>(a);
+        } else {
+            k.fn<<<grid, k.nt, fft_smem_bytes<T>(a.logR, ec), st>>>(a);
+        }
         mrc_prof_post(kclass_fft<T>(), st, rd + wr, 5.0 * (double)M * a.logR * E);
         logNs += a.logR;
     }
@@ -189,6 +236,10 @@ cudaError_t init_run()
         for (int l = 0; l < 11; ++l) {
             cudaError_t e = cudaFuncSetAttribute(t[i][l].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             if (e != cudaSuccess) return e;
+            if (t[i][l].pipe) {
+                e = cudaFuncSetAttribute(t[i][l].pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                if (e != cudaSuccess) return e;
+            }
         }
     return cudaSuccess;
 }

@@ -34,6 +34,7 @@ struct FftArgs {
     double dst_scale;       // signed power of two
     float dst_scale_f;      // the same, for the FP32-based precisions
     int dst_eye_d;          // REAL64*: if > 0 add 1 to the diagonal of real row 0 (d = this)
+    void *dst2;             // double-float DST_CPLX only: also write the hi parts here as FP32 complex (or null)
     int tma;                // CPLX source staged into shared memory by bulk copies (first stage)
     int *status;            // device status word: MRC_ERR_TIMEOUT (6) if a bounded wait gives up
 };
@@ -64,6 +65,7 @@ struct FftDst {
     int64_t lo, hi, row0;
     double scale;
     int eye_d;
+    void *ptr2 = nullptr;  // double-float DST_CPLX: FP32 copy of the hi parts (FftArgs::dst2)
 };
 
 // prof.cu: device status word that bounded in-kernel waits report timeouts to

@@ -298,6 +298,32 @@ def test_fft_bulk_copy_staging_matches_oracle(mrc):
     assert e_rel(pmx, ref) <= TOL_REL
 
 
+def test_fft_pipelined_pass_matches_plain_pass(mrc):
+    """The persistent cp.async-pipelined pass (opt-in: MRC_FFT_PIPE=1 for
+    two-pass FP32 transforms, =all adds double-float) does the
+    same arithmetic as the one-tile-per-CTA pass: the mixed inverse must agree
+    between the settings and stay within the parity gate.  N = 5000 gives
+    transforms of 2^12 and 2^13 points (two passes), a partial last Newton
+    level and a ragged valid-row range; d = 6 leaves E = 36 (not a multiple
+    of 8) and d = 12 takes E = 144 through the pipelined pass."""
+    import os
+    for d in (6, 12):
+        q, _ = synth.weibull_model(d, 5000, seed=61 + d)
+        A = synth.identity_minus(q)
+        ref = oracle.inverse_left(A)
+        out = {}
+        for mode in ("0", "1", "all"):
+            os.environ["MRC_FFT_PIPE"] = mode
+            try:
+                out[mode] = mrc.inverse(dev(A), prec="mixed").cpu().numpy()
+                mrc.sync_status()
+            finally:
+                del os.environ["MRC_FFT_PIPE"]
+        for mode, got in out.items():
+            assert e_rel(got, ref) <= TOL_REL, (d, mode)
+            assert np.abs(got - out["0"]).max() <= 1e-13, (d, mode)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_reward_matches_oracle(mrc, prec):
     """V = psi * r with a rectangular reward sequence (Eq. (reward)); the oracle
