@@ -77,58 +77,63 @@ __device__ __forceinline__ dd dd_fma(dd a, dd b, dd c)
 // pipe.  Magnitudes below 2^-126 are flushed to a signed zero: every use here
 // compares absolute errors far above that.
 
-// binary64 -> nearest binary32 (ties to even); exponents outside the normal
-// binary32 range go through the hardware conversion.
+// binary64 -> nearest binary32 (ties to even).  Outside the normal binary32
+// range: below it a signed zero, above it a signed infinity (NaN stays a
+// quiet NaN) -- selected with integer operations too, so that no predicated
+// FP64 instruction is left in the FFT kernels that call this per element.
 __device__ __forceinline__ float f64_to_f32_rn(double x)
 {
     const long long b = __double_as_longlong(x);
     const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+    const unsigned sg = hw & 0x80000000u;
     const int ex = (int)((hw >> 20) & 0x7ffu);
-    if (ex < 897 || ex > 1150) return ex < 897 ? __int_as_float((int)(hw & 0x80000000u)) : __double2float_rn(x);
     const unsigned m23 = ((hw & 0xfffffu) << 3) | (lw >> 29);
     const unsigned rem = lw & 0x1fffffffu;
-    const unsigned up = (rem > 0x10000000u) | ((rem == 0x10000000u) & m23);
-    const unsigned fb = (hw & 0x80000000u) | ((((unsigned)(ex - 896)) << 23) + m23 + (up & 1u));
+    const unsigned up = ((rem > 0x10000000u) | ((rem == 0x10000000u) & m23)) & 1u;
+    unsigned fb = sg | ((((unsigned)(ex - 896)) << 23) + m23 + up);  // a carry may round up to infinity
+    const unsigned big = sg | 0x7f800000u | ((ex == 2047 && ((hw & 0xfffffu) | lw)) ? 0x00400000u : 0u);
+    fb = ex < 897 ? sg : fb;
+    fb = ex > 1150 ? big : fb;
     return __uint_as_float(fb);
 }
 
-// binary64 -> double-float (hi = nearest binary32, lo = the rest rounded to binary32)
+// binary64 -> double-float (hi = nearest binary32, lo = the rest rounded to
+// binary32; lo flushes to zero below 2^-126), integer operations only.
 __device__ __forceinline__ dd dd_from_double(double x)
 {
     const long long b = __double_as_longlong(x);
     const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+    const unsigned sg = hw & 0x80000000u;
     const int ex = (int)((hw >> 20) & 0x7ffu);
-    if (ex < 897 || ex > 1150) {
-        if (ex < 897) return {__int_as_float((int)(hw & 0x80000000u)), 0.0f};
-        float hi = __double2float_rn(x);
-        return {hi, __double2float_rn(x - (double)hi)};
-    }
     const unsigned m23 = ((hw & 0xfffffu) << 3) | (lw >> 29);
     const unsigned rem = lw & 0x1fffffffu;
     const unsigned up = ((rem > 0x10000000u) | ((rem == 0x10000000u) & m23)) & 1u;
-    const unsigned fb = (hw & 0x80000000u) | ((((unsigned)(ex - 896)) << 23) + m23 + up);
-    // x - hi = (rem - up 2^29) 2^(ex - 1075), sign of x
-    float lo = 0.0f;
-    if (ex >= 949) {
-        const int r = (int)rem - (int)(up << 29);
-        lo = __int2float_rn(r) * __uint_as_float(((unsigned)(ex - 948)) << 23);
-        if (hw & 0x80000000u) lo = -lo;
-    }
+    unsigned fb = sg | ((((unsigned)(ex - 896)) << 23) + m23 + up);
+    // x - hi = (rem - up 2^29) 2^(ex - 1075), with the sign of x
+    const int r = (int)rem - (int)(up << 29);
+    float lo = __int2float_rn(sg ? -r : r) * __uint_as_float(((unsigned)max(ex - 948, 1)) << 23);
+    lo = (ex >= 949 && ex <= 1150) ? lo : 0.0f;
+    const unsigned big = sg | 0x7f800000u | ((ex == 2047 && ((hw & 0xfffffu) | lw)) ? 0x00400000u : 0u);
+    fb = ex < 897 ? sg : fb;
+    fb = ex > 1150 ? big : fb;
     return {__uint_as_float(fb), lo};
 }
 
-// binary32 -> binary64, exact (binary32 subnormals flush to zero)
+// binary32 -> binary64, exact (binary32 subnormals flush to zero; infinities
+// and NaNs keep their class), integer operations only
 __device__ __forceinline__ double f32_to_f64(float f)
 {
     const unsigned u = __float_as_uint(f);
-    const unsigned e8 = (u >> 23) & 0xffu;
-    if (e8 == 0u) return __longlong_as_double((long long)(u & 0x80000000u) << 32);
-    if (e8 == 0xffu) return (double)f;
-    const unsigned hw = (u & 0x80000000u) | ((e8 + 896u) << 20) | ((u & 0x7fffffu) >> 3);
-    const unsigned lw = (u & 0x7fffffu) << 29;
+    const unsigned e8 = (u >> 23) & 0xffu, sg = u & 0x80000000u, m = u & 0x7fffffu;
+    const unsigned e11 = e8 == 0xffu ? 0x7ffu : e8 + 896u;
+    unsigned hw = sg | (e11 << 20) | (m >> 3), lw = m << 29;
+    hw = e8 == 0u ? sg : hw;
+    lw = e8 == 0u ? 0u : lw;
     return __longlong_as_double(((long long)hw << 32) | lw);
 }
 
+// the sum of two exact binary64 conversions is exact (at most 48 significant
+// bits): one FP64 add, used only where a double-float result is stored as FP64
 __device__ __forceinline__ double dd_to_double(dd x) { return f32_to_f64(x.hi) + f32_to_f64(x.lo); }
 
 // ---------------------------------------------------------------------------
@@ -149,6 +154,8 @@ struct Ar<double> {
     static __device__ __forceinline__ double from_d(double x) { return x; }
     static __device__ __forceinline__ double to_d(double x) { return x; }
     static __device__ __forceinline__ double zero() { return 0.0; }
+    static __device__ __forceinline__ double one() { return 1.0; }
+    static __device__ __forceinline__ double rsqrt2() { return 0.70710678118654752440; }
 };
 
 template <>
@@ -163,6 +170,8 @@ struct Ar<float> {
     static __device__ __forceinline__ float from_d(double x) { return f64_to_f32_rn(x); }
     static __device__ __forceinline__ double to_d(float x) { return f32_to_f64(x); }
     static __device__ __forceinline__ float zero() { return 0.0f; }
+    static __device__ __forceinline__ float one() { return 1.0f; }
+    static __device__ __forceinline__ float rsqrt2() { return 0x1.6a09e6p-1f; }
 };
 
 template <>
@@ -181,6 +190,9 @@ struct Ar<dd> {
     static __device__ __forceinline__ dd from_d(double x) { return dd_from_double(x); }
     static __device__ __forceinline__ double to_d(dd x) { return dd_to_double(x); }
     static __device__ __forceinline__ dd zero() { return {0.0f, 0.0f}; }
+    static __device__ __forceinline__ dd one() { return {1.0f, 0.0f}; }
+    // sqrt(1/2) = hi + lo within 4e-16
+    static __device__ __forceinline__ dd rsqrt2() { return {0x1.6a09e6p-1f, 0x1.9fcef4p-27f}; }
 };
 
 // ---------------------------------------------------------------------------

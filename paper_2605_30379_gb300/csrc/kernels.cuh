@@ -16,6 +16,7 @@
 // exactly the L/2+1 frequencies of the half spectrum (Eq. (fft-convolution)
 // restricted to Hermitian spectra).
 #pragma once
+#include <type_traits>
 #include <utility>
 
 #include "arith.cuh"
@@ -30,22 +31,23 @@
 // shared-memory exchange per stage, and writes element f to
 // (j/Ns)*Ns*R + (j mod Ns) + f*Ns.  After the last pass the output is in
 // natural frequency order.
-template <class T>
+template <class T, int SRC>
 __device__ __forceinline__ cx<T> fft_load(const FftArgs &a, int64_t k, int e)
 {
-    if (a.src_mode == SRC_CPLX) {
+    if constexpr (SRC == SRC_CPLX) {
         if (k >= a.src_nvalid) return c_zero<T>();
         const cx<T> *s = reinterpret_cast<const cx<T> *>(a.src);
         cx<T> v = s[(a.src_row0 + k) * (int64_t)a.src_ld + e];
         return a.src_neg ? c_neg(v) : v;
+    } else {
+        // packed pair of real rows 2k, 2k+1
+        const double *s = reinterpret_cast<const double *>(a.src);
+        const int64_t r0 = 2 * k, r1 = 2 * k + 1;
+        const double x0 = (r0 < a.src_nvalid) ? s[(a.src_row0 + r0) * (int64_t)a.src_ld + e] : 0.0;
+        const double x1 = (r1 < a.src_nvalid) ? s[(a.src_row0 + r1) * (int64_t)a.src_ld + e] : 0.0;
+        cx<T> v = c_from_d<T>(x0, x1);
+        return a.src_neg ? c_neg(v) : v;
     }
-    // SRC_REAL64: packed pair of real rows 2k, 2k+1
-    const double *s = reinterpret_cast<const double *>(a.src);
-    int64_t r0 = 2 * k, r1 = 2 * k + 1;
-    double x0 = (r0 < a.src_nvalid) ? s[(a.src_row0 + r0) * (int64_t)a.src_ld + e] : 0.0;
-    double x1 = (r1 < a.src_nvalid) ? s[(a.src_row0 + r1) * (int64_t)a.src_ld + e] : 0.0;
-    cx<T> v = c_from_d<T>(x0, x1);
-    return a.src_neg ? c_neg(v) : v;
 }
 
 // multiply by the (signed power of two) output scale in the working precision
@@ -56,31 +58,37 @@ __device__ __forceinline__ cx<T> scale_out(const FftArgs &a, cx<T> v)
     else return {Ar<T>::scal_f(v.re, a.dst_scale_f), Ar<T>::scal_f(v.im, a.dst_scale_f)};
 }
 
-template <class T>
+// Store of one output point; DST is the destination mode, fixed per launch
+// (the stage branches on it once, outside its per-point loop).  No FP64
+// instruction is issued here for the FP32-based precisions except the add
+// of DST_REAL64_ADD and the final FP64 add of a double-float value.
+template <class T, int DST>
 __device__ __forceinline__ void fft_store(const FftArgs &a, int64_t k, int e, cx<T> v)
 {
-    if (a.dst_mode == DST_CPLX) {
+    if constexpr (DST == DST_CPLX) {
         cx<T> *d = reinterpret_cast<cx<T> *>(a.dst);
-        if (a.dst_scale != 1.0) v = scale_out(a, v);
+        if (a.dst_scaled) v = scale_out(a, v);
         d[k * (int64_t)a.dst_ld + e] = v;
         if constexpr (__is_same(T, dd))
             if (a.dst2) reinterpret_cast<cx<float> *>(a.dst2)[k * (int64_t)a.dst_ld + e] = {v.re.hi, v.im.hi};
-        return;
-    }
-    // real rows 2k (re) and 2k+1 (im), window [lo, hi); the power-of-two
-    // scale is applied in the working precision (exact) before conversion
-    double *d = reinterpret_cast<double *>(a.dst);
-    v = scale_out(a, v);
-    const T vals[2] = {v.re, v.im};
+    } else {
+        // real rows 2k (re) and 2k+1 (im), window [lo, hi); the power-of-two
+        // scale and the identity of row 0 are applied in the working
+        // precision before the conversion
+        double *d = reinterpret_cast<double *>(a.dst);
+        v = scale_out(a, v);
+        const T vals[2] = {v.re, v.im};
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        int64_t r = 2 * k + h;
-        if (r < a.dst_lo || r >= a.dst_hi) continue;
-        double x = Ar<T>::to_d(vals[h]);
-        if (a.dst_eye_d > 0 && r == 0 && (e % (a.dst_eye_d + 1)) == 0) x += 1.0;
-        double *p = d + (a.dst_row0 + (r - a.dst_lo)) * (int64_t)a.dst_ld + e;
-        if (a.dst_mode == DST_REAL64_ADD) *p += x;
-        else *p = x;
+        for (int h = 0; h < 2; ++h) {
+            const int64_t r = 2 * k + h;
+            if (r < a.dst_lo || r >= a.dst_hi) continue;
+            T y = vals[h];
+            if (a.dst_eye_d > 0 && r == 0 && (e % (a.dst_eye_d + 1)) == 0) y = Ar<T>::add(y, Ar<T>::one());
+            const double x = Ar<T>::to_d(y);
+            double *p = d + (a.dst_row0 + (r - a.dst_lo)) * (int64_t)a.dst_ld + e;
+            if constexpr (DST == DST_REAL64_ADD) *p += x;
+            else *p = x;
+        }
     }
 }
 
@@ -115,7 +123,7 @@ __device__ __forceinline__ void dft4(cx<T> *v)
 template <class T, bool INV>
 __device__ __forceinline__ void dft8(cx<T> *v)
 {
-    const T s = Ar<T>::from_d(0.70710678118654752440);
+    const T s = Ar<T>::rsqrt2();
     cx<T> a[4], b[4];
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
@@ -198,6 +206,29 @@ __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<
     constexpr bool FIRST = (S == 0), LAST = (S == P::NSTAGE - 1);
     const int tid = threadIdx.x;
     cx<T> v[UPT][r];
+    // first stage from global memory: one loop per source mode
+    auto load_global = [&](auto src_tag) {
+        constexpr int SRC = decltype(src_tag)::value;
+#pragma unroll
+        for (int u = 0; u < UPT; ++u) {
+            const int unit = tid + u * NT;
+            const int e = unit & (EC - 1), b = unit >> P::LEC;
+#pragma unroll
+            for (int q = 0; q < r; ++q) {
+                const int rho = b + q * (R / r);
+                cx<T> x = c_zero<T>();
+                if (e < ecount) x = fft_load<T, SRC>(a, j + (int64_t)rho * (a.M >> LOGR), e0 + e);
+                if (a.Ns > 1) x = c_mul(x, spt[rho]);
+                v[u][q] = x;
+            }
+        }
+    };
+    if constexpr (FIRST && !PIPE) {
+        if (!staged) {
+            if (a.src_mode == SRC_CPLX) load_global(std::integral_constant<int, SRC_CPLX>{});
+            else load_global(std::integral_constant<int, SRC_REAL64>{});
+        }
+    }
 #pragma unroll
     for (int u = 0; u < UPT; ++u) {
         const int unit = tid + u * NT;
@@ -217,15 +248,12 @@ __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<
                 if (a.Ns > 1) x = c_mul(x, INV ? c_conj(spt[rho]) : spt[rho]);
                 v[u][q] = x;
             } else if constexpr (FIRST) {
-                cx<T> x = c_zero<T>();
                 if (staged) {
-                    x = sm[rho * EC + e];  // rows past the valid range were zero-filled
+                    cx<T> x = sm[rho * EC + e];  // rows past the valid range were zero-filled
                     if (a.src_neg) x = c_neg(x);
-                } else if (e < ecount) {
-                    x = fft_load<T>(a, j + (int64_t)rho * (a.M >> LOGR), e0 + e);
+                    if (a.Ns > 1) x = c_mul(x, spt[rho]);
+                    v[u][q] = x;
                 }
-                if (a.Ns > 1) x = c_mul(x, spt[rho]);
-                v[u][q] = x;
             } else {
                 v[u][q] = sm[rho * EC + e];
             }
@@ -242,22 +270,33 @@ __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<
         }
         dft_r<T, INV, LR>(v[u]);
     }
+    auto store_global = [&](auto dst_tag) {
+        constexpr int DST = decltype(dst_tag)::value;
 #pragma unroll
-    for (int u = 0; u < UPT; ++u) {
-        const int unit = tid + u * NT;
-        const int e = unit & (EC - 1), b = unit >> P::LEC;
-        const int ob = ((b >> LNS) << (LNS + LR)) + (b & (Ns - 1));
+        for (int u = 0; u < UPT; ++u) {
+            const int unit = tid + u * NT;
+            const int e = unit & (EC - 1), b = unit >> P::LEC;
+            const int ob = ((b >> LNS) << (LNS + LR)) + (b & (Ns - 1));
 #pragma unroll
-        for (int q = 0; q < r; ++q) {
-            const int o = ob + q * Ns;
-            if constexpr (LAST) {
-                if (e < ecount) fft_store<T>(a, base_out + (int64_t)o * a.Ns, e0 + e, v[u][q]);
-            } else {
-                sm[o * EC + e] = v[u][q];
-            }
+            for (int q = 0; q < r; ++q)
+                if (e < ecount) fft_store<T, DST>(a, base_out + (int64_t)(ob + q * Ns) * a.Ns, e0 + e, v[u][q]);
         }
+    };
+    if constexpr (LAST) {
+        if (a.dst_mode == DST_CPLX) store_global(std::integral_constant<int, DST_CPLX>{});
+        else if (a.dst_mode == DST_REAL64) store_global(std::integral_constant<int, DST_REAL64>{});
+        else store_global(std::integral_constant<int, DST_REAL64_ADD>{});
+    } else {
+#pragma unroll
+        for (int u = 0; u < UPT; ++u) {
+            const int unit = tid + u * NT;
+            const int e = unit & (EC - 1), b = unit >> P::LEC;
+            const int ob = ((b >> LNS) << (LNS + LR)) + (b & (Ns - 1));
+#pragma unroll
+            for (int q = 0; q < r; ++q) sm[(ob + q * Ns) * EC + e] = v[u][q];
+        }
+        __syncthreads();
     }
-    if constexpr (!LAST) __syncthreads();
 }
 
 // Bulk-copy staging of a complex source (TMA, cp.async.bulk): warp 0 copies

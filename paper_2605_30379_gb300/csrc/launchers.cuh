@@ -138,6 +138,7 @@ cudaError_t fft_run(const FftSrc &src, const FftDst &dst, int64_t M, int E, int 
             a.dst_scale = 1.0; a.dst_eye_d = 0;
         }
         a.dst_scale_f = (float)a.dst_scale;
+        a.dst_scaled = a.dst_scale != 1.0;
         // bulk-copy staging of a complex source: 16-byte aligned row segments
         // of whole chunks, and at least one warp besides the copying warp
         {

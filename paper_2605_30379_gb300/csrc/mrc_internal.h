@@ -33,6 +33,7 @@ struct FftArgs {
     int64_t dst_row0;       // REAL64*: destination row of real row dst_lo
     double dst_scale;       // signed power of two
     float dst_scale_f;      // the same, for the FP32-based precisions
+    int dst_scaled;         // dst_scale != 1 (decided on the host: no FP64 compare in the kernels)
     int dst_eye_d;          // REAL64*: if > 0 add 1 to the diagonal of real row 0 (d = this)
     void *dst2;             // double-float DST_CPLX only: also write the hi parts here as FP32 complex (or null)
     int tma;                // CPLX source staged into shared memory by bulk copies (first stage)
