@@ -204,7 +204,7 @@ bool env_is_simt(const char *name)
 cudaError_t launch_choice(int prec, int choice, const void *zx, const void *zy, void *zc, int64_t M, int r, int m,
                           int c, const void *tw, cudaStream_t st)
 {
-    if (choice == 3) return mrc_pairmul_dd_ozaki(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
+    if (choice == 3) return mrc_pairmul_dd_tc(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
     return OPS[prec].pairmul_cfg(zx, zy, zc, M, r, m, c, choice, tw, MRC_TW_LOG, st);
 }
 
@@ -264,6 +264,8 @@ cudaError_t pairmul_any(mrc_ctx *cx, int prec, const void *zx, const void *zy, v
     const char *fv = getenv("MRC_F32_PRODUCT");
     if (prec == PREC_F32 && newton_level && mrc_tf32x3_supported(r, m, c) && fv && strcmp(fv, "tf32x3") == 0)
         return mrc_pairmul_f32_tf32x3(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
+    if (prec == PREC_F32 && mrc_tc_supported(r, m, c) && fv && strcmp(fv, "tc") == 0)
+        return mrc_pairmul_f32_tc(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
     // FP32 products stay on the FP32 pipes unless MRC_F32_PRODUCT=tensor: at
     // d <= 64 the per-entry digit work outweighs the tensor-core savings
     // (d = 64, N = 2^18: 118 ms on the tensor cores against 54.5 ms)
@@ -274,8 +276,11 @@ cudaError_t pairmul_any(mrc_ctx *cx, int prec, const void *zx, const void *zy, v
         const int ch = tuned_choice(cx, prec, zx, zy, zc, M, r, m, c, tw, st);
         if (ch >= 0) return launch_choice(prec, ch, zx, zy, zc, M, r, m, c, tw, st);
     }
-    if (prec == PREC_DD && mrc_ozaki_supported(r, m, c) && !env_is_simt("MRC_DD_PRODUCT"))
-        return mrc_pairmul_dd_ozaki(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
+    if (prec == PREC_DD && mrc_tc_supported(r, m, c) && !env_is_simt("MRC_DD_PRODUCT")) {
+        const char *dv = getenv("MRC_DD_PRODUCT");
+        if (dv && strcmp(dv, "mma") == 0) return mrc_pairmul_dd_ozaki(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
+        return mrc_pairmul_dd_tc(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
+    }
     return OPS[prec].pairmul(zx, zy, zc, M, r, m, c, tw, MRC_TW_LOG, st);
 }
 
@@ -558,6 +563,7 @@ mrc_status mrc_create(mrc_ctx **out, int device, size_t max_workspace_bytes)
         if (OPS[p].init() != cudaSuccess) return MRC_ERR_CUDA;
     if (mrc_ozaki_init() != cudaSuccess) return MRC_ERR_CUDA;
     if (mrc_tf32x3_init() != cudaSuccess) return MRC_ERR_CUDA;
+    if (mrc_tc_init() != cudaSuccess) return MRC_ERR_CUDA;
     mrc_ctx *c = new mrc_ctx();
     c->device = device;
     c->cap = max_workspace_bytes;

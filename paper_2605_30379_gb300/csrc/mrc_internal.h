@@ -112,6 +112,14 @@ cudaError_t mrc_pairmul_dd_ozaki(const void *zx, const void *zy, void *zc, int64
 cudaError_t mrc_pairmul_f32_ozaki(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw,
                                   int tw_log, cudaStream_t st);
 
+// ozaki_tc.cu: the same digit products on the tcgen05 tensor cores (TMEM accumulators)
+bool mrc_tc_supported(int r, int m, int c);
+cudaError_t mrc_tc_init(void);
+cudaError_t mrc_pairmul_dd_tc(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
+                              cudaStream_t st);
+cudaError_t mrc_pairmul_f32_tc(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
+                               cudaStream_t st);
+
 // tf32x3.cu: FP32 square products (16 <= d <= 64) as three TF32 tensor-core products
 bool mrc_tf32x3_supported(int r, int m, int c);
 cudaError_t mrc_tf32x3_init(void);

@@ -1,0 +1,495 @@
+// ozaki_tc.cu -- per-frequency complex matrix products of the FFT-Newton path
+// (Eq. (fft-convolution): C(phi) = X(phi) Y(phi) at every frequency of the
+// half spectrum) as exact digit products on the fifth-generation tensor
+// cores: tcgen05.mma, BF16 operands in shared memory, FP32 accumulators in
+// tensor memory (TMEM).  Square d x d with 32 <= d <= 64 (padded to 64).
+//
+// For the frequency pair {f, M-f} one CTA forms, at each frequency phi,
+//     D1 = [X_r; X_i] . Y_r,    D2 = [X_r; X_i] . Y_i        (128 x 64 each)
+//     C_r = D1[0:64] - D2[64:128],    C_i = D2[0:64] + D1[64:128].
+// Every real product is a sum over digit pairs (s, t) (digits.cuh): the
+// rows of [X_r; X_i] are scaled by 2^-sigma_i and the columns of Y by
+// 2^-tau_j, split into S balanced base-256 digits, and stored as S digit
+// tiles A_s (128 x 64, MN-major) and S tiles each for Y_r and Y_i (64 x 64,
+// K-major).  All pairs of one weight group g = s + t >= GMIN accumulate into
+// one 64-column FP32 accumulator in TMEM -- exact, since a group holds at
+// most 6 pairs of 64-term dot products of digits <= 128 (below 2^23).  The
+// group sums are then scaled by their powers of two (exact) and added top
+// group first in the working precision: a compensated double-float sum
+// (TwoSum of the high parts, error below 2^-48 of the magnitudes) for the
+// residual product, plain FP32 for the FP32 one.  Nothing here converts to
+// or from 64-bit integers: on this GPU those conversions share the narrow
+// FP64 pipe, and an int64 fold of the same sums kept it 47% busy.
+//
+// Schedule per frequency: all threads split X and Y into digit tiles; one
+// thread issues the MMAs of D1 (every pair, four K = 16 steps each, M = 128,
+// N = 64) and commits them to an mbarrier; all threads wait (bounded), read
+// the accumulators with tcgen05.ld and fold them; the same for D2; D1 and D2
+// then meet in shared memory (the digit tiles are free by then) and each
+// thread forms 8 complex outputs.  C(f) is stored unmerged and read back by
+// the same thread once C(M-f) is known, when both are merged into the packed
+// output spectrum (the real-FFT merge of kernels.cuh).  The kernel is
+// persistent: CTA b takes pairs b, b + grid, ...
+//
+// A bounded wait that gives up sets MRC_ERR_TIMEOUT in the status word; the
+// CTA then waits (bounded) for its MMAs in flight, frees its TMEM and exits.
+#include "digits.cuh"
+
+namespace {
+
+using namespace mrc_digits;
+
+constexpr int TC_THREADS = 512;
+constexpr int TC_A_TILE = 128 * 64 * 2;  // bytes of one [X_r; X_i] digit tile
+constexpr int TC_B_TILE = 64 * 64 * 2;   // bytes of one Y_r or Y_i digit tile
+constexpr int TC_XLD = 65;               // row length (values) of the D1 / D2 exchange
+constexpr unsigned TC_TMEM_COLS = 512;
+constexpr int TC_SPIN = 1 << 24;
+
+template <class T>
+__host__ __device__ constexpr size_t tc_tiles() { return (size_t)OzP<T>::S * (TC_A_TILE + 2 * TC_B_TILE); }
+template <class T>
+__host__ __device__ constexpr size_t tc_smem() { return tc_tiles<T>() + 4 * 64 * sizeof(int); }
+static_assert((size_t)2 * 128 * TC_XLD * sizeof(dd) <= (size_t)5 * (TC_A_TILE + 2 * TC_B_TILE), "exchange fits the tiles");
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Byte offset of (m, k) in an MN-major tile: 8 consecutive m in 16 bytes,
+// core matrices of 8 k rows, k groups 128 bytes apart, m groups 1024 apart.
+__device__ __forceinline__ int mn_off(int m, int k) { return (m >> 3) * 1024 + (k >> 3) * 128 + (k & 7) * 16 + (m & 7) * 2; }
+// Byte offset of (n, k) in a K-major tile: 8 consecutive k in 16 bytes, core
+// matrices of 8 n rows, k groups 128 bytes apart, n groups 1024 apart.
+__device__ __forceinline__ int k_off(int n, int k) { return (n >> 3) * 1024 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2; }
+
+// Shared-memory matrix descriptor: start address, leading-dimension byte
+// offset 128 (next 8-element K group), stride byte offset 1024 (next 8 rows
+// of M or N), the fixed 0b001 at bits 46-48, no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(unsigned addr)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9, 10-12 = 1), A MN-major (bit 15), B K-major, N >> 3 at bit 17,
+// M >> 4 at bit 24: M = 128, N = 64.
+constexpr unsigned TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(unsigned dtm, uint64_t ad, uint64_t bd, unsigned acc)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtm),
+                 "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_commit(unsigned mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// bounded wait for the completion of phase `parity` of an mbarrier
+__device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity)
+{
+    for (int it = 0; it < TC_SPIN; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// 32 TMEM lanes x 16 consecutive 32-bit columns: thread `lane` of the warp
+// receives lane (base lane + lane), columns col .. col + 15.
+__device__ __forceinline__ void tc_ld16(unsigned taddr, unsigned (&r)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+// MMAs of one product D = [X_r; X_i] . B over every kept digit pair: group
+// g accumulates in TMEM columns 64 (g - GMIN) .. +63 (the first MMA of a
+// group overwrites, the rest accumulate).
+template <int S, int GMIN>
+__device__ __forceinline__ void tc_issue(unsigned tmem, unsigned a0, unsigned b0)
+{
+    for (int g = GMIN; g <= 2 * (S - 1); ++g) {
+        const unsigned dcol = tmem + (unsigned)(g - GMIN) * 64u;
+        unsigned acc = 0;
+        for (int s = max(0, g - (S - 1)); s <= min(S - 1, g); ++s) {
+            const int t = g - s;
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                tc_mma(dcol, tc_desc(a0 + s * TC_A_TILE + ks * 256), tc_desc(b0 + t * TC_B_TILE + ks * 256), acc);
+                acc = 1;
+            }
+        }
+    }
+}
+
+// value + v for a float v: one TwoSum of the high parts, lo parts added once
+// (the sloppy double-float add of arith.cuh with a float operand)
+__device__ __forceinline__ dd tc_add(dd a, float v)
+{
+    const dd s = dd_two_sum(a.hi, v);
+    return dd_fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ float tc_add(float a, float v) { return __fadd_rn(a, v); }
+
+// Fold the NG group accumulators of TMEM lanes 32 q + lane, columns
+// cb .. cb + 15: sum over g of acc_g 2^(8 (g - NG + 1)), top group first
+// (every term an exact FP32 value).
+template <class T, int NG>
+__device__ __forceinline__ void tc_fold(unsigned tmem, int q, int cb, T (&out)[16])
+{
+#pragma unroll
+    for (int g = NG - 1; g >= 0; --g) {
+        unsigned r[16];
+        tc_ld16(tmem + ((unsigned)(32 * q) << 16) + (unsigned)(g * 64 + cb), r);
+        const float w = __uint_as_float((unsigned)(127 - 8 * (NG - 1 - g)) << 23);  // 2^(8 (g - NG + 1))
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const float v = __uint_as_float(r[c]) * w;
+            if (g == NG - 1) {
+                if constexpr (__is_same(T, dd)) out[c] = dd{v, 0.0f};
+                else out[c] = v;
+            } else {
+                out[c] = tc_add(out[c], v);
+            }
+        }
+    }
+}
+
+// BF16 bits of two exact small integers (|q| <= 128 has at most 8
+// significant bits, so the high half of the binary32 is the BF16 value),
+// packed low | high
+__device__ __forceinline__ unsigned tc_pack2(float lo, float hi)
+{
+    return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+}
+
+__device__ __forceinline__ dd tc_scale(dd x, int e) { return {scale2(x.hi, e), scale2(x.lo, e)}; }
+__device__ __forceinline__ float tc_scale(float x, int e) { return scale2(x, e); }
+
+// Digit tiles of X(phi) (phi: packed rows ra, partner rb, twiddle w): thread
+// (m8 = tid / 64, k = tid % 64) splits the 8 entries X[8 m8 .. 8 m8 + 7][k]
+// (lanes read consecutive k: coalesced) and writes, per digit, 16 bytes of
+// 8 consecutive rows into the MN-major tile A_s (rows i: real part, rows
+// 64 + i: imaginary part).
+template <class T>
+__device__ __forceinline__ void tc_split_x(const PairArgs &a, unsigned char *sA, const int *sig, int64_t ra,
+                                           int64_t rb, cx<T> w)
+{
+    constexpr int S = OzP<T>::S;
+    const cx<T> *ZX = reinterpret_cast<const cx<T> *>(a.zx);
+    const int d = a.r;
+    const int64_t E = (int64_t)d * d;
+    const int k = threadIdx.x & 63, m8 = threadIdx.x >> 6;
+    unsigned wr[S][4], wi[S][4];
+    float pr[S], pi[S];  // digits of the even entry of each pair
+#pragma unroll
+    for (int ii = 0; ii < 8; ++ii) {
+        const int i = 8 * m8 + ii;
+        float qr[S], qi[S];
+        if (i < d && k < d) {
+            const int64_t e = (int64_t)i * d + k;
+            const cx<T> x = split_real(ZX[ra * E + e], ZX[rb * E + e], w);
+            const float sc = pow2f(-sig[i]);
+            split_digits(x.re, sc, qr);
+            split_digits(x.im, sc, qi);
+        } else {
+#pragma unroll
+            for (int s = 0; s < S; ++s) qr[s] = qi[s] = 0.0f;
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            if (ii & 1) {
+                wr[s][ii >> 1] = tc_pack2(pr[s], qr[s]);
+                wi[s][ii >> 1] = tc_pack2(pi[s], qi[s]);
+            } else {
+                pr[s] = qr[s];
+                pi[s] = qi[s];
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        unsigned char *t = sA + s * TC_A_TILE;
+        *reinterpret_cast<uint4 *>(t + mn_off(8 * m8, k)) = make_uint4(wr[s][0], wr[s][1], wr[s][2], wr[s][3]);
+        *reinterpret_cast<uint4 *>(t + mn_off(64 + 8 * m8, k)) = make_uint4(wi[s][0], wi[s][1], wi[s][2], wi[s][3]);
+    }
+}
+
+// Digit tiles of Y(phi): thread (k8 = tid / 64, j = tid % 64) splits
+// Y[8 k8 .. 8 k8 + 7][j] (lanes read consecutive j: coalesced) and writes,
+// per digit, 16 bytes of 8 consecutive k into the K-major tiles of Y_r and
+// Y_i (row n = j).
+template <class T>
+__device__ __forceinline__ void tc_split_y(const PairArgs &a, unsigned char *sBr, unsigned char *sBi, const int *tau,
+                                           int64_t ra, int64_t rb, cx<T> w)
+{
+    constexpr int S = OzP<T>::S;
+    const cx<T> *ZY = reinterpret_cast<const cx<T> *>(a.zy);
+    const int d = a.r;
+    const int64_t E = (int64_t)d * d;
+    const int j = threadIdx.x & 63, k8 = threadIdx.x >> 6;
+    unsigned wr[S][4], wi[S][4];
+    float pr[S], pi[S];
+    const float sc = j < d ? pow2f(-tau[j]) : 0.0f;
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+        const int k = 8 * k8 + kk;
+        float qr[S], qi[S];
+        if (k < d && j < d) {
+            const int64_t e = (int64_t)k * d + j;
+            const cx<T> y = split_real(ZY[ra * E + e], ZY[rb * E + e], w);
+            split_digits(y.re, sc, qr);
+            split_digits(y.im, sc, qi);
+        } else {
+#pragma unroll
+            for (int s = 0; s < S; ++s) qr[s] = qi[s] = 0.0f;
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            if (kk & 1) {
+                wr[s][kk >> 1] = tc_pack2(pr[s], qr[s]);
+                wi[s][kk >> 1] = tc_pack2(pi[s], qi[s]);
+            } else {
+                pr[s] = qr[s];
+                pi[s] = qi[s];
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        *reinterpret_cast<uint4 *>(sBr + s * TC_B_TILE + k_off(j, 8 * k8)) =
+            make_uint4(wr[s][0], wr[s][1], wr[s][2], wr[s][3]);
+        *reinterpret_cast<uint4 *>(sBi + s * TC_B_TILE + k_off(j, 8 * k8)) =
+            make_uint4(wi[s][0], wi[s][1], wi[s][2], wi[s][3]);
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(TC_THREADS, 1) oztc_pairmul_kernel(PairArgs a, int *status)
+{
+    constexpr int S = OzP<T>::S, GMIN = OzP<T>::GMIN, NG = 2 * (S - 1) - GMIN + 1;
+    static_assert(NG * 64 <= (int)TC_TMEM_COLS, "group accumulators fit in TMEM");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *sA = smem;                 // [S] 128 x 64 MN-major
+    unsigned char *sBr = sA + S * TC_A_TILE;  // [S] 64 x 64 K-major (Y_r)
+    unsigned char *sBi = sBr + S * TC_B_TILE; // [S] 64 x 64 K-major (Y_i)
+    T *xs = reinterpret_cast<T *>(smem);      // D1 | D2 exchange (reuses the tiles)
+    unsigned *bx = reinterpret_cast<unsigned *>(smem + tc_tiles<T>());
+    unsigned *by = bx + 64;
+    int *sig = reinterpret_cast<int *>(by + 64);
+    int *tau = sig + 64;
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ unsigned tslot;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned mb = smem_u32(&mbar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tslot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = tslot;
+    unsigned parity = 0;
+    bool failed = false;
+
+    const cx<T> *ZX = reinterpret_cast<const cx<T> *>(a.zx);
+    const cx<T> *ZY = reinterpret_cast<const cx<T> *>(a.zy);
+    cx<T> *ZC = reinterpret_cast<cx<T> *>(a.zc);
+    const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
+    const int d = a.r;
+    const int64_t E = (int64_t)d * d, M = a.M;
+    const int q = warp & 3, cb = (warp >> 2) * 16;  // TMEM lanes 32 q .., columns cb .. cb + 15
+
+    for (int64_t p = blockIdx.x; p < a.npairs && !failed; p += gridDim.x) {
+        const int64_t f = p, gL = M - p, gZ = gL & (M - 1);
+        const cx<T> wf = tw[f << (a.tw_log - a.logM - 1)];
+        const cx<T> wg = c_neg(c_conj(wf));
+        const bool two = (gZ != f);
+        const int nfreq = (gL == f) ? 1 : 2;  // p = M/2 pairs with itself
+
+        // ---- row bounds of X and column bounds of Y over both frequencies:
+        // |Xh(f)|, |Xh(g)| <= |Z(f)| + |Z(g)| entrywise
+        for (int t = tid; t < 128; t += TC_THREADS) bx[t] = 0u;
+        __syncthreads();
+        {
+            const int k = tid & 63;
+            float my = 0.0f;
+            for (int t = tid; t < 64 * 64; t += TC_THREADS) {
+                const int i = t >> 6;
+                float mx = 0.0f;
+                if (i < d && k < d) {
+                    const int64_t e = (int64_t)i * d + k;
+                    const cx<T> xa = ZX[f * E + e], xb = ZX[gZ * E + e];
+                    const cx<T> ya = ZY[f * E + e], yb = ZY[gZ * E + e];
+                    mx = fabsf(hi_part(xa.re)) + fabsf(hi_part(xa.im)) + fabsf(hi_part(xb.re)) +
+                         fabsf(hi_part(xb.im));
+                    my = fmaxf(my, fabsf(hi_part(ya.re)) + fabsf(hi_part(ya.im)) + fabsf(hi_part(yb.re)) +
+                                       fabsf(hi_part(yb.im)));
+                }
+                const unsigned wmx = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));  // one row per warp
+                if (lane == 0) atomicMax(&bx[i], wmx);
+            }
+            atomicMax(&by[k], __float_as_uint(my));
+        }
+        __syncthreads();
+        if (tid < 64) {
+            sig[tid] = scale_exp(__uint_as_float(bx[tid]));
+            tau[tid] = scale_exp(__uint_as_float(by[tid]));
+        }
+        __syncthreads();
+
+        for (int phase = 0; phase < nfreq && !failed; ++phase) {
+            const int64_t ra = phase == 0 ? f : gZ, rb = phase == 0 ? gZ : f;
+            const cx<T> w = phase == 0 ? wf : wg;
+            tc_split_x<T>(a, sA, sig, ra, rb, w);
+            tc_split_y<T>(a, sBr, sBi, tau, ra, rb, w);
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // digit tiles visible to the MMAs
+            __syncthreads();
+
+            T d1[16], d2[16];
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                if (tid == 0) {
+                    tc_fence_after();
+                    tc_issue<S, GMIN>(tmem, smem_u32(sA), smem_u32(half == 0 ? sBr : sBi));
+                    tc_commit(mb);
+                }
+                const bool ok = tc_wait(mb, parity);
+                parity ^= 1u;
+                if (__syncthreads_or(!ok)) {
+                    failed = true;
+                    break;
+                }
+                tc_fence_after();
+                if (half == 0) tc_fold<T, NG>(tmem, q, cb, d1);
+                else tc_fold<T, NG>(tmem, q, cb, d2);
+                tc_fence_before();
+                __syncthreads();  // accumulators read before the next MMAs; after D2 the tiles are free
+            }
+            if (failed) break;
+
+            // ---- D1 and D2 meet in shared memory; C_r = D1 top - D2 bottom, C_i = D2 top + D1 bottom
+            {
+                const int row = 32 * q + lane;
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    xs[row * TC_XLD + cb + c] = d1[c];
+                    xs[(128 + row) * TC_XLD + cb + c] = d2[c];
+                }
+            }
+            __syncthreads();
+            {
+                const int i = tid & 63, jb = tid >> 6;
+                const T *x1 = xs, *x2 = xs + 128 * TC_XLD;
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    const int j = 8 * jb + jj;
+                    if (i >= d || j >= d) continue;
+                    const T cr = Ar<T>::sub(x1[i * TC_XLD + j], x2[(64 + i) * TC_XLD + j]);
+                    const T ci = Ar<T>::add(x2[i * TC_XLD + j], x1[(64 + i) * TC_XLD + j]);
+                    // the fold factored out 2^(8 (NG - 1)) of the group weights 2^(8 (g - GMIN))
+                    const int ex = sig[i] + tau[j] + 8 * GMIN - 16 * S + 8 * (NG - 1);
+                    const cx<T> v = {tc_scale(cr, ex), tc_scale(ci, ex)};
+                    const int64_t e = (int64_t)i * d + j;
+                    if (nfreq == 1) {
+                        ZC[f * E + e] = merge_real(v, v, c_conj(wf));  // p = M/2: C(g) = C(f)
+                    } else if (phase == 0) {
+                        ZC[f * E + e] = v;  // C(f), merged once C(g) is known (same thread)
+                    } else {
+                        const cx<T> cf = ZC[f * E + e];
+                        ZC[f * E + e] = merge_real(cf, v, c_conj(wf));
+                        if (two) ZC[gZ * E + e] = merge_real(v, cf, c_conj(wg));
+                    }
+                }
+            }
+            __syncthreads();  // exchange read before the next digit tiles
+        }
+    }
+
+    if (failed) {
+        if (tid == 0 && status) atomicExch(status, 6);
+        tc_wait(mb, parity);  // let MMAs still in flight finish before the TMEM is freed
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+} // namespace
+
+bool mrc_tc_supported(int r, int m, int c) { return r == m && m == c && r >= 32 && r <= 64; }
+
+cudaError_t mrc_tc_init(void)
+{
+    cudaError_t e = cudaFuncSetAttribute(oztc_pairmul_kernel<dd>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tc_smem<dd>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(oztc_pairmul_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tc_smem<float>());
+}
+
+template <class T>
+static cudaError_t tc_run(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
+                          cudaStream_t st, int kclass)
+{
+    PairArgs a{};
+    a.zx = zx; a.zy = zy; a.zc = zc; a.tw = tw; a.tw_log = tw_log; a.M = M;
+    int l = 0;
+    while (((int64_t)1 << l) < M) ++l;
+    a.logM = l;
+    a.npairs = M >= 2 ? M / 2 + 1 : 1;
+    a.r = a.m = a.c = d;
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (nsm <= 0) nsm = 1;
+    }
+    const unsigned grid = (unsigned)std::min<int64_t>(a.npairs, nsm);
+    const double bytes = (double)M * 3.0 * d * d * sizeof(cx<T>);
+    const double flops = 8.0 * d * d * d * (double)(M + 1);
+    mrc_prof_pre(kclass, st);
+    oztc_pairmul_kernel<T><<<grid, TC_THREADS, tc_smem<T>(), st>>>(a, mrc_status_word());
+    mrc_prof_post(kclass, st, bytes, flops);
+    return cudaGetLastError();
+}
+
+cudaError_t mrc_pairmul_dd_tc(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
+                              cudaStream_t st)
+{
+    return tc_run<dd>(zx, zy, zc, M, d, tw, tw_log, st, 6);
+}
+
+cudaError_t mrc_pairmul_f32_tc(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
+                               cudaStream_t st)
+{
+    return tc_run<float>(zx, zy, zc, M, d, tw, tw_log, st, 5);
+}

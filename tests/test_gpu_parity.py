@@ -229,26 +229,34 @@ def test_batched_reports_singular_model(mrc):
         assert np.abs(o.cpu().numpy() - oracle.inverse_left(good)).max() <= TOL64
 
 
-@pytest.mark.parametrize("d,N", [(40, 300), (64, 200), (48, 513)])
+@pytest.mark.parametrize("d,N", [(40, 300), (64, 200), (48, 513), (33, 129)])
 def test_tensor_core_dd_residual_matches_oracle(mrc, d, N):
-    """The double-float residual product for 32 <= d <= 64 runs on the BF16
-    tensor cores (exact digit products); it must match the oracle's residual
-    and the FP32-pipe double-float kernel to 1e-12."""
+    """The double-float residual product for 32 <= d <= 64 runs as exact digit
+    products on the tensor cores: by default tcgen05 (TMEM accumulators),
+    MRC_DD_PRODUCT=mma the mma.sync kernel, =simt the FP32-pipe kernel.  Each
+    must match the oracle's residual, and the three each other, to 1e-12
+    (d = 33: padded tiles with a ragged edge; N = 129: a partial last pair
+    range and the self-paired middle frequency)."""
     import os
     rng = np.random.default_rng(d)
     q, _ = synth.weibull_model(d, N, seed=d)
     A = synth.identity_minus(q)
     psi = oracle.inverse_left(A) + 1e-6 * rng.standard_normal(A.shape)
     rl_ref, rr_ref = oracle.residuals(A, psi)
-    rl, rr, _ = mrc.residual(dev(A), dev(psi), sides=3, prec="mixed")
-    assert np.abs(rl.cpu().numpy() - rl_ref).max() <= 1e-12
-    assert np.abs(rr.cpu().numpy() - rr_ref).max() <= 1e-12
-    os.environ["MRC_DD_PRODUCT"] = "simt"
-    try:
-        rl2, _, _ = mrc.residual(dev(A), dev(psi), sides=1, prec="mixed")
-    finally:
-        del os.environ["MRC_DD_PRODUCT"]
-    assert (rl - rl2).abs().max().item() <= 1e-12
+    out = {}
+    for mode in ("", "mma", "simt"):
+        if mode:
+            os.environ["MRC_DD_PRODUCT"] = mode
+        try:
+            rl, rr, _ = mrc.residual(dev(A), dev(psi), sides=3, prec="mixed")
+            mrc.sync_status()
+        finally:
+            os.environ.pop("MRC_DD_PRODUCT", None)
+        assert np.abs(rl.cpu().numpy() - rl_ref).max() <= 1e-12, mode
+        assert np.abs(rr.cpu().numpy() - rr_ref).max() <= 1e-12, mode
+        out[mode] = rl
+    assert (out[""] - out["simt"]).abs().max().item() <= 1e-12
+    assert (out[""] - out["mma"]).abs().max().item() <= 1e-12
 
 
 def test_mixed_inverse_d64_lognormal_prefix(mrc):
@@ -261,10 +269,11 @@ def test_mixed_inverse_d64_lognormal_prefix(mrc):
     assert rep["res_max_abs"] <= TOL_REL
 
 
-@pytest.mark.parametrize("mode", ["tensor", "tf32x3"])
+@pytest.mark.parametrize("mode", ["tensor", "tf32x3", "tc"])
 def test_mixed_inverse_with_fp32_tensor_products(mrc, mode):
     """Opt-in FP32 tensor-core products: MRC_F32_PRODUCT=tensor (5-digit
-    products everywhere) and =tf32x3 (Newton levels as three TF32 products);
+    products everywhere, mma.sync), =tc (the same on tcgen05) and =tf32x3
+    (Newton levels as three TF32 products);
     the refined inverse must still meet the residual gate."""
     import os
     q, _ = synth.weibull_model(48, 700, seed=31)
