@@ -248,7 +248,10 @@ mrc_status mrc_inverse_noalloc(int d, int64_t N, const double *A, double *psi, v
  * the summed device time (ms), the number of timed launches and the charged
  * bytes and flops, then switches recording off.  At most 8192 launches are
  * timed per begin/end; later launches are counted by mrc_launch_count only.
- * Not thread safe.
+ * Launches on the context's low-priority side stream (the double-float
+ * spectrum of A that a single-model mixed inverse computes while its Newton
+ * levels run) are not timed: they overlap the critical path, so their event
+ * durations would include time spent waiting for SMs.  Not thread safe.
  */
 #define MRC_K_FFT_F64 1
 #define MRC_K_FFT_F32 2

@@ -57,6 +57,7 @@ struct mrc_ctx {
 };
 
 void mrc_prof_set_capturing(bool on);
+void mrc_prof_set_untimed(cudaStream_t st);
 
 namespace {
 
@@ -593,7 +594,10 @@ mrc_status mrc_destroy(mrc_ctx *c)
     cudaFree(c->d_acc);
     cudaEventDestroy(c->ev0);
     cudaEventDestroy(c->ev1);
-    if (c->aux) cudaStreamDestroy(c->aux);
+    if (c->aux) {
+        mrc_prof_set_untimed(nullptr);
+        cudaStreamDestroy(c->aux);
+    }
     if (c->hi) cudaStreamDestroy(c->hi);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -645,6 +649,7 @@ mrc_status mrc_inverse(mrc_ctx *c, int d, int64_t N, const double *A, double *ps
         int least = 0, greatest = 0;
         CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
         CK(cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, least));
+        mrc_prof_set_untimed(c->aux);
         CK(cudaStreamCreateWithPriority(&c->hi, cudaStreamNonBlocking, greatest));
         CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));

@@ -59,6 +59,34 @@ __device__ __forceinline__ dd dd_mul(dd x, dd y)
     return dd_fast_two_sum(p, e);
 }
 
+// x + y without the final normalisation: hi is the rounded sum of the high
+// parts, lo collects their exact error and both low parts, and |lo| may
+// exceed half an ulp of hi.  Chains of these inside one small DFT are
+// normalised once at its end (dd_norm); every operation here accepts such
+// unnormalised operands, and the error stays a small multiple of
+// 2^-48 (|x| + |y|).
+__device__ __forceinline__ dd dd_add_nn(dd x, dd y)
+{
+    const dd s = dd_two_sum(x.hi, y.hi);
+    return {s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo))};
+}
+__device__ __forceinline__ dd dd_norm(dd x) { return dd_fast_two_sum(x.hi, x.lo); }
+
+// a*b + c*d with one TwoSum: the two high products and their exact errors
+// (FMA), the four cross terms folded into the low part, one normalisation
+__device__ __forceinline__ dd dd_dot2(dd a, dd b, dd c, dd d)
+{
+    const float p1 = __fmul_rn(a.hi, b.hi), p2 = __fmul_rn(c.hi, d.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p1);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    float f = __fmaf_rn(c.hi, d.hi, -p2);
+    f = __fmaf_rn(c.hi, d.lo, f);
+    f = __fmaf_rn(c.lo, d.hi, f);
+    const dd s = dd_two_sum(p1, p2);
+    return dd_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, f)));
+}
+
 // a*b + c with one normalisation
 __device__ __forceinline__ dd dd_fma(dd a, dd b, dd c)
 {
@@ -155,6 +183,9 @@ struct Ar<double> {
     static __device__ __forceinline__ double to_d(double x) { return x; }
     static __device__ __forceinline__ double zero() { return 0.0; }
     static __device__ __forceinline__ double one() { return 1.0; }
+    static __device__ __forceinline__ double add_nn(double a, double b) { return a + b; }
+    static __device__ __forceinline__ double sub_nn(double a, double b) { return a - b; }
+    static __device__ __forceinline__ double norm(double a) { return a; }
     static __device__ __forceinline__ double rsqrt2() { return 0.70710678118654752440; }
 };
 
@@ -171,6 +202,9 @@ struct Ar<float> {
     static __device__ __forceinline__ double to_d(float x) { return f32_to_f64(x); }
     static __device__ __forceinline__ float zero() { return 0.0f; }
     static __device__ __forceinline__ float one() { return 1.0f; }
+    static __device__ __forceinline__ float add_nn(float a, float b) { return a + b; }
+    static __device__ __forceinline__ float sub_nn(float a, float b) { return a - b; }
+    static __device__ __forceinline__ float norm(float a) { return a; }
     static __device__ __forceinline__ float rsqrt2() { return 0x1.6a09e6p-1f; }
 };
 
@@ -191,6 +225,9 @@ struct Ar<dd> {
     static __device__ __forceinline__ double to_d(dd x) { return dd_to_double(x); }
     static __device__ __forceinline__ dd zero() { return {0.0f, 0.0f}; }
     static __device__ __forceinline__ dd one() { return {1.0f, 0.0f}; }
+    static __device__ __forceinline__ dd add_nn(dd a, dd b) { return dd_add_nn(a, b); }
+    static __device__ __forceinline__ dd sub_nn(dd a, dd b) { return dd_add_nn(a, dd_neg(b)); }
+    static __device__ __forceinline__ dd norm(dd a) { return dd_norm(a); }
     // sqrt(1/2) = hi + lo within 4e-16
     static __device__ __forceinline__ dd rsqrt2() { return {0x1.6a09e6p-1f, 0x1.9fcef4p-27f}; }
 };
@@ -216,6 +253,18 @@ __device__ __forceinline__ cx<T> c_mul(cx<T> a, cx<T> b)
     return {Ar<T>::fma(a.re, b.re, Ar<T>::neg(Ar<T>::mul(a.im, b.im))),
             Ar<T>::fma(a.re, b.im, Ar<T>::mul(a.im, b.re))};
 }
+// double-float a * b: each component one dot product with one normalisation
+__device__ __forceinline__ cx<dd> c_mul(cx<dd> a, cx<dd> b)
+{
+    return {dd_dot2(a.re, b.re, dd_neg(a.im), b.im), dd_dot2(a.re, b.im, a.im, b.re)};
+}
+// sums without the final normalisation (see dd_add_nn) and the normalisation
+template <class T>
+__device__ __forceinline__ cx<T> c_add_nn(cx<T> a, cx<T> b) { return {Ar<T>::add_nn(a.re, b.re), Ar<T>::add_nn(a.im, b.im)}; }
+template <class T>
+__device__ __forceinline__ cx<T> c_sub_nn(cx<T> a, cx<T> b) { return {Ar<T>::sub_nn(a.re, b.re), Ar<T>::sub_nn(a.im, b.im)}; }
+template <class T>
+__device__ __forceinline__ cx<T> c_norm(cx<T> a) { return {Ar<T>::norm(a.re), Ar<T>::norm(a.im)}; }
 // c += a * b
 template <class T>
 __device__ __forceinline__ void c_mac(cx<T> &c, cx<T> a, cx<T> b)

@@ -104,19 +104,19 @@ template <class T, bool INV>
 __device__ __forceinline__ void dft2(cx<T> *v)
 {
     cx<T> t = v[0];
-    v[0] = c_add(t, v[1]);
-    v[1] = c_sub(t, v[1]);
+    v[0] = c_add_nn(t, v[1]);
+    v[1] = c_sub_nn(t, v[1]);
 }
 
 template <class T, bool INV>
 __device__ __forceinline__ void dft4(cx<T> *v)
 {
-    cx<T> c0 = c_add(v[0], v[2]), c2 = c_sub(v[0], v[2]);
-    cx<T> c1 = c_add(v[1], v[3]), c3 = mul_mi<T, INV>(c_sub(v[1], v[3]));
-    v[0] = c_add(c0, c1);
-    v[2] = c_sub(c0, c1);
-    v[1] = c_add(c2, c3);
-    v[3] = c_sub(c2, c3);
+    cx<T> c0 = c_add_nn(v[0], v[2]), c2 = c_sub_nn(v[0], v[2]);
+    cx<T> c1 = c_add_nn(v[1], v[3]), c3 = mul_mi<T, INV>(c_sub_nn(v[1], v[3]));
+    v[0] = c_add_nn(c0, c1);
+    v[2] = c_sub_nn(c0, c1);
+    v[1] = c_add_nn(c2, c3);
+    v[3] = c_sub_nn(c2, c3);
 }
 
 // radix-8 = one radix-2 step (decimation in frequency) + two radix-4 DFTs
@@ -127,18 +127,18 @@ __device__ __forceinline__ void dft8(cx<T> *v)
     cx<T> a[4], b[4];
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
-        a[n] = c_add(v[n], v[n + 4]);
-        b[n] = c_sub(v[n], v[n + 4]);
+        a[n] = c_add_nn(v[n], v[n + 4]);
+        b[n] = c_sub_nn(v[n], v[n + 4]);
     }
     // b_n *= W_8^{n} (forward) or W_8^{-n} (inverse)
     {
         cx<T> x = b[1];
-        b[1] = INV ? cx<T>{Ar<T>::mul(Ar<T>::sub(x.re, x.im), s), Ar<T>::mul(Ar<T>::add(x.re, x.im), s)}
-                   : cx<T>{Ar<T>::mul(Ar<T>::add(x.re, x.im), s), Ar<T>::mul(Ar<T>::sub(x.im, x.re), s)};
+        b[1] = INV ? cx<T>{Ar<T>::mul(Ar<T>::sub_nn(x.re, x.im), s), Ar<T>::mul(Ar<T>::add_nn(x.re, x.im), s)}
+                   : cx<T>{Ar<T>::mul(Ar<T>::add_nn(x.re, x.im), s), Ar<T>::mul(Ar<T>::sub_nn(x.im, x.re), s)};
         b[2] = mul_mi<T, INV>(b[2]);
         x = b[3];
-        b[3] = INV ? cx<T>{Ar<T>::mul(Ar<T>::neg(Ar<T>::add(x.re, x.im)), s), Ar<T>::mul(Ar<T>::sub(x.re, x.im), s)}
-                   : cx<T>{Ar<T>::mul(Ar<T>::sub(x.im, x.re), s), Ar<T>::mul(Ar<T>::neg(Ar<T>::add(x.re, x.im)), s)};
+        b[3] = INV ? cx<T>{Ar<T>::mul(Ar<T>::neg(Ar<T>::add_nn(x.re, x.im)), s), Ar<T>::mul(Ar<T>::sub_nn(x.re, x.im), s)}
+                   : cx<T>{Ar<T>::mul(Ar<T>::sub_nn(x.im, x.re), s), Ar<T>::mul(Ar<T>::neg(Ar<T>::add_nn(x.re, x.im)), s)};
     }
     dft4<T, INV>(a);
     dft4<T, INV>(b);
@@ -149,13 +149,21 @@ __device__ __forceinline__ void dft8(cx<T> *v)
     }
 }
 
+// The adds inside one small DFT skip the double-float normalisation
+// (c_add_nn); dft_r normalises its outputs once.
 template <class T, bool INV, int LR>
 __device__ __forceinline__ void dft_r(cx<T> *v)
 {
     if constexpr (LR == 0) return;
-    else if constexpr (LR == 1) dft2<T, INV>(v);
-    else if constexpr (LR == 2) dft4<T, INV>(v);
-    else dft8<T, INV>(v);
+    else {
+        if constexpr (LR == 1) dft2<T, INV>(v);
+        else if constexpr (LR == 2) dft4<T, INV>(v);
+        else dft8<T, INV>(v);
+        if constexpr (__is_same(T, dd)) {
+#pragma unroll
+            for (int q = 0; q < (1 << LR); ++q) v[q] = c_norm(v[q]);
+        }
+    }
 }
 
 // Entries per CTA of the passes: for 8-byte complex values (FP32) 8, i.e.

@@ -4,7 +4,10 @@
 // counter is always on.  When a kernel class is selected with
 // mrc_profile_begin, CUDA events are recorded around each launch of that class
 // on its own stream, together with the algorithmic bytes and flops the launch
-// is charged with; mrc_profile_end sums them.  Not thread safe: profile one
+// is charged with; mrc_profile_end sums them.  Launches on an untimed stream
+// (mrc_prof_set_untimed: the low-priority side stream whose kernels overlap
+// the critical path, so that their event durations include time spent
+// waiting for SMs) are counted but not timed.  Not thread safe: profile one
 // host thread at a time.
 #include <stdlib.h>
 
@@ -30,6 +33,11 @@ constexpr size_t kPool = 16384;
 void mrc_prof_set_capturing(bool on) { g_prof.capturing = on; }
 
 namespace {
+cudaStream_t g_untimed = nullptr;
+}
+void mrc_prof_set_untimed(cudaStream_t st) { g_untimed = st; }
+
+namespace {
 int *g_status_word = nullptr;
 }
 int *mrc_status_word(void) { return g_status_word; }
@@ -44,14 +52,14 @@ bool mrc_fft_tma_enabled(void)
 void mrc_prof_pre(int kclass, cudaStream_t st)
 {
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    if (g_prof.capturing) return;
+    if (g_prof.capturing || (g_untimed && st == g_untimed)) return;
     if (g_prof.kclass && kclass == g_prof.kclass && g_prof.used + 2 <= g_prof.pool.size())
         cudaEventRecord(g_prof.pool[g_prof.used], st);
 }
 
 void mrc_prof_post(int kclass, cudaStream_t st, double bytes, double flops)
 {
-    if (g_prof.capturing) return;
+    if (g_prof.capturing || (g_untimed && st == g_untimed)) return;
     if (g_prof.kclass && kclass == g_prof.kclass && g_prof.used + 2 <= g_prof.pool.size()) {
         cudaEventRecord(g_prof.pool[g_prof.used + 1], st);
         g_prof.used += 2;
