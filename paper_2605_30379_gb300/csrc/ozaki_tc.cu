@@ -105,14 +105,12 @@ __device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity)
     return false;
 }
 
-// 32 TMEM lanes x 16 consecutive 32-bit columns: thread `lane` of the warp
-// receives lane (base lane + lane), columns col .. col + 15.
-__device__ __forceinline__ void tc_ld16(unsigned taddr, unsigned (&r)[16])
+// 32 TMEM lanes x 8 consecutive 32-bit columns: thread `lane` of the warp
+// receives lane (base lane + lane), columns col .. col + 7.
+__device__ __forceinline__ void tc_ld8(unsigned taddr, unsigned (&r)[8])
 {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                   "=r"(r[15])
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                  : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
@@ -147,25 +145,40 @@ __device__ __forceinline__ dd tc_add(dd a, float v)
 __device__ __forceinline__ float tc_add(float a, float v) { return __fadd_rn(a, v); }
 
 // Fold the NG group accumulators of TMEM lanes 32 q + lane, columns
-// cb .. cb + 15: sum over g of acc_g 2^(8 (g - NG + 1)), top group first
-// (every term an exact FP32 value).
+// cb .. cb + 15: sum over g of acc_g 2^(8 (g - NG + 1)), every term an exact
+// FP32 value.  The top three groups are added as a compensated double-float
+// sum; below them (weights 2^-24 and less of the top group) plain FP32 adds
+// suffice -- their rounding, under 2^-46 of the magnitudes, is of the order
+// of the digit pairs the split drops -- and the low sum joins once.
 template <class T, int NG>
 __device__ __forceinline__ void tc_fold(unsigned tmem, int q, int cb, T (&out)[16])
 {
 #pragma unroll
-    for (int g = NG - 1; g >= 0; --g) {
-        unsigned r[16];
-        tc_ld16(tmem + ((unsigned)(32 * q) << 16) + (unsigned)(g * 64 + cb), r);
-        const float w = __uint_as_float((unsigned)(127 - 8 * (NG - 1 - g)) << 23);  // 2^(8 (g - NG + 1))
+    for (int h = 0; h < 2; ++h) {  // two halves of 8 columns: fewer live registers
+        float lo[8];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-            const float v = __uint_as_float(r[c]) * w;
-            if (g == NG - 1) {
-                if constexpr (__is_same(T, dd)) out[c] = dd{v, 0.0f};
-                else out[c] = v;
-            } else {
-                out[c] = tc_add(out[c], v);
+        for (int g = NG - 1; g >= 0; --g) {
+            unsigned r[8];
+            tc_ld8(tmem + ((unsigned)(32 * q) << 16) + (unsigned)(g * 64 + cb + 8 * h), r);
+            const float w = __uint_as_float((unsigned)(127 - 8 * (NG - 1 - g)) << 23);  // 2^(8 (g - NG + 1))
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float v = __uint_as_float(r[c]) * w;
+                T &o = out[8 * h + c];
+                if constexpr (__is_same(T, dd)) {
+                    if (g == NG - 1) o = dd{v, 0.0f};
+                    else if (g >= NG - 3) o = tc_add(o, v);
+                    else if (g == NG - 4) lo[c] = v;
+                    else lo[c] = __fadd_rn(lo[c], v);
+                } else {
+                    if (g == NG - 1) o = v;
+                    else o = tc_add(o, v);
+                }
             }
+        }
+        if constexpr (__is_same(T, dd) && NG > 3) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) out[8 * h + c] = tc_add(out[8 * h + c], lo[c]);
         }
     }
 }
