@@ -653,6 +653,128 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) pairmul_kernel(PairArgs
         }
 }
 
+// The same product with the two frequencies of the pair on two halves of
+// the CTA (2 x NTX x NTY threads): thread group fq in {0: f, 1: g} keeps only
+// its own TM x TN accumulators, which halves the registers per thread and
+// lets two CTAs share an SM.  Each thread's TM rows and TN columns are
+// contiguous in shared memory; the Y tile stores column tx * TN + v at
+// (v / 2) * 2 NTX + 2 tx + v % 2, so that the 16-byte loads of the FP32
+// kernel fall on consecutive addresses across tx.  After the k loop the g
+// half hands C(g) to the f half through shared memory (the tiles' space),
+// which merges both into the packed output spectrum.
+template <int NTX, int TN>
+__device__ __forceinline__ int pm2_ycol(int jj)
+{
+    const int tx = jj / TN, v = jj - (jj / TN) * TN;
+    return (v >> 1) * (2 * NTX) + 2 * tx + (v & 1);
+}
+
+template <class T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__(2 * (BM / TM) * (BN / TN), 2) pairmul2_kernel(PairArgs a)
+{
+    constexpr int NTX = BN / TN, NTY = BM / TM, NTF = NTX * NTY, NT = 2 * NTF;
+    constexpr int XLD = BM + (sizeof(cx<T>) == 8 ? 2 : 1), YLD = BN + (sizeof(cx<T>) == 8 ? 2 : 1);
+    constexpr int TILE = 2 * BK * (XLD + YLD);  // complex values: X and Y tiles of both frequencies
+    constexpr int XCH = BM * YLD;               // the C(g) exchange
+    static_assert(TN % 2 == 0, "column pairs");
+    __shared__ __align__(16) cx<T> sbuf[TILE > XCH ? TILE : XCH];
+    cx<T> *Xs = sbuf;                  // [2][BK][XLD]
+    cx<T> *Ys = sbuf + 2 * BK * XLD;   // [2][BK][YLD], permuted columns
+    const cx<T> *ZX = reinterpret_cast<const cx<T> *>(a.zx);
+    const cx<T> *ZY = reinterpret_cast<const cx<T> *>(a.zy);
+    cx<T> *ZC = reinterpret_cast<cx<T> *>(a.zc);
+    const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
+
+    const int64_t p = blockIdx.x, M = a.M;
+    const int64_t f = p, gL = M - p, gZ = gL & (M - 1);
+    const int ntile_c = (a.c + BN - 1) / BN;
+    const int i0 = (blockIdx.y / ntile_c) * BM, j0 = (blockIdx.y % ntile_c) * BN;
+    const int fq = threadIdx.x / NTF, lt = threadIdx.x - fq * NTF;
+    const int tx = lt % NTX, ty = lt / NTX;
+    const cx<T> wf = tw[f << (a.tw_log - a.logM - 1)];
+    const cx<T> wg = c_neg(c_conj(wf));
+    const int64_t EX = (int64_t)a.r * a.m, EY = (int64_t)a.m * a.c, EC = (int64_t)a.r * a.c;
+    const cx<T> *xf = ZX + f * EX, *xg = ZX + gZ * EX;
+    const cx<T> *yf = ZY + f * EY, *yg = ZY + gZ * EY;
+
+    cx<T> acc[TM][TN];
+#pragma unroll
+    for (int u = 0; u < TM; ++u)
+#pragma unroll
+        for (int v = 0; v < TN; ++v) acc[u][v] = c_zero<T>();
+
+    for (int k0 = 0; k0 < a.m; k0 += BK) {
+        for (int idx = threadIdx.x; idx < BM * BK; idx += NT) {
+            const int ii = idx / BK, kk = idx - (idx / BK) * BK;
+            const int i = i0 + ii, k = k0 + kk;
+            cx<T> vf = c_zero<T>(), vg = c_zero<T>();
+            if (i < a.r && k < a.m) {
+                const cx<T> za = xf[(int64_t)i * a.m + k], zb = xg[(int64_t)i * a.m + k];
+                vf = split_real(za, zb, wf);
+                vg = split_real(zb, za, wg);
+            }
+            Xs[kk * XLD + ii] = vf;
+            Xs[(BK + kk) * XLD + ii] = vg;
+        }
+        for (int idx = threadIdx.x; idx < BK * BN; idx += NT) {
+            const int kk = idx / BN, jj = idx - (idx / BN) * BN;
+            const int k = k0 + kk, jx = j0 + jj;
+            cx<T> vf = c_zero<T>(), vg = c_zero<T>();
+            if (k < a.m && jx < a.c) {
+                const cx<T> za = yf[(int64_t)k * a.c + jx], zb = yg[(int64_t)k * a.c + jx];
+                vf = split_real(za, zb, wf);
+                vg = split_real(zb, za, wg);
+            }
+            const int pc = pm2_ycol<NTX, TN>(jj);
+            Ys[kk * YLD + pc] = vf;
+            Ys[(BK + kk) * YLD + pc] = vg;
+        }
+        __syncthreads();
+        const cx<T> *xb = Xs + fq * BK * XLD + ty * TM;
+        const cx<T> *yb = Ys + fq * BK * YLD + 2 * tx;
+#pragma unroll 4
+        for (int kk = 0; kk < BK; ++kk) {
+            cx<T> xa[TM], ya[TN];
+#pragma unroll
+            for (int u = 0; u < TM; ++u) xa[u] = xb[kk * XLD + u];
+#pragma unroll
+            for (int h = 0; h < TN / 2; ++h) {
+                ya[2 * h] = yb[kk * YLD + h * 2 * NTX];
+                ya[2 * h + 1] = yb[kk * YLD + h * 2 * NTX + 1];
+            }
+#pragma unroll
+            for (int u = 0; u < TM; ++u)
+#pragma unroll
+                for (int v = 0; v < TN; ++v) c_mac(acc[u][v], xa[u], ya[v]);
+        }
+        __syncthreads();
+    }
+
+    // C(g) to shared memory, then the f half merges both
+    if (fq == 1) {
+#pragma unroll
+        for (int u = 0; u < TM; ++u)
+#pragma unroll
+            for (int v = 0; v < TN; ++v) sbuf[(ty * TM + u) * YLD + tx * TN + v] = acc[u][v];
+    }
+    __syncthreads();
+    if (fq == 0) {
+        const cx<T> wfc = c_conj(wf), wgc = c_conj(wg);
+        const bool two = (gZ != f);
+#pragma unroll
+        for (int u = 0; u < TM; ++u)
+#pragma unroll
+            for (int v = 0; v < TN; ++v) {
+                const int i = i0 + ty * TM + u, jx = j0 + tx * TN + v;
+                if (i >= a.r || jx >= a.c) continue;
+                const cx<T> cg = sbuf[(ty * TM + u) * YLD + tx * TN + v];
+                const int64_t e = (int64_t)i * a.c + jx;
+                ZC[f * EC + e] = merge_real(acc[u][v], cg, wfc);
+                if (two) ZC[gZ * EC + e] = merge_real(cg, acc[u][v], wgc);
+            }
+    }
+}
+
 // Frequency-pair product with a diagonal right factor:
 //   Ch(f)_{ij} = Xh(f)_{ij} * Yh(f)_j   (X: [E = r*c], Y: [c]),
 // the per-entry scalar convolutions P_ij = psi_ij * h_j of Eq. (transition-discrete).

@@ -185,6 +185,19 @@ cudaError_t pairmul_launch(const PairArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <class T, int BM, int BN, int BK, int TM, int TN>
+cudaError_t pairmul2_launch(const PairArgs &a, cudaStream_t st)
+{
+    const int tiles = ((a.r + BM - 1) / BM) * ((a.c + BN - 1) / BN);
+    dim3 grid((unsigned)a.npairs, (unsigned)tiles);
+    const double bytes = (double)a.M * ((double)a.r * a.m + (double)a.m * a.c + (double)a.r * a.c) * sizeof(cx<T>);
+    const double flops = 8.0 * a.r * a.m * a.c * (double)(a.M + 1);
+    mrc_prof_pre(kclass_pair<T>(), st);
+    pairmul2_kernel<T, BM, BN, BK, TM, TN><<<grid, 2 * (BM / TM) * (BN / TN), 0, st>>>(a);
+    mrc_prof_post(kclass_pair<T>(), st, bytes, flops);
+    return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t pairmul_run(const void *zx, const void *zy, void *zc, int64_t M, int r, int m, int c, int cfg, const void *tw,
                         int tw_log, cudaStream_t st)
@@ -199,6 +212,13 @@ cudaError_t pairmul_run(const void *zx, const void *zy, void *zc, int64_t M, int
     if (cfg < 0) cfg = mx <= 16 ? 0 : (mx <= 32 ? 1 : 2);
     if (cfg == 0) return pairmul_launch<T, 16, 16, 16, 2, 2>(a, st);
     if (cfg == 1) return pairmul_launch<T, 32, 32, 16, 2, 2>(a, st);
+    // FP32, 64 x 64 tiles: the frequencies of a pair on two halves of the CTA
+    // (half the registers per thread, two CTAs per SM); MRC_PAIR_SPLIT=0 keeps
+    // both frequencies in every thread
+    if constexpr (std::is_same<T, float>::value) {
+        const char *v = getenv("MRC_PAIR_SPLIT");
+        if (!(v && v[0] == '0')) return pairmul2_launch<T, 64, 64, 8, 4, 4>(a, st);
+    }
     return pairmul_launch<T, 64, 64, 8, 4, 4>(a, st);
 }
 

@@ -333,6 +333,30 @@ def test_fft_pipelined_pass_matches_plain_pass(mrc):
             assert np.abs(got - out["0"]).max() <= 1e-13, (d, mode)
 
 
+@pytest.mark.parametrize("d,N", [(64, 700), (40, 1500), (70, 300)])
+def test_fp32_pair_product_split_matches_unsplit(mrc, d, N):
+    """The FP32 64 x 64-tile product puts the two frequencies of a pair on two
+    halves of the CTA (default) or both in every thread (MRC_PAIR_SPLIT=0).
+    The per-output arithmetic is the same, so the mixed inverses must agree
+    and both stay within the parity gate (d = 70: several output tiles with
+    ragged edges; d = 40: one partial tile)."""
+    import os
+    q, _ = synth.weibull_model(d, N, seed=70 + d)
+    A = synth.identity_minus(q)
+    ref = oracle.inverse_left(A)
+    out = {}
+    for mode in ("", "0"):
+        if mode:
+            os.environ["MRC_PAIR_SPLIT"] = mode
+        try:
+            out[mode] = mrc.inverse(dev(A), prec="mixed").cpu().numpy()
+            mrc.sync_status()
+        finally:
+            os.environ.pop("MRC_PAIR_SPLIT", None)
+        assert e_rel(out[mode], ref) <= TOL_REL, mode
+    assert np.abs(out[""] - out["0"]).max() <= 1e-13
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_reward_matches_oracle(mrc, prec):
     """V = psi * r with a rectangular reward sequence (Eq. (reward)); the oracle
