@@ -29,16 +29,32 @@ def _deps_mtime():
     return max(ts)
 
 
+STAMP = os.path.join(BUILD, "flags.txt")
+
+
+def _extra_flags():
+    return os.environ.get("MRC_NVCC_FLAGS", "").split()
+
+
+def _stamp_matches():
+    try:
+        with open(STAMP) as fh:
+            return fh.read() == " ".join(_extra_flags())
+    except OSError:
+        return not _extra_flags()
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
+    """Compile and link libmrc.so unless it is newer than every source and was
+    built with the same MRC_NVCC_FLAGS (extra nvcc options, e.g. -D macros)."""
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime() and _stamp_matches():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        extra = os.environ.get("MRC_NVCC_FLAGS", "").split()
-        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *_extra_flags(), "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -54,6 +70,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as fh:
+        fh.write(" ".join(_extra_flags()))
     return LIB
 
 

@@ -174,8 +174,11 @@ __device__ __forceinline__ void dft_r(cx<T> *v)
 #ifndef MRC_F32_EC
 #define MRC_F32_EC 8
 #endif
+#ifndef MRC_DD_EC
+#define MRC_DD_EC 8
+#endif
 template <class T>
-constexpr int fft_default_ec() { return sizeof(cx<T>) == 8 ? MRC_F32_EC : 8; }
+constexpr int fft_default_ec() { return sizeof(cx<T>) == 8 ? MRC_F32_EC : MRC_DD_EC; }
 
 // Compile-time plan of one pass: R = 2^LOGR points split into in-CTA stages
 // of radix 2^FIRST then 8, 8, ...; EC entries per CTA; NT threads, each
