@@ -117,6 +117,26 @@ mrc_status mrc_inverse(mrc_ctx *ctx, int d, int64_t N, const double *A, double *
                        const mrc_options *opt, void *stream, mrc_report *report);
 
 /*
+ * mrc_inverse_host -- the same inverse as mrc_inverse (same kernels, same
+ * results) for a sequence that lives in host memory, with the transfers in
+ * the call: A is uploaded in the row ranges the Newton doubling consumes
+ * (level m of Eq. (newton) reads A(0) .. A(2m-1), Section 3), on an
+ * internal copy stream, so that the first levels start while the rest of A
+ * is still in transit; psi is copied back on `stream` after the last sweep.
+ *   A_host  : host, [N][d][d] doubles.  Pinned (page-locked) memory lets the
+ *             uploads overlap the kernels; pageable memory works too, with
+ *             the copies serialised by the CUDA runtime.
+ *   psi_host: host, [N][d][d] doubles, written when the call's work on
+ *             `stream` completes (synchronise `stream`, or pass a report).
+ *   d, N, opt, stream, report: as mrc_inverse.  The device copies of A and
+ *             psi live in the context workspace (2 N d^2 doubles more than
+ *             mrc_inverse_workspace_bytes).
+ * Errors: as mrc_inverse.
+ */
+mrc_status mrc_inverse_host(mrc_ctx *ctx, int d, int64_t N, const double *A_host, double *psi_host,
+                            const mrc_options *opt, void *stream, mrc_report *report);
+
+/*
  * mrc_inverse_batched -- mrc_inverse over `nmodels` independent models with
  * their own d[b] and N[b] (host arrays), A[b]/psi[b] device pointers held in
  * HOST arrays of pointers (no counterpart in the paper beyond applying

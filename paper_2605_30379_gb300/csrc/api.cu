@@ -44,6 +44,10 @@ struct mrc_ctx {
     // spectrum of A is computed on `aux` (lowest priority)
     cudaStream_t aux = nullptr, hi = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
+    // host-buffer inverse: copy stream and one event per uploaded row range
+    cudaStream_t cpy = nullptr;
+    cudaEvent_t ev_cpy_fork = nullptr;
+    cudaEvent_t ev_rows[32] = {};
     // batching
     cudaStream_t bst[MRC_BATCH_STREAMS] = {};
     cudaEvent_t bev[MRC_BATCH_STREAMS] = {};
@@ -96,6 +100,21 @@ struct Arena {
         void *p = base + off;
         off += align_up(bytes);
         return p;
+    }
+};
+
+// Row ranges of A still being uploaded (mrc_inverse_host): ranges
+// [end[i-1], end[i]) complete at ev[i]; wait(s, rows) makes stream s wait
+// until rows [0, rows) are on the device.  n == 0: everything is there.
+struct RowWait {
+    int n = 0;
+    int64_t end[32] = {};
+    cudaEvent_t ev[32] = {};
+    cudaError_t wait(cudaStream_t s, int64_t rows) const
+    {
+        for (int i = 0; i < n; ++i)
+            if (end[i] >= rows) return cudaStreamWaitEvent(s, ev[i], 0);
+        return n ? cudaStreamWaitEvent(s, ev[n - 1], 0) : cudaSuccess;
     }
 };
 
@@ -327,7 +346,7 @@ mrc_status conv_product(mrc_ctx *c, Arena &ar, int prec, const double *X, int64_
 // already correct; each level m -> min(2m, N) follows Eq. (newton) with the
 // middle product (L = 2m): E = A*B (cyclic), R = -E[m, 2m), B[m, 2m) = (B*R)[0, m).
 mrc_status newton_levels(mrc_ctx *c, Arena &ar, int prec, int d, int64_t N, const double *A, double *psi,
-                         int64_t m0, int *levels, cudaStream_t st)
+                         int64_t m0, int *levels, cudaStream_t st, const RowWait *rw = nullptr)
 {
     const PrecOps &op = OPS[prec];
     const int E = d * d;
@@ -341,6 +360,7 @@ mrc_status newton_levels(mrc_ctx *c, Arena &ar, int prec, int d, int64_t N, cons
     int lv = 0;
     for (int64_t m = m0; m < N; m <<= 1, ++lv) {
         const int64_t M = m, m2 = std::min<int64_t>(2 * m, N);
+        if (rw) CK(rw->wait(st, m2));  // this level reads A[0, 2m)
         FftSrc sA{SRC_REAL64, A, 0, std::min<int64_t>(2 * m, N), E, 0};
         FftSrc sB{SRC_REAL64, psi, 0, m, E, 0};
         FftDst to0{DST_CPLX, b0, E, 0, 0, 0, 1.0, 0};
@@ -374,7 +394,8 @@ bool valid_dN(int d, int64_t N) { return d >= 1 && d <= 512 && N >= 1 && N <= ((
 // waits for both before the first residual.  Without `split` (batched calls,
 // whose models already overlap on several streams) everything runs on `st`.
 mrc_status inverse_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A, double *psi, int prec, int sweeps,
-                        int *levels, cudaStream_t st, int *status = nullptr, bool split = false)
+                        int *levels, cudaStream_t st, int *status = nullptr, bool split = false,
+                        const RowWait *rw = nullptr)
 {
     const size_t E = (size_t)d * d;
     double *gjw = (double *)ar.take(sizeof(double) * 2 * E);
@@ -392,16 +413,18 @@ mrc_status inverse_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A
             sa = c->aux;
             sn = c->hi;
         }
+        if (rw) CK(rw->wait(sa, N));
         FftSrc sx{SRC_REAL64, A, 0, N, (int)E, 0};
         FftDst dx{DST_CPLX, ahat, (int)E, 0, 0, 0, 1.0, 0};
         CK(OPS[PREC_DD].fft(sx, dx, Mr, (int)E, -1, ascr, c->tw[PREC_DD], MRC_TW_LOG, sa));
         if (split) CK(cudaEventRecord(c->ev_join, c->aux));
     }
-    CK(mrc_gauss_jordan(A, psi, gjw, d, status ? status : c->d_status, sn));
     const int64_t m0 = base_size(d, N);
+    if (rw) CK(rw->wait(sn, m0));
+    CK(mrc_gauss_jordan(A, psi, gjw, d, status ? status : c->d_status, sn));
     CK(mrc_base_case(A, psi, d, m0, sn));
     const size_t mark = ar.off;
-    mrc_status s = newton_levels(c, ar, prec == MRC_FP64 ? PREC_F64 : PREC_F32, d, N, A, psi, m0, levels, sn);
+    mrc_status s = newton_levels(c, ar, prec == MRC_FP64 ? PREC_F64 : PREC_F32, d, N, A, psi, m0, levels, sn, rw);
     if (s != MRC_OK) return s;
     ar.off = mark;
     if (prec == MRC_MIXED) {
@@ -536,6 +559,21 @@ void tune_save(mrc_ctx *cx)
 } // namespace
 
 // ===========================================================================
+// the single-model mixed inverse's two internal streams (created on first use)
+static mrc_status ensure_split_streams(mrc_ctx *c)
+{
+    if (c->aux) return MRC_OK;
+    int least = 0, greatest = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CK(cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, least));
+    mrc_prof_set_untimed(c->aux);
+    CK(cudaStreamCreateWithPriority(&c->hi, cudaStreamNonBlocking, greatest));
+    CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming));
+    return MRC_OK;
+}
+
 extern "C" {
 
 const char *mrc_status_string(mrc_status s)
@@ -602,6 +640,10 @@ mrc_status mrc_destroy(mrc_ctx *c)
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_join2) cudaEventDestroy(c->ev_join2);
+    if (c->cpy) cudaStreamDestroy(c->cpy);
+    if (c->ev_cpy_fork) cudaEventDestroy(c->ev_cpy_fork);
+    for (auto e : c->ev_rows)
+        if (e) cudaEventDestroy(e);
     for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
     for (int k = 0; k < MRC_BATCH_STREAMS; ++k) {
         if (c->bst[k]) cudaStreamDestroy(c->bst[k]);
@@ -645,16 +687,7 @@ mrc_status mrc_inverse(mrc_ctx *c, int d, int64_t N, const double *A, double *ps
     Arena ar{(char *)c->ws};
     int levels = 0;
     if (report) CK(cudaEventRecord(c->ev0, st));
-    if (prec == MRC_MIXED && !c->aux) {
-        int least = 0, greatest = 0;
-        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-        CK(cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, least));
-        mrc_prof_set_untimed(c->aux);
-        CK(cudaStreamCreateWithPriority(&c->hi, cudaStreamNonBlocking, greatest));
-        CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming));
-    }
+    if (prec == MRC_MIXED && (s = ensure_split_streams(c)) != MRC_OK) return s;
     s = inverse_impl(c, ar, d, N, A, psi, prec, sweeps, &levels, st, nullptr, prec == MRC_MIXED);
     if (s != MRC_OK) return s;
     if (report) {
@@ -671,6 +704,77 @@ mrc_status mrc_inverse(mrc_ctx *c, int d, int64_t N, const double *A, double *ps
         if (check) {
             Arena ar2{(char *)c->ws};
             s = residual_impl(c, ar2, d, N, A, psi, 1, nullptr, nullptr, MRC_MIXED, st, report);
+            if (s != MRC_OK) return s;
+            if (!(report->res_max_abs <= opt->target_residual)) return MRC_ERR_NOT_CONVERGED;
+        }
+    }
+    return MRC_OK;
+}
+
+mrc_status mrc_inverse_host(mrc_ctx *c, int d, int64_t N, const double *A_host, double *psi_host,
+                            const mrc_options *opt, void *stream, mrc_report *report)
+{
+    if (!c || !A_host || !psi_host || !valid_dN(d, N)) return MRC_ERR_INVALID_ARG;
+    TuneScope tscope(c, opt);
+    const int prec = opt ? opt->prec : MRC_FP64;
+    if (prec != MRC_FP64 && prec != MRC_MIXED) return MRC_ERR_INVALID_ARG;
+    int sweeps = opt ? opt->refine_sweeps : 1;
+    if (prec == MRC_MIXED && sweeps <= 0) sweeps = 1;
+    if (sweeps > 4) return MRC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaSetDevice(c->device);
+    mrc_status s;
+    if ((s = ensure_tw(c, prec == MRC_FP64 ? PREC_F64 : PREC_F32, st)) != MRC_OK) return s;
+    if (prec == MRC_MIXED && (s = ensure_tw(c, PREC_DD, st)) != MRC_OK) return s;
+    const size_t E = (size_t)d * d, bytes = (size_t)N * E * sizeof(double), seq = align_up(bytes);
+    const bool check = report && prec == MRC_MIXED && opt && opt->target_residual > 0;
+    size_t need = ws_inverse(d, N, prec);
+    if (check) need = std::max(need, ws_residual(d, N, MRC_MIXED, true));
+    if ((s = ensure_ws(c, 2 * seq + need)) != MRC_OK) return s;
+    double *dA = (double *)c->ws, *dpsi = (double *)((char *)c->ws + seq);
+    if (!c->cpy) {
+        CK(cudaStreamCreateWithFlags(&c->cpy, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->ev_cpy_fork, cudaEventDisableTiming));
+        for (auto &e : c->ev_rows) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    if (prec == MRC_MIXED && (s = ensure_split_streams(c)) != MRC_OK) return s;
+    // upload A in the row ranges the Newton levels consume: [0, 2 m0), then doubling
+    if (report) CK(cudaEventRecord(c->ev0, st));
+    CK(cudaEventRecord(c->ev_cpy_fork, st));  // earlier work on st may still use the workspace
+    CK(cudaStreamWaitEvent(c->cpy, c->ev_cpy_fork, 0));
+    RowWait rw;
+    int64_t r0 = 0, r1 = std::min<int64_t>(2 * base_size(d, N), N);
+    while (r0 < N && rw.n < 32) {
+        if (rw.n == 31) r1 = N;
+        CK(cudaMemcpyAsync(dA + r0 * E, A_host + r0 * E, (size_t)(r1 - r0) * E * sizeof(double),
+                           cudaMemcpyHostToDevice, c->cpy));
+        CK(cudaEventRecord(c->ev_rows[rw.n], c->cpy));
+        rw.end[rw.n] = r1;
+        rw.ev[rw.n] = c->ev_rows[rw.n];
+        ++rw.n;
+        r0 = r1;
+        r1 = std::min<int64_t>(2 * r1, N);
+    }
+    Arena ar{(char *)c->ws + 2 * seq};
+    int levels = 0;
+    s = inverse_impl(c, ar, d, N, dA, dpsi, prec, sweeps, &levels, st, nullptr, prec == MRC_MIXED, &rw);
+    if (s != MRC_OK) return s;
+    CK(rw.wait(st, N));
+    CK(cudaMemcpyAsync(psi_host, dpsi, bytes, cudaMemcpyDeviceToHost, st));
+    if (report) {
+        CK(cudaEventRecord(c->ev1, st));
+        memset(report, 0, sizeof(*report));
+        report->res_left_l1 = report->res_right_l1 = report->res_max_abs = -1.0;
+        report->levels = levels;
+        report->sweeps = prec == MRC_MIXED ? sweeps : 0;
+        s = read_status(c, st);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        report->ms = ms;
+        if (s != MRC_OK) return s;
+        if (check) {
+            Arena ar2{(char *)c->ws + 2 * seq};
+            s = residual_impl(c, ar2, d, N, dA, dpsi, 1, nullptr, nullptr, MRC_MIXED, st, report);
             if (s != MRC_OK) return s;
             if (!(report->res_max_abs <= opt->target_residual)) return MRC_ERR_NOT_CONVERGED;
         }

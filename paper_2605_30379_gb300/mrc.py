@@ -71,6 +71,7 @@ def load():
         lib.mrc_inverse_workspace_bytes.argtypes = [I, I64, I]
         lib.mrc_inverse_workspace_bytes.restype = SZ
         lib.mrc_inverse.argtypes = [P, I, I64, P, P, ctypes.POINTER(_Options), P, ctypes.POINTER(_Report)]
+        lib.mrc_inverse_host.argtypes = [P, I, I64, P, P, ctypes.POINTER(_Options), P, ctypes.POINTER(_Report)]
         lib.mrc_inverse_batched.argtypes = [P, I, P, P, P, P, ctypes.POINTER(_Options), P, ctypes.POINTER(_Report)]
         lib.mrc_residual.argtypes = [P, I, I64, P, P, I, P, P, I, P, ctypes.POINTER(_Report)]
         lib.mrc_transition.argtypes = [P, I, I64, P, P, P, I, P]
@@ -147,6 +148,30 @@ def inverse(A, prec="fp64", sweeps=1, target_residual=0.0, report=False, out=Non
                             ctypes.byref(_opts(prec, sweeps, target_residual, autotune)), _stream(stream),
                             ctypes.byref(rep) if report else None)
     _check(st, "mrc_inverse")
+    return (psi, rep.as_dict()) if report else psi
+
+
+def inverse_host(A, prec="fp64", sweeps=1, target_residual=0.0, report=False, out=None, stream=None,
+                 autotune=False, device=None):
+    """psi = A^{(-1)} mod x^N from host memory (mrc_inverse_host): A is a CPU
+    float64 tensor [N, d, d] (pinned memory lets the upload overlap the
+    Newton levels); the result is written into `out` (a CPU tensor, pinned
+    preferred), valid once the stream has been synchronised (a report
+    synchronises)."""
+    if not (isinstance(A, torch.Tensor) and not A.is_cuda and A.dtype == torch.float64 and A.dim() == 3):
+        raise TypeError("A must be a CPU float64 tensor [N, d, d]")
+    A = A.contiguous()
+    N, d, d2 = A.shape
+    if d != d2:
+        raise ValueError("A must be square per coefficient")
+    psi = torch.empty_like(A) if out is None else out
+    if psi.is_cuda or psi.dtype != torch.float64 or psi.shape != A.shape or not psi.is_contiguous():
+        raise TypeError("out must be a contiguous CPU float64 tensor shaped like A")
+    rep = _Report()
+    st = load().mrc_inverse_host(context(device), d, N, _ptr(A), _ptr(psi),
+                                 ctypes.byref(_opts(prec, sweeps, target_residual, autotune)), _stream(stream),
+                                 ctypes.byref(rep) if report else None)
+    _check(st, "mrc_inverse_host")
     return (psi, rep.as_dict()) if report else psi
 
 

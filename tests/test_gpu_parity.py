@@ -358,6 +358,34 @@ def test_fp32_pair_product_split_matches_unsplit(mrc, d, N):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_inverse_from_host_buffers_matches_device_call(mrc, prec, pinned):
+    """mrc_inverse_host uploads A in the row ranges the Newton levels read
+    (overlapping the first levels) and copies psi back; it runs the same
+    kernels as mrc_inverse, so the results agree, pinned or pageable, and
+    match the oracle.  N = 3000 gives several upload ranges and a partial
+    last one; two calls in a row reuse the context's copy stream."""
+    q, _ = synth.weibull_model(12, 3000, seed=81)
+    A = synth.identity_minus(q)
+    ref = oracle.inverse_left(A)
+    dev_psi = mrc.inverse(dev(A), prec=prec).cpu().numpy()
+    A_host = torch.from_numpy(A)
+    if pinned:
+        A_host = A_host.pin_memory()
+    for _ in range(2):
+        out = torch.empty(A.shape, dtype=torch.float64)
+        if pinned:
+            out = out.pin_memory()
+        got, rep = mrc.inverse_host(A_host, prec=prec, out=out, report=True)
+        got = got.numpy()
+        assert np.abs(got - dev_psi).max() <= 1e-13
+        if prec == "fp64":
+            assert np.abs(got - ref).max() <= TOL64
+        else:
+            assert e_rel(got, ref) <= TOL_REL
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_reward_matches_oracle(mrc, prec):
     """V = psi * r with a rectangular reward sequence (Eq. (reward)); the oracle
     side is its direct convolution, and V must solve V = r + q * V."""
