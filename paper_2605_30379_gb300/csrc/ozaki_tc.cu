@@ -5,31 +5,34 @@
 // tensor memory (TMEM).  Square d x d with 32 <= d <= 64 (padded to 64).
 //
 // For the frequency pair {f, M-f} one CTA forms, at each frequency phi,
-//     D1 = [X_r; X_i] . Y_r,    D2 = [X_r; X_i] . Y_i        (128 x 64 each)
-//     C_r = D1[0:64] - D2[64:128],    C_i = D2[0:64] + D1[64:128].
-// Every real product is a sum over digit pairs (s, t) (digits.cuh): the
-// rows of [X_r; X_i] are scaled by 2^-sigma_i and the columns of Y by
-// 2^-tau_j, split into S balanced base-256 digits, and stored as S digit
-// tiles A_s (128 x 64, MN-major) and S tiles each for Y_r and Y_i (64 x 64,
-// K-major).  All pairs of one weight group g = s + t >= GMIN accumulate into
-// one 64-column FP32 accumulator in TMEM -- exact, since a group holds at
-// most 6 pairs of 64-term dot products of digits <= 128 (below 2^23).  The
-// group sums are then scaled by their powers of two (exact) and added top
-// group first in the working precision: a compensated double-float sum
-// (TwoSum of the high parts, error below 2^-48 of the magnitudes) for the
-// residual product, plain FP32 for the FP32 one.  Nothing here converts to
-// or from 64-bit integers: on this GPU those conversions share the narrow
-// FP64 pipe, and an int64 fold of the same sums kept it 47% busy.
+//     D = A1 . Y_r + A2 . Y_i = [C_r; C_i]                      (128 x 64),
+//     A1 = [X_r; X_i],  A2 = [-X_i; X_r],
+// i.e. C_r = X_r Y_r - X_i Y_i and C_i = X_i Y_r + X_r Y_i in one
+// accumulator.  The rows of X are scaled by 2^-sigma_i and the columns of Y
+// by 2^-tau_j, every value is split into S balanced base-256 digits
+// (digits.cuh), and each digit of X is stored once as a 192-row MN-major
+// tile [-X_i; X_r; X_i]: A1 is its rows 64..191 and A2 its rows 0..127, two
+// descriptors into the same tile.  Y_r and Y_i digits are K-major 64-row
+// tiles.  All digit pairs (s, t) of one weight group g = s + t >= GMIN
+// accumulate into one 64-column FP32 accumulator in TMEM -- exact, since a
+// group holds at most 6 pairs of two 64-term dot products of digits <= 128
+// (below 2^24).  The group sums are then scaled by their powers of two
+// (exact) and added top group first in the working precision: a compensated
+// double-float sum for the residual product, plain FP32 for the FP32 one.
+// Nothing here converts to or from 64-bit integers: on this GPU those
+// conversions share the narrow FP64 pipe.
 //
-// Schedule per frequency: all threads split X and Y into digit tiles; one
-// thread issues the MMAs of D1 (every pair, four K = 16 steps each, M = 128,
-// N = 64) and commits them to an mbarrier; all threads wait (bounded), read
-// the accumulators with tcgen05.ld and fold them; the same for D2; D1 and D2
-// then meet in shared memory (the digit tiles are free by then) and each
-// thread forms 8 complex outputs.  C(f) is stored unmerged and read back by
-// the same thread once C(M-f) is known, when both are merged into the packed
-// output spectrum (the real-FFT merge of kernels.cuh).  The kernel is
-// persistent: CTA b takes pairs b, b + grid, ...
+// Schedule per frequency, in two halves of K (k < 32, k >= 32; 120 KB of
+// digit tiles each for double-float): threads 0..255 split X and threads
+// 256..511 split Y into digit tiles; one thread issues the MMAs (every kept
+// pair, two K = 16 steps, A1 with Y_r and A2 with Y_i, M = 128, N = 64) and
+// commits them to an mbarrier; all threads wait (bounded) before the tiles
+// are rewritten.  After the second half every warp reads its lanes of the
+// accumulators with tcgen05.ld and folds them; C_r and C_i meet in shared
+// memory and each thread forms 8 complex outputs.  C(f) is stored unmerged
+// and read back by the same thread once C(M-f) is known, when both are
+// merged into the packed output spectrum (the real-FFT merge of
+// kernels.cuh).  The kernel is persistent: CTA b takes pairs b, b + grid, ...
 //
 // A bounded wait that gives up sets MRC_ERR_TIMEOUT in the status word; the
 // CTA then waits (bounded) for its MMAs in flight, frees its TMEM and exits.
@@ -40,9 +43,11 @@ namespace {
 using namespace mrc_digits;
 
 constexpr int TC_THREADS = 512;
-constexpr int TC_A_TILE = 128 * 64 * 2;  // bytes of one [X_r; X_i] digit tile
-constexpr int TC_B_TILE = 64 * 64 * 2;   // bytes of one Y_r or Y_i digit tile
-constexpr int TC_XLD = 65;               // row length (values) of the D1 / D2 exchange
+constexpr int TC_KH = 32;                  // K per half
+constexpr int TC_SBO = (TC_KH / 8) * 128;  // bytes between 8-row groups of a tile (4 K groups of 128 bytes)
+constexpr int TC_A_TILE = 192 * TC_KH * 2; // bytes of one [-X_i; X_r; X_i] digit tile (one K half)
+constexpr int TC_B_TILE = 64 * TC_KH * 2;  // bytes of one Y_r or Y_i digit tile (one K half)
+constexpr int TC_XLD = 65;                 // row length (values) of the C_r / C_i exchange
 constexpr unsigned TC_TMEM_COLS = 512;
 constexpr int TC_SPIN = 1 << 24;
 
@@ -50,23 +55,24 @@ template <class T>
 __host__ __device__ constexpr size_t tc_tiles() { return (size_t)OzP<T>::S * (TC_A_TILE + 2 * TC_B_TILE); }
 template <class T>
 __host__ __device__ constexpr size_t tc_smem() { return tc_tiles<T>() + 4 * 64 * sizeof(int); }
-static_assert((size_t)2 * 128 * TC_XLD * sizeof(dd) <= (size_t)5 * (TC_A_TILE + 2 * TC_B_TILE), "exchange fits the tiles");
+static_assert((size_t)128 * TC_XLD * sizeof(dd) <= (size_t)5 * (TC_A_TILE + 2 * TC_B_TILE), "exchange fits the tiles");
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-// Byte offset of (m, k) in an MN-major tile: 8 consecutive m in 16 bytes,
-// core matrices of 8 k rows, k groups 128 bytes apart, m groups 1024 apart.
-__device__ __forceinline__ int mn_off(int m, int k) { return (m >> 3) * 1024 + (k >> 3) * 128 + (k & 7) * 16 + (m & 7) * 2; }
+// Byte offset of (m, k) in an MN-major tile (one K half): 8 consecutive m in
+// 16 bytes, core matrices of 8 k rows, k groups 128 bytes apart, m groups
+// TC_SBO apart.
+__device__ __forceinline__ int mn_off(int m, int k) { return (m >> 3) * TC_SBO + (k >> 3) * 128 + (k & 7) * 16 + (m & 7) * 2; }
 // Byte offset of (n, k) in a K-major tile: 8 consecutive k in 16 bytes, core
-// matrices of 8 n rows, k groups 128 bytes apart, n groups 1024 apart.
-__device__ __forceinline__ int k_off(int n, int k) { return (n >> 3) * 1024 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2; }
+// matrices of 8 n rows, k groups 128 bytes apart, n groups TC_SBO apart.
+__device__ __forceinline__ int k_off(int n, int k) { return (n >> 3) * TC_SBO + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2; }
 
 // Shared-memory matrix descriptor: start address, leading-dimension byte
-// offset 128 (next 8-element K group), stride byte offset 1024 (next 8 rows
-// of M or N), the fixed 0b001 at bits 46-48, no swizzle.
+// offset 128 (next 8-element K group), stride byte offset TC_SBO (next 8
+// rows of M or N), the fixed 0b001 at bits 46-48, no swizzle.
 __device__ __forceinline__ uint64_t tc_desc(unsigned addr)
 {
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(TC_SBO >> 4) << 32) |
            ((uint64_t)1 << 46);
 }
 
@@ -115,21 +121,23 @@ __device__ __forceinline__ void tc_ld8(unsigned taddr, unsigned (&r)[8])
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
-// MMAs of one product D = [X_r; X_i] . B over every kept digit pair: group
-// g accumulates in TMEM columns 64 (g - GMIN) .. +63 (the first MMA of a
-// group overwrites, the rest accumulate).
+// MMAs of one K half of D = A1 . Y_r + A2 . Y_i over every kept digit pair:
+// group g accumulates in TMEM columns 64 (g - GMIN) .. +63; `fresh` makes
+// the first MMA of each group overwrite (the first K half).
 template <int S, int GMIN>
-__device__ __forceinline__ void tc_issue(unsigned tmem, unsigned a0, unsigned b0)
+__device__ __forceinline__ void tc_issue(unsigned tmem, unsigned a0, unsigned br0, unsigned bi0, bool fresh)
 {
     for (int g = GMIN; g <= 2 * (S - 1); ++g) {
         const unsigned dcol = tmem + (unsigned)(g - GMIN) * 64u;
-        unsigned acc = 0;
+        unsigned acc = fresh ? 0u : 1u;
         for (int s = max(0, g - (S - 1)); s <= min(S - 1, g); ++s) {
             const int t = g - s;
+            const unsigned as = a0 + s * TC_A_TILE;
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-                tc_mma(dcol, tc_desc(a0 + s * TC_A_TILE + ks * 256), tc_desc(b0 + t * TC_B_TILE + ks * 256), acc);
+            for (int ks = 0; ks < TC_KH / 16; ++ks) {
+                tc_mma(dcol, tc_desc(as + 8 * TC_SBO + ks * 256), tc_desc(br0 + t * TC_B_TILE + ks * 256), acc);
                 acc = 1;
+                tc_mma(dcol, tc_desc(as + ks * 256), tc_desc(bi0 + t * TC_B_TILE + ks * 256), 1u);
             }
         }
     }
@@ -191,31 +199,28 @@ __device__ __forceinline__ unsigned tc_pack2(float lo, float hi)
     return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
 
-__device__ __forceinline__ dd tc_scale(dd x, int e) { return {scale2(x.hi, e), scale2(x.lo, e)}; }
-__device__ __forceinline__ float tc_scale(float x, int e) { return scale2(x, e); }
-
-// Digit tiles of X(phi) (phi: packed rows ra, partner rb, twiddle w): thread
-// (m8 = tid / 64, k = tid % 64) splits the 8 entries X[8 m8 .. 8 m8 + 7][k]
-// (lanes read consecutive k: coalesced) and writes, per digit, 16 bytes of
-// 8 consecutive rows into the MN-major tile A_s (rows i: real part, rows
-// 64 + i: imaginary part).
+// Digit tiles of X(phi) for the K half k0 .. k0 + 31 (phi: packed rows ra,
+// partner rb, twiddle w): thread t < 256, (i8 = t / 32, k = t % 32), splits
+// X[8 i8 .. 8 i8 + 7][k0 + k] (lanes read consecutive k: coalesced) and
+// writes, per digit, 16 bytes of 8 consecutive rows into each of the three
+// blocks of the MN-major tile: -X_i (rows 0..63), X_r (64..127), X_i (128..191).
 template <class T>
 __device__ __forceinline__ void tc_split_x(const PairArgs &a, unsigned char *sA, const int *sig, int64_t ra,
-                                           int64_t rb, cx<T> w)
+                                           int64_t rb, cx<T> w, int k0, int t)
 {
     constexpr int S = OzP<T>::S;
     const cx<T> *ZX = reinterpret_cast<const cx<T> *>(a.zx);
     const int d = a.r;
     const int64_t E = (int64_t)d * d;
-    const int k = threadIdx.x & 63, m8 = threadIdx.x >> 6;
+    const int k = t & 31, i8 = t >> 5, kg = k0 + k;
     unsigned wr[S][4], wi[S][4];
     float pr[S], pi[S];  // digits of the even entry of each pair
 #pragma unroll
     for (int ii = 0; ii < 8; ++ii) {
-        const int i = 8 * m8 + ii;
+        const int i = 8 * i8 + ii;
         float qr[S], qi[S];
-        if (i < d && k < d) {
-            const int64_t e = (int64_t)i * d + k;
+        if (i < d && kg < d) {
+            const int64_t e = (int64_t)i * d + kg;
             const cx<T> x = split_real(ZX[ra * E + e], ZX[rb * E + e], w);
             const float sc = pow2f(-sig[i]);
             split_digits(x.re, sc, qr);
@@ -237,31 +242,35 @@ __device__ __forceinline__ void tc_split_x(const PairArgs &a, unsigned char *sA,
     }
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        unsigned char *t = sA + s * TC_A_TILE;
-        *reinterpret_cast<uint4 *>(t + mn_off(8 * m8, k)) = make_uint4(wr[s][0], wr[s][1], wr[s][2], wr[s][3]);
-        *reinterpret_cast<uint4 *>(t + mn_off(64 + 8 * m8, k)) = make_uint4(wi[s][0], wi[s][1], wi[s][2], wi[s][3]);
+        unsigned char *tl = sA + s * TC_A_TILE;
+        const uint4 vr = make_uint4(wr[s][0], wr[s][1], wr[s][2], wr[s][3]);
+        const uint4 vi = make_uint4(wi[s][0], wi[s][1], wi[s][2], wi[s][3]);
+        const uint4 vn = make_uint4(vi.x ^ 0x80008000u, vi.y ^ 0x80008000u, vi.z ^ 0x80008000u, vi.w ^ 0x80008000u);
+        *reinterpret_cast<uint4 *>(tl + mn_off(8 * i8, k)) = vn;
+        *reinterpret_cast<uint4 *>(tl + mn_off(64 + 8 * i8, k)) = vr;
+        *reinterpret_cast<uint4 *>(tl + mn_off(128 + 8 * i8, k)) = vi;
     }
 }
 
-// Digit tiles of Y(phi): thread (k8 = tid / 64, j = tid % 64) splits
-// Y[8 k8 .. 8 k8 + 7][j] (lanes read consecutive j: coalesced) and writes,
-// per digit, 16 bytes of 8 consecutive k into the K-major tiles of Y_r and
-// Y_i (row n = j).
+// Digit tiles of Y(phi) for the K half k0 .. k0 + 31: thread t < 256,
+// (k8 = t / 64, j = t % 64), splits Y[k0 + 8 k8 .. + 7][j] (lanes read
+// consecutive j: coalesced) and writes, per digit, 16 bytes of 8
+// consecutive k into the K-major tiles of Y_r and Y_i (row n = j).
 template <class T>
 __device__ __forceinline__ void tc_split_y(const PairArgs &a, unsigned char *sBr, unsigned char *sBi, const int *tau,
-                                           int64_t ra, int64_t rb, cx<T> w)
+                                           int64_t ra, int64_t rb, cx<T> w, int k0, int t)
 {
     constexpr int S = OzP<T>::S;
     const cx<T> *ZY = reinterpret_cast<const cx<T> *>(a.zy);
     const int d = a.r;
     const int64_t E = (int64_t)d * d;
-    const int j = threadIdx.x & 63, k8 = threadIdx.x >> 6;
+    const int j = t & 63, k8 = t >> 6;
     unsigned wr[S][4], wi[S][4];
     float pr[S], pi[S];
     const float sc = j < d ? pow2f(-tau[j]) : 0.0f;
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk) {
-        const int k = 8 * k8 + kk;
+        const int k = k0 + 8 * k8 + kk;
         float qr[S], qi[S];
         if (k < d && j < d) {
             const int64_t e = (int64_t)k * d + j;
@@ -292,16 +301,19 @@ __device__ __forceinline__ void tc_split_y(const PairArgs &a, unsigned char *sBr
     }
 }
 
+__device__ __forceinline__ dd tc_scale(dd x, int e) { return {scale2(x.hi, e), scale2(x.lo, e)}; }
+__device__ __forceinline__ float tc_scale(float x, int e) { return scale2(x, e); }
+
 template <class T>
 __global__ void __launch_bounds__(TC_THREADS, 1) oztc_pairmul_kernel(PairArgs a, int *status)
 {
     constexpr int S = OzP<T>::S, GMIN = OzP<T>::GMIN, NG = 2 * (S - 1) - GMIN + 1;
     static_assert(NG * 64 <= (int)TC_TMEM_COLS, "group accumulators fit in TMEM");
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *sA = smem;                 // [S] 128 x 64 MN-major
-    unsigned char *sBr = sA + S * TC_A_TILE;  // [S] 64 x 64 K-major (Y_r)
-    unsigned char *sBi = sBr + S * TC_B_TILE; // [S] 64 x 64 K-major (Y_i)
-    T *xs = reinterpret_cast<T *>(smem);      // D1 | D2 exchange (reuses the tiles)
+    unsigned char *sA = smem;                 // [S] 192 x 32 MN-major: -X_i, X_r, X_i
+    unsigned char *sBr = sA + S * TC_A_TILE;  // [S] 64 x 32 K-major (Y_r)
+    unsigned char *sBi = sBr + S * TC_B_TILE; // [S] 64 x 32 K-major (Y_i)
+    T *xs = reinterpret_cast<T *>(smem);      // C_r | C_i exchange (reuses the tiles)
     unsigned *bx = reinterpret_cast<unsigned *>(smem + tc_tiles<T>());
     unsigned *by = bx + 64;
     int *sig = reinterpret_cast<int *>(by + 64);
@@ -377,55 +389,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1) oztc_pairmul_kernel(PairArgs a,
         for (int phase = 0; phase < nfreq && !failed; ++phase) {
             const int64_t ra = phase == 0 ? f : gZ, rb = phase == 0 ? gZ : f;
             const cx<T> w = phase == 0 ? wf : wg;
-            tc_split_x<T>(a, sA, sig, ra, rb, w);
-            tc_split_y<T>(a, sBr, sBi, tau, ra, rb, w);
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // digit tiles visible to the MMAs
-            __syncthreads();
-
-            T d1[16], d2[16];
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
+            for (int kh = 0; kh < 64 / TC_KH; ++kh) {
+                if (tid < 256) tc_split_x<T>(a, sA, sig, ra, rb, w, kh * TC_KH, tid);
+                else tc_split_y<T>(a, sBr, sBi, tau, ra, rb, w, kh * TC_KH, tid - 256);
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // digit tiles visible to the MMAs
+                __syncthreads();
                 if (tid == 0) {
                     tc_fence_after();
-                    tc_issue<S, GMIN>(tmem, smem_u32(sA), smem_u32(half == 0 ? sBr : sBi));
+                    tc_issue<S, GMIN>(tmem, smem_u32(sA), smem_u32(sBr), smem_u32(sBi), kh == 0);
                     tc_commit(mb);
                 }
-                const bool ok = tc_wait(mb, parity);
+                const bool ok = tc_wait(mb, parity);  // before the tiles are rewritten or the sums read
                 parity ^= 1u;
                 if (__syncthreads_or(!ok)) {
                     failed = true;
                     break;
                 }
-                tc_fence_after();
-                if (half == 0) tc_fold<T, NG>(tmem, q, cb, d1);
-                else tc_fold<T, NG>(tmem, q, cb, d2);
-                tc_fence_before();
-                __syncthreads();  // accumulators read before the next MMAs; after D2 the tiles are free
             }
             if (failed) break;
 
-            // ---- D1 and D2 meet in shared memory; C_r = D1 top - D2 bottom, C_i = D2 top + D1 bottom
+            // ---- fold the group sums of D = [C_r; C_i]; C_r and C_i meet in shared memory
+            T dv[16];
+            tc_fence_after();
+            tc_fold<T, NG>(tmem, q, cb, dv);
+            tc_fence_before();
+            __syncthreads();  // accumulators read before the next MMAs
             {
                 const int row = 32 * q + lane;
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    xs[row * TC_XLD + cb + c] = d1[c];
-                    xs[(128 + row) * TC_XLD + cb + c] = d2[c];
-                }
+                for (int c = 0; c < 16; ++c) xs[row * TC_XLD + cb + c] = dv[c];
             }
             __syncthreads();
             {
                 const int i = tid & 63, jb = tid >> 6;
-                const T *x1 = xs, *x2 = xs + 128 * TC_XLD;
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) {
                     const int j = 8 * jb + jj;
                     if (i >= d || j >= d) continue;
-                    const T cr = Ar<T>::sub(x1[i * TC_XLD + j], x2[(64 + i) * TC_XLD + j]);
-                    const T ci = Ar<T>::add(x2[i * TC_XLD + j], x1[(64 + i) * TC_XLD + j]);
                     // the fold factored out 2^(8 (NG - 1)) of the group weights 2^(8 (g - GMIN))
                     const int ex = sig[i] + tau[j] + 8 * GMIN - 16 * S + 8 * (NG - 1);
-                    const cx<T> v = {tc_scale(cr, ex), tc_scale(ci, ex)};
+                    const cx<T> v = {tc_scale(xs[i * TC_XLD + j], ex), tc_scale(xs[(64 + i) * TC_XLD + j], ex)};
                     const int64_t e = (int64_t)i * d + j;
                     if (nfreq == 1) {
                         ZC[f * E + e] = merge_real(v, v, c_conj(wf));  // p = M/2: C(g) = C(f)
