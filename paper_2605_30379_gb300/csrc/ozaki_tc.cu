@@ -23,8 +23,8 @@
 // conversions share the narrow FP64 pipe.
 //
 // Schedule per frequency, in two halves of K (k < 32, k >= 32; 120 KB of
-// digit tiles each for double-float): threads 0..255 split X and threads
-// 256..511 split Y into digit tiles; one thread issues the MMAs (every kept
+// digit tiles each for double-float): every thread splits four entries of X
+// and then four of Y into digit tiles; one thread issues the MMAs (every kept
 // pair, two K = 16 steps, A1 with Y_r and A2 with Y_i, M = 128, N = 64) and
 // commits them to an mbarrier; all threads wait (bounded) before the tiles
 // are rewritten.  After the second half every warp reads its lanes of the
@@ -200,10 +200,11 @@ __device__ __forceinline__ unsigned tc_pack2(float lo, float hi)
 }
 
 // Digit tiles of X(phi) for the K half k0 .. k0 + 31 (phi: packed rows ra,
-// partner rb, twiddle w): thread t < 256, (i8 = t / 32, k = t % 32), splits
-// X[8 i8 .. 8 i8 + 7][k0 + k] (lanes read consecutive k: coalesced) and
-// writes, per digit, 16 bytes of 8 consecutive rows into each of the three
-// blocks of the MN-major tile: -X_i (rows 0..63), X_r (64..127), X_i (128..191).
+// partner rb, twiddle w): thread t (i4 = t / 32, k = t % 32) splits
+// X[4 i4 .. 4 i4 + 3][k0 + k] (lanes read consecutive k: coalesced) and
+// writes, per digit, 8 bytes of 4 consecutive rows into each of the three
+// blocks of the MN-major tile: -X_i (rows 0..63), X_r (64..127), X_i
+// (128..191).  All warps run this, then tc_split_y, in the same order.
 template <class T>
 __device__ __forceinline__ void tc_split_x(const PairArgs &a, unsigned char *sA, const int *sig, int64_t ra,
                                            int64_t rb, cx<T> w, int k0, int t)
@@ -212,23 +213,25 @@ __device__ __forceinline__ void tc_split_x(const PairArgs &a, unsigned char *sA,
     const cx<T> *ZX = reinterpret_cast<const cx<T> *>(a.zx);
     const int d = a.r;
     const int64_t E = (int64_t)d * d;
-    const int k = t & 31, i8 = t >> 5, kg = k0 + k;
-    unsigned wr[S][4], wi[S][4];
+    const int k = t & 31, i4 = t >> 5, kg = k0 + k;
+    cx<T> z[4][2];
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii) {  // loads first
+        const int i = 4 * i4 + ii;
+        const int64_t e = (int64_t)i * d + kg;
+        z[ii][0] = (i < d && kg < d) ? ZX[ra * E + e] : c_zero<T>();
+        z[ii][1] = (i < d && kg < d) ? ZX[rb * E + e] : c_zero<T>();
+    }
+    unsigned wr[S][2], wi[S][2];
     float pr[S], pi[S];  // digits of the even entry of each pair
 #pragma unroll
-    for (int ii = 0; ii < 8; ++ii) {
-        const int i = 8 * i8 + ii;
+    for (int ii = 0; ii < 4; ++ii) {
+        const int i = 4 * i4 + ii;
         float qr[S], qi[S];
-        if (i < d && kg < d) {
-            const int64_t e = (int64_t)i * d + kg;
-            const cx<T> x = split_real(ZX[ra * E + e], ZX[rb * E + e], w);
-            const float sc = pow2f(-sig[i]);
-            split_digits(x.re, sc, qr);
-            split_digits(x.im, sc, qi);
-        } else {
-#pragma unroll
-            for (int s = 0; s < S; ++s) qr[s] = qi[s] = 0.0f;
-        }
+        const cx<T> x = split_real(z[ii][0], z[ii][1], w);
+        const float sc = i < d ? pow2f(-sig[i]) : 0.0f;
+        split_digits(x.re, sc, qr);
+        split_digits(x.im, sc, qi);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             if (ii & 1) {
@@ -243,19 +246,17 @@ __device__ __forceinline__ void tc_split_x(const PairArgs &a, unsigned char *sA,
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         unsigned char *tl = sA + s * TC_A_TILE;
-        const uint4 vr = make_uint4(wr[s][0], wr[s][1], wr[s][2], wr[s][3]);
-        const uint4 vi = make_uint4(wi[s][0], wi[s][1], wi[s][2], wi[s][3]);
-        const uint4 vn = make_uint4(vi.x ^ 0x80008000u, vi.y ^ 0x80008000u, vi.z ^ 0x80008000u, vi.w ^ 0x80008000u);
-        *reinterpret_cast<uint4 *>(tl + mn_off(8 * i8, k)) = vn;
-        *reinterpret_cast<uint4 *>(tl + mn_off(64 + 8 * i8, k)) = vr;
-        *reinterpret_cast<uint4 *>(tl + mn_off(128 + 8 * i8, k)) = vi;
+        *reinterpret_cast<uint2 *>(tl + mn_off(4 * i4, k)) =
+            make_uint2(wi[s][0] ^ 0x80008000u, wi[s][1] ^ 0x80008000u);
+        *reinterpret_cast<uint2 *>(tl + mn_off(64 + 4 * i4, k)) = make_uint2(wr[s][0], wr[s][1]);
+        *reinterpret_cast<uint2 *>(tl + mn_off(128 + 4 * i4, k)) = make_uint2(wi[s][0], wi[s][1]);
     }
 }
 
-// Digit tiles of Y(phi) for the K half k0 .. k0 + 31: thread t < 256,
-// (k8 = t / 64, j = t % 64), splits Y[k0 + 8 k8 .. + 7][j] (lanes read
-// consecutive j: coalesced) and writes, per digit, 16 bytes of 8
-// consecutive k into the K-major tiles of Y_r and Y_i (row n = j).
+// Digit tiles of Y(phi) for the K half k0 .. k0 + 31: thread t (k4 = t / 64,
+// j = t % 64) splits Y[k0 + 4 k4 .. + 3][j] (lanes read consecutive j:
+// coalesced) and writes, per digit, 8 bytes of 4 consecutive k into the
+// K-major tiles of Y_r and Y_i (row n = j).
 template <class T>
 __device__ __forceinline__ void tc_split_y(const PairArgs &a, unsigned char *sBr, unsigned char *sBi, const int *tau,
                                            int64_t ra, int64_t rb, cx<T> w, int k0, int t)
@@ -264,23 +265,24 @@ __device__ __forceinline__ void tc_split_y(const PairArgs &a, unsigned char *sBr
     const cx<T> *ZY = reinterpret_cast<const cx<T> *>(a.zy);
     const int d = a.r;
     const int64_t E = (int64_t)d * d;
-    const int j = t & 63, k8 = t >> 6;
-    unsigned wr[S][4], wi[S][4];
+    const int j = t & 63, k4 = t >> 6;
+    cx<T> z[4][2];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {  // loads first
+        const int k = k0 + 4 * k4 + kk;
+        const int64_t e = (int64_t)k * d + j;
+        z[kk][0] = (k < d && j < d) ? ZY[ra * E + e] : c_zero<T>();
+        z[kk][1] = (k < d && j < d) ? ZY[rb * E + e] : c_zero<T>();
+    }
+    unsigned wr[S][2], wi[S][2];
     float pr[S], pi[S];
     const float sc = j < d ? pow2f(-tau[j]) : 0.0f;
 #pragma unroll
-    for (int kk = 0; kk < 8; ++kk) {
-        const int k = k0 + 8 * k8 + kk;
+    for (int kk = 0; kk < 4; ++kk) {
         float qr[S], qi[S];
-        if (k < d && j < d) {
-            const int64_t e = (int64_t)k * d + j;
-            const cx<T> y = split_real(ZY[ra * E + e], ZY[rb * E + e], w);
-            split_digits(y.re, sc, qr);
-            split_digits(y.im, sc, qi);
-        } else {
-#pragma unroll
-            for (int s = 0; s < S; ++s) qr[s] = qi[s] = 0.0f;
-        }
+        const cx<T> y = split_real(z[kk][0], z[kk][1], w);
+        split_digits(y.re, sc, qr);
+        split_digits(y.im, sc, qi);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             if (kk & 1) {
@@ -294,10 +296,8 @@ __device__ __forceinline__ void tc_split_y(const PairArgs &a, unsigned char *sBr
     }
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        *reinterpret_cast<uint4 *>(sBr + s * TC_B_TILE + k_off(j, 8 * k8)) =
-            make_uint4(wr[s][0], wr[s][1], wr[s][2], wr[s][3]);
-        *reinterpret_cast<uint4 *>(sBi + s * TC_B_TILE + k_off(j, 8 * k8)) =
-            make_uint4(wi[s][0], wi[s][1], wi[s][2], wi[s][3]);
+        *reinterpret_cast<uint2 *>(sBr + s * TC_B_TILE + k_off(j, 4 * k4)) = make_uint2(wr[s][0], wr[s][1]);
+        *reinterpret_cast<uint2 *>(sBi + s * TC_B_TILE + k_off(j, 4 * k4)) = make_uint2(wi[s][0], wi[s][1]);
     }
 }
 
@@ -390,8 +390,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) oztc_pairmul_kernel(PairArgs a,
             const int64_t ra = phase == 0 ? f : gZ, rb = phase == 0 ? gZ : f;
             const cx<T> w = phase == 0 ? wf : wg;
             for (int kh = 0; kh < 64 / TC_KH; ++kh) {
-                if (tid < 256) tc_split_x<T>(a, sA, sig, ra, rb, w, kh * TC_KH, tid);
-                else tc_split_y<T>(a, sBr, sBi, tau, ra, rb, w, kh * TC_KH, tid - 256);
+                tc_split_x<T>(a, sA, sig, ra, rb, w, kh * TC_KH, tid);
+                tc_split_y<T>(a, sBr, sBi, tau, ra, rb, w, kh * TC_KH, tid);
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // digit tiles visible to the MMAs
                 __syncthreads();
                 if (tid == 0) {
