@@ -34,6 +34,8 @@ import time
 
 import numpy as np
 
+HERE = os.path.dirname(os.path.abspath(__file__))
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -101,6 +103,36 @@ def roofline_for(kclass, ms_total, launches, bytes_, flops, peaks, sm_mhz):
     return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
             "frac": ach / peak, "traffic": None, "launches": launches, "avg_ms": per_ms,
             "peak_source": f"FP32 FFMA: 152x128 lanes x 2 x {clk/1e6:.0f} MHz"}
+
+
+def sources_digest():
+    """sha256 over the kernel sources (csrc/ and the C header), as recorded
+    beside an ncu traffic capture."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(HERE, "paper_2605_30379_gb300", "csrc")
+    files = [os.path.join("paper_2605_30379_gb300/csrc", f) for f in sorted(os.listdir(csrc))] + ["include/mrc.h"]
+    for f in files:
+        h.update(f.encode())
+        with open(os.path.join(HERE, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(workload, kclass):
+    """DRAM bytes per launch of kernel class `kclass` (dram__bytes_read.sum +
+    dram__bytes_write.sum, averaged over the class's launches in one step)
+    from the committed ncu capture of this workload -- only while the kernel
+    sources are the ones the capture was taken on; else None."""
+    path = os.path.join(HERE, "profiles", f"traffic_{workload}.json")
+    try:
+        with open(path) as fh:
+            doc = json.load(fh)
+    except (OSError, ValueError):
+        return None, None
+    if doc.get("sources_sha256") != sources_digest() or kclass not in doc.get("classes", {}):
+        return None, None
+    return doc["classes"][kclass]["dram_bytes_per_launch"], os.path.relpath(path, HERE)
 
 
 class ClockSampler:
@@ -393,6 +425,7 @@ def main():
                         clocks["sm_mhz"] if clocks else None)
     if roof:
         roof["peak_kind"] = peak_kind
+        roof["traffic"], roof["traffic_source"] = measured_traffic(args.workload, roof["kernel"])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
