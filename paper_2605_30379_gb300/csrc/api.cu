@@ -251,7 +251,7 @@ int tuned_choice(mrc_ctx *cx, int prec, const void *zx, const void *zy, void *zc
     if (it != cx->tune.end()) return it->second;
     if (cx->capturing) return -1;
     int cands[4] = {0, 1, 2, 3};
-    const int nc = (prec == PREC_DD && mrc_ozaki_supported(r, m, c)) ? 4 : 3;
+    const int nc = (prec == PREC_DD && mrc_tc_supported(r, m, c)) ? 4 : 3;
     float best = 1e30f;
     int pick = -1;
     for (int k = 0; k < nc; ++k) {
@@ -298,7 +298,8 @@ cudaError_t pairmul_any(mrc_ctx *cx, int prec, const void *zx, const void *zy, v
     }
     if (prec == PREC_DD && mrc_tc_supported(r, m, c) && !env_is_simt("MRC_DD_PRODUCT")) {
         const char *dv = getenv("MRC_DD_PRODUCT");
-        if (dv && strcmp(dv, "mma") == 0) return mrc_pairmul_dd_ozaki(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
+        if (dv && strcmp(dv, "mma") == 0 && mrc_ozaki_supported(r, m, c))
+            return mrc_pairmul_dd_ozaki(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
         return mrc_pairmul_dd_tc(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
     }
     return OPS[prec].pairmul(zx, zy, zc, M, r, m, c, tw, MRC_TW_LOG, st);

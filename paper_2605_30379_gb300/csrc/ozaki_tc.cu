@@ -2,9 +2,13 @@
 // (Eq. (fft-convolution): C(phi) = X(phi) Y(phi) at every frequency of the
 // half spectrum) as exact digit products on the fifth-generation tensor
 // cores: tcgen05.mma, BF16 operands in shared memory, FP32 accumulators in
-// tensor memory (TMEM).  Square d x d with 32 <= d <= 64 (padded to 64).
+// tensor memory (TMEM).  Square d x d with 32 <= d <= 512: 64 x 64 output
+// tiles (padded), K in chunks of 64 whose group sums are exact and are added
+// in the working precision; the row and column scalings are taken once per
+// frequency pair over whole rows and columns.
 //
-// For the frequency pair {f, M-f} one CTA forms, at each frequency phi,
+// For the frequency pair {f, M-f} one CTA forms, at each frequency phi and
+// for each output tile and K chunk,
 //     D = A1 . Y_r + A2 . Y_i = [C_r; C_i]                      (128 x 64),
 //     A1 = [X_r; X_i],  A2 = [-X_i; X_r],
 // i.e. C_r = X_r Y_r - X_i Y_i and C_i = X_i Y_r + X_r Y_i in one
@@ -53,9 +57,17 @@ constexpr int TC_SPIN = 1 << 24;
 
 template <class T>
 __host__ __device__ constexpr size_t tc_tiles() { return (size_t)OzP<T>::S * (TC_A_TILE + 2 * TC_B_TILE); }
+constexpr int TC_DMAX = 512;  // largest d (rows of X / columns of Y whose scalings are kept)
+// digit tiles | the 128 x 64 output-tile accumulator (C_r; C_i rows) | row and column bounds and exponents
 template <class T>
-__host__ __device__ constexpr size_t tc_smem() { return tc_tiles<T>() + 4 * 64 * sizeof(int); }
+__host__ __device__ constexpr size_t tc_xs_off() { return tc_tiles<T>(); }
+template <class T>
+__host__ __device__ constexpr size_t tc_small_bounds_off() { return tc_tiles<T>(); }
+template <class T>
+__host__ __device__ constexpr size_t tc_small_smem() { return tc_tiles<T>() + 4 * 64 * sizeof(int); }
 static_assert((size_t)128 * TC_XLD * sizeof(dd) <= (size_t)5 * (TC_A_TILE + 2 * TC_B_TILE), "exchange fits the tiles");
+template <class T>
+__host__ __device__ constexpr size_t tc_smem() { return tc_tiles<T>() + (size_t)128 * TC_XLD * sizeof(T) + 4 * TC_DMAX * sizeof(int); }
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -207,7 +219,7 @@ __device__ __forceinline__ unsigned tc_pack2(float lo, float hi)
 // (128..191).  All warps run this, then tc_split_y, in the same order.
 template <class T>
 __device__ __forceinline__ void tc_split_x(const PairArgs &a, unsigned char *sA, const int *sig, int64_t ra,
-                                           int64_t rb, cx<T> w, int k0, int t)
+                                           int64_t rb, cx<T> w, int i0, int k0, int t)
 {
     constexpr int S = OzP<T>::S;
     const cx<T> *ZX = reinterpret_cast<const cx<T> *>(a.zx);
@@ -217,7 +229,7 @@ __device__ __forceinline__ void tc_split_x(const PairArgs &a, unsigned char *sA,
     cx<T> z[4][2];
 #pragma unroll
     for (int ii = 0; ii < 4; ++ii) {  // loads first
-        const int i = 4 * i4 + ii;
+        const int i = i0 + 4 * i4 + ii;
         const int64_t e = (int64_t)i * d + kg;
         z[ii][0] = (i < d && kg < d) ? ZX[ra * E + e] : c_zero<T>();
         z[ii][1] = (i < d && kg < d) ? ZX[rb * E + e] : c_zero<T>();
@@ -226,7 +238,7 @@ __device__ __forceinline__ void tc_split_x(const PairArgs &a, unsigned char *sA,
     float pr[S], pi[S];  // digits of the even entry of each pair
 #pragma unroll
     for (int ii = 0; ii < 4; ++ii) {
-        const int i = 4 * i4 + ii;
+        const int i = i0 + 4 * i4 + ii;
         float qr[S], qi[S];
         const cx<T> x = split_real(z[ii][0], z[ii][1], w);
         const float sc = i < d ? pow2f(-sig[i]) : 0.0f;
@@ -259,13 +271,13 @@ __device__ __forceinline__ void tc_split_x(const PairArgs &a, unsigned char *sA,
 // K-major tiles of Y_r and Y_i (row n = j).
 template <class T>
 __device__ __forceinline__ void tc_split_y(const PairArgs &a, unsigned char *sBr, unsigned char *sBi, const int *tau,
-                                           int64_t ra, int64_t rb, cx<T> w, int k0, int t)
+                                           int64_t ra, int64_t rb, cx<T> w, int j0, int k0, int t)
 {
     constexpr int S = OzP<T>::S;
     const cx<T> *ZY = reinterpret_cast<const cx<T> *>(a.zy);
     const int d = a.r;
     const int64_t E = (int64_t)d * d;
-    const int j = t & 63, k4 = t >> 6;
+    const int jt = t & 63, k4 = t >> 6, j = j0 + jt;
     cx<T> z[4][2];
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {  // loads first
@@ -296,14 +308,18 @@ __device__ __forceinline__ void tc_split_y(const PairArgs &a, unsigned char *sBr
     }
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        *reinterpret_cast<uint2 *>(sBr + s * TC_B_TILE + k_off(j, 4 * k4)) = make_uint2(wr[s][0], wr[s][1]);
-        *reinterpret_cast<uint2 *>(sBi + s * TC_B_TILE + k_off(j, 4 * k4)) = make_uint2(wi[s][0], wi[s][1]);
+        *reinterpret_cast<uint2 *>(sBr + s * TC_B_TILE + k_off(jt, 4 * k4)) = make_uint2(wr[s][0], wr[s][1]);
+        *reinterpret_cast<uint2 *>(sBi + s * TC_B_TILE + k_off(jt, 4 * k4)) = make_uint2(wi[s][0], wi[s][1]);
     }
 }
 
 __device__ __forceinline__ dd tc_scale(dd x, int e) { return {scale2(x.hi, e), scale2(x.lo, e)}; }
 __device__ __forceinline__ float tc_scale(float x, int e) { return scale2(x, e); }
 
+// d <= 64: one output tile and one K chunk per frequency; the exchange of
+// C_r and C_i reuses the digit tiles and the bounds sit right after them
+// (a smaller and tighter kernel than the tiled one below, which it matches
+// result for result).
 template <class T>
 __global__ void __launch_bounds__(TC_THREADS, 1) oztc_pairmul_kernel(PairArgs a, int *status)
 {
@@ -314,7 +330,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) oztc_pairmul_kernel(PairArgs a,
     unsigned char *sBr = sA + S * TC_A_TILE;  // [S] 64 x 32 K-major (Y_r)
     unsigned char *sBi = sBr + S * TC_B_TILE; // [S] 64 x 32 K-major (Y_i)
     T *xs = reinterpret_cast<T *>(smem);      // C_r | C_i exchange (reuses the tiles)
-    unsigned *bx = reinterpret_cast<unsigned *>(smem + tc_tiles<T>());
+    unsigned *bx = reinterpret_cast<unsigned *>(smem + tc_small_bounds_off<T>());
     unsigned *by = bx + 64;
     int *sig = reinterpret_cast<int *>(by + 64);
     int *tau = sig + 64;
@@ -390,8 +406,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) oztc_pairmul_kernel(PairArgs a,
             const int64_t ra = phase == 0 ? f : gZ, rb = phase == 0 ? gZ : f;
             const cx<T> w = phase == 0 ? wf : wg;
             for (int kh = 0; kh < 64 / TC_KH; ++kh) {
-                tc_split_x<T>(a, sA, sig, ra, rb, w, kh * TC_KH, tid);
-                tc_split_y<T>(a, sBr, sBi, tau, ra, rb, w, kh * TC_KH, tid);
+                tc_split_x<T>(a, sA, sig, ra, rb, w, 0, kh * TC_KH, tid);
+                tc_split_y<T>(a, sBr, sBi, tau, ra, rb, w, 0, kh * TC_KH, tid);
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // digit tiles visible to the MMAs
                 __syncthreads();
                 if (tid == 0) {
@@ -458,17 +474,191 @@ __global__ void __launch_bounds__(TC_THREADS, 1) oztc_pairmul_kernel(PairArgs a,
     }
 }
 
+// d > 64: 64 x 64 output tiles and 64-deep K chunks.
+template <class T>
+__global__ void __launch_bounds__(TC_THREADS, 1) oztc_tiled_kernel(PairArgs a, int *status)
+{
+    constexpr int S = OzP<T>::S, GMIN = OzP<T>::GMIN, NG = 2 * (S - 1) - GMIN + 1;
+    static_assert(NG * 64 <= (int)TC_TMEM_COLS, "group accumulators fit in TMEM");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *sA = smem;                 // [S] 192 x 32 MN-major: -X_i, X_r, X_i
+    unsigned char *sBr = sA + S * TC_A_TILE;  // [S] 64 x 32 K-major (Y_r)
+    unsigned char *sBi = sBr + S * TC_B_TILE; // [S] 64 x 32 K-major (Y_i)
+    T *xs = reinterpret_cast<T *>(smem + tc_xs_off<T>());  // [C_r; C_i] of one output tile, summed over K chunks
+    unsigned *bx = reinterpret_cast<unsigned *>(xs + 128 * TC_XLD);
+    unsigned *by = bx + TC_DMAX;
+    int *sig = reinterpret_cast<int *>(by + TC_DMAX);
+    int *tau = sig + TC_DMAX;
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ unsigned tslot;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned mb = smem_u32(&mbar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tslot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = tslot;
+    unsigned parity = 0;
+    bool failed = false;
+
+    const cx<T> *ZX = reinterpret_cast<const cx<T> *>(a.zx);
+    const cx<T> *ZY = reinterpret_cast<const cx<T> *>(a.zy);
+    cx<T> *ZC = reinterpret_cast<cx<T> *>(a.zc);
+    const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
+    const int d = a.r, nt = (d + 63) / 64;  // 64 x 64 output tiles per side, 64-deep K chunks
+    const int64_t E = (int64_t)d * d, M = a.M;
+    const int q = warp & 3, cb = (warp >> 2) * 16;  // TMEM lanes 32 q .., columns cb .. cb + 15
+
+    for (int64_t p = blockIdx.x; p < a.npairs && !failed; p += gridDim.x) {
+        const int64_t f = p, gL = M - p, gZ = gL & (M - 1);
+        const cx<T> wf = tw[f << (a.tw_log - a.logM - 1)];
+        const cx<T> wg = c_neg(c_conj(wf));
+        const bool two = (gZ != f);
+        const int nfreq = (gL == f) ? 1 : 2;  // p = M/2 pairs with itself
+
+        // ---- row bounds of X (a warp per row) and column bounds of Y (eight
+        // threads per column, rows k = kq, kq + 8, ...) over both
+        // frequencies: |Xh(f)|, |Xh(g)| <= |Z(f)| + |Z(g)| entrywise
+        for (int j = tid; j < d; j += TC_THREADS) by[j] = 0u;
+        __syncthreads();
+        for (int i = warp; i < d; i += TC_THREADS / 32) {
+            float mx = 0.0f;
+            for (int k = lane; k < d; k += 32) {
+                const int64_t e = (int64_t)i * d + k;
+                const cx<T> xa = ZX[f * E + e], xb = ZX[gZ * E + e];
+                mx = fmaxf(mx, fabsf(hi_part(xa.re)) + fabsf(hi_part(xa.im)) + fabsf(hi_part(xb.re)) +
+                                   fabsf(hi_part(xb.im)));
+            }
+            mx = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(mx)));
+            if (lane == 0) sig[i] = scale_exp(mx);
+        }
+        for (int jb = 0; jb < nt; ++jb) {
+            const int j = 64 * jb + (tid & 63);
+            if (j >= d) continue;
+            float my = 0.0f;
+            for (int k = tid >> 6; k < d; k += TC_THREADS / 64) {
+                const int64_t e = (int64_t)k * d + j;
+                const cx<T> ya = ZY[f * E + e], yb = ZY[gZ * E + e];
+                my = fmaxf(my, fabsf(hi_part(ya.re)) + fabsf(hi_part(ya.im)) + fabsf(hi_part(yb.re)) +
+                                   fabsf(hi_part(yb.im)));
+            }
+            atomicMax(&by[j], __float_as_uint(my));  // nonnegative floats order as their bits
+        }
+        __syncthreads();
+        for (int j = tid; j < d; j += TC_THREADS) tau[j] = scale_exp(__uint_as_float(by[j]));
+        __syncthreads();
+
+        for (int tile = 0; tile < nt * nt && !failed; ++tile) {
+            const int i0 = (tile / nt) * 64, j0 = (tile % nt) * 64;
+            for (int phase = 0; phase < nfreq && !failed; ++phase) {
+                const int64_t ra = phase == 0 ? f : gZ, rb = phase == 0 ? gZ : f;
+                const cx<T> w = phase == 0 ? wf : wg;
+                for (int kc = 0; kc < nt && !failed; ++kc) {
+                    for (int kh = 0; kh < 64 / TC_KH; ++kh) {
+                        const int k0 = 64 * kc + kh * TC_KH;
+                        tc_split_x<T>(a, sA, sig, ra, rb, w, i0, k0, tid);
+                        tc_split_y<T>(a, sBr, sBi, tau, ra, rb, w, j0, k0, tid);
+                        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // tiles visible to the MMAs
+                        __syncthreads();
+                        if (tid == 0) {
+                            tc_fence_after();
+                            tc_issue<S, GMIN>(tmem, smem_u32(sA), smem_u32(sBr), smem_u32(sBi), kh == 0);
+                            tc_commit(mb);
+                        }
+                        const bool ok = tc_wait(mb, parity);  // before the tiles are rewritten or the sums read
+                        parity ^= 1u;
+                        if (__syncthreads_or(!ok)) {
+                            failed = true;
+                            break;
+                        }
+                    }
+                    if (failed) break;
+                    // ---- fold this K chunk's group sums (exact per chunk) into the tile accumulator
+                    T dv[16];
+                    tc_fence_after();
+                    tc_fold<T, NG>(tmem, q, cb, dv);
+                    tc_fence_before();
+                    T *xr = xs + (32 * q + lane) * TC_XLD + cb;
+                    if (kc == 0) {
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) xr[c] = dv[c];
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) xr[c] = Ar<T>::add(xr[c], dv[c]);
+                    }
+                }
+                if (failed) break;
+                __syncthreads();  // the tile's C_r and C_i complete in shared memory
+                {
+                    const int i = tid & 63, jb = tid >> 6;
+                    const int gi = i0 + i;
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+                        const int gj = j0 + 8 * jb + jj;
+                        if (gi >= d || gj >= d) continue;
+                        // the fold factored out 2^(8 (NG - 1)) of the group weights 2^(8 (g - GMIN))
+                        const int ex = sig[gi] + tau[gj] + 8 * GMIN - 16 * S + 8 * (NG - 1);
+                        const cx<T> v = {tc_scale(xs[i * TC_XLD + 8 * jb + jj], ex),
+                                         tc_scale(xs[(64 + i) * TC_XLD + 8 * jb + jj], ex)};
+                        const int64_t e = (int64_t)gi * d + gj;
+                        if (nfreq == 1) {
+                            ZC[f * E + e] = merge_real(v, v, c_conj(wf));  // p = M/2: C(g) = C(f)
+                        } else if (phase == 0) {
+                            ZC[f * E + e] = v;  // C(f), merged once C(g) is known (same thread)
+                        } else {
+                            const cx<T> cf = ZC[f * E + e];
+                            ZC[f * E + e] = merge_real(cf, v, c_conj(wf));
+                            if (two) ZC[gZ * E + e] = merge_real(v, cf, c_conj(wg));
+                        }
+                    }
+                }
+                __syncthreads();  // the tile accumulator is read before the next tile's first fold
+            }
+        }
+        __syncthreads();  // bounds of this pair are read before the next pair's
+    }
+
+    if (failed) {
+        if (tid == 0 && status) atomicExch(status, 6);
+        tc_wait(mb, parity);  // let MMAs still in flight finish before the TMEM is freed
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
 } // namespace
 
-bool mrc_tc_supported(int r, int m, int c) { return r == m && m == c && r >= 32 && r <= 64; }
+bool mrc_tc_supported(int r, int m, int c) { return r == m && m == c && r >= 32 && r <= TC_DMAX; }
 
 cudaError_t mrc_tc_init(void)
 {
     cudaError_t e = cudaFuncSetAttribute(oztc_pairmul_kernel<dd>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tc_smem<dd>());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(oztc_pairmul_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)tc_smem<float>());
+                                         (int)tc_small_smem<dd>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(oztc_pairmul_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tc_small_smem<float>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(oztc_tiled_kernel<dd>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tc_smem<dd>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(oztc_tiled_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tc_smem<float>());
+    return e;
 }
 
 template <class T>
@@ -493,7 +683,8 @@ static cudaError_t tc_run(const void *zx, const void *zy, void *zc, int64_t M, i
     const double bytes = (double)M * 3.0 * d * d * sizeof(cx<T>);
     const double flops = 8.0 * d * d * d * (double)(M + 1);
     mrc_prof_pre(kclass, st);
-    oztc_pairmul_kernel<T><<<grid, TC_THREADS, tc_smem<T>(), st>>>(a, mrc_status_word());
+    if (d <= 64) oztc_pairmul_kernel<T><<<grid, TC_THREADS, tc_small_smem<T>(), st>>>(a, mrc_status_word());
+    else oztc_tiled_kernel<T><<<grid, TC_THREADS, tc_smem<T>(), st>>>(a, mrc_status_word());
     mrc_prof_post(kclass, st, bytes, flops);
     return cudaGetLastError();
 }
