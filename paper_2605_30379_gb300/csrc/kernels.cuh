@@ -417,6 +417,25 @@ __global__ void __launch_bounds__(FftPlan<T, LOGR, EC>::NT) fft_pass_kernel(FftA
     else fft_pass_body<T, LOGR, EC, false>(a);
 }
 
+// The same pass with a minimum of resident CTAs per SM (MRC_FFT32_MINB x 512
+// threads; 0 at build time = off), used for the FP32 passes of at most 8
+// points per thread.  With 4 (2048 threads: 32 registers, a 40-byte spill)
+// the FP32 passes are latency-bound at full occupancy instead of 75 %: FP32
+// FFT 89.5 -> 83.5 ms at d = 64, N = 2^18.  Not for the double-float passes:
+// there an explicit minimum, even of 1, raised ptxas's register choice from
+// 64 to 96-109.
+#ifndef MRC_FFT32_MINB
+#define MRC_FFT32_MINB 4
+#endif
+template <class T, int LOGR, int EC>
+__global__ void __launch_bounds__(FftPlan<T, LOGR, EC>::NT,
+                                  MRC_FFT32_MINB > 0 ? (MRC_FFT32_MINB * 512) / FftPlan<T, LOGR, EC>::NT : 1)
+    fft_pass_kernel_mb(FftArgs a)
+{
+    if (a.dir > 0) fft_pass_body<T, LOGR, EC, true>(a);
+    else fft_pass_body<T, LOGR, EC, false>(a);
+}
+
 // ---------------------------------------------------------------------------
 // Persistent pipelined pass.  The same Stockham pass as fft_pass_kernel, but
 // each CTA loops over tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... with
@@ -838,11 +857,20 @@ constexpr FftKernel fft_pipe_or_null()
     else return nullptr;
 }
 
+template <class T, int L, int EC>
+constexpr FftKernel fft_pass_or_mb()
+{
+    if constexpr (MRC_FFT32_MINB > 0 && sizeof(cx<T>) == 8 && FftPlan<T, L, EC>::EPT <= 8 &&
+                  FftPlan<T, L, EC>::NT <= MRC_FFT32_MINB * 512)
+        return fft_pass_kernel_mb<T, L, EC>;
+    else return fft_pass_kernel<T, L, EC>;
+}
+
 template <class T, int OFF, int... L>
 void fft_fill_shifted(FftEntry (*t)[11], std::integer_sequence<int, L...>)
 {
     constexpr int ECD = fft_default_ec<T>();
-    ((t[0][OFF + L] = FftEntry{fft_pass_kernel<T, OFF + L, ECD>, FftPlan<T, OFF + L, ECD>::NT,
+    ((t[0][OFF + L] = FftEntry{fft_pass_or_mb<T, OFF + L, ECD>(), FftPlan<T, OFF + L, ECD>::NT,
                                fft_pipe_or_null<T, OFF + L, ECD>()}), ...);
     ((t[1][OFF + L] = FftEntry{fft_pass_kernel<T, OFF + L, 4>, FftPlan<T, OFF + L, 4>::NT, nullptr}), ...);
 }
