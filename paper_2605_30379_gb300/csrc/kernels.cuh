@@ -681,9 +681,11 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) pairmul_kernel(PairArgs
 // lets two CTAs share an SM.  Each thread's TM rows and TN columns are
 // contiguous in shared memory; the Y tile stores column tx * TN + v at
 // (v / 2) * 2 NTX + 2 tx + v % 2, so that the 16-byte loads of the FP32
-// kernel fall on consecutive addresses across tx.  After the k loop the g
-// half hands C(g) to the f half through shared memory (the tiles' space),
-// which merges both into the packed output spectrum.
+// kernel fall on consecutive addresses across tx.  The k tiles are double
+// buffered: the next tile's spectra are loaded into registers before the
+// current tile is multiplied and split into the other buffer after it.
+// After the k loop the g half hands C(g) to the f half through shared memory
+// (the tiles' space), which merges both into the packed output spectrum.
 template <int NTX, int TN>
 __device__ __forceinline__ int pm2_ycol(int jj)
 {
@@ -698,10 +700,9 @@ __global__ void __launch_bounds__(2 * (BM / TM) * (BN / TN), 2) pairmul2_kernel(
     constexpr int XLD = BM + (sizeof(cx<T>) == 8 ? 2 : 1), YLD = BN + (sizeof(cx<T>) == 8 ? 2 : 1);
     constexpr int TILE = 2 * BK * (XLD + YLD);  // complex values: X and Y tiles of both frequencies
     constexpr int XCH = BM * YLD;               // the C(g) exchange
+    constexpr int XPT = (BM * BK + NT - 1) / NT, YPT = (BK * BN + NT - 1) / NT;  // fill items per thread
     static_assert(TN % 2 == 0, "column pairs");
-    __shared__ __align__(16) cx<T> sbuf[TILE > XCH ? TILE : XCH];
-    cx<T> *Xs = sbuf;                  // [2][BK][XLD]
-    cx<T> *Ys = sbuf + 2 * BK * XLD;   // [2][BK][YLD], permuted columns
+    __shared__ __align__(16) cx<T> sbuf[2 * TILE > XCH ? 2 * TILE : XCH];  // two tile buffers
     const cx<T> *ZX = reinterpret_cast<const cx<T> *>(a.zx);
     const cx<T> *ZY = reinterpret_cast<const cx<T> *>(a.zy);
     cx<T> *ZC = reinterpret_cast<cx<T> *>(a.zc);
@@ -719,39 +720,63 @@ __global__ void __launch_bounds__(2 * (BM / TM) * (BN / TN), 2) pairmul2_kernel(
     const cx<T> *xf = ZX + f * EX, *xg = ZX + gZ * EX;
     const cx<T> *yf = ZY + f * EY, *yg = ZY + gZ * EY;
 
+    // raw spectra of the next k tile, held in registers while the current one is multiplied
+    cx<T> rx[XPT][2], ry[YPT][2];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int n = 0; n < XPT; ++n) {
+            const int idx = threadIdx.x + n * NT;
+            const int ii = idx / BK, kk = idx - (idx / BK) * BK;
+            const int i = i0 + ii, k = k0 + kk;
+            const bool ok = idx < BM * BK && i < a.r && k < a.m;
+            rx[n][0] = ok ? xf[(int64_t)i * a.m + k] : c_zero<T>();
+            rx[n][1] = ok ? xg[(int64_t)i * a.m + k] : c_zero<T>();
+        }
+#pragma unroll
+        for (int n = 0; n < YPT; ++n) {
+            const int idx = threadIdx.x + n * NT;
+            const int kk = idx / BN, jj = idx - (idx / BN) * BN;
+            const int k = k0 + kk, jx = j0 + jj;
+            const bool ok = idx < BK * BN && k < a.m && jx < a.c;
+            ry[n][0] = ok ? yf[(int64_t)k * a.c + jx] : c_zero<T>();
+            ry[n][1] = ok ? yg[(int64_t)k * a.c + jx] : c_zero<T>();
+        }
+    };
+    auto store = [&](cx<T> *buf) {
+        cx<T> *Xs = buf, *Ys = buf + 2 * BK * XLD;
+#pragma unroll
+        for (int n = 0; n < XPT; ++n) {
+            const int idx = threadIdx.x + n * NT;
+            if (idx >= BM * BK) break;
+            const int ii = idx / BK, kk = idx - (idx / BK) * BK;
+            Xs[kk * XLD + ii] = split_real(rx[n][0], rx[n][1], wf);
+            Xs[(BK + kk) * XLD + ii] = split_real(rx[n][1], rx[n][0], wg);
+        }
+#pragma unroll
+        for (int n = 0; n < YPT; ++n) {
+            const int idx = threadIdx.x + n * NT;
+            if (idx >= BK * BN) break;
+            const int kk = idx / BN, jj = idx - (idx / BN) * BN;
+            const int pc = pm2_ycol<NTX, TN>(jj);
+            Ys[kk * YLD + pc] = split_real(ry[n][0], ry[n][1], wf);
+            Ys[(BK + kk) * YLD + pc] = split_real(ry[n][1], ry[n][0], wg);
+        }
+    };
+
     cx<T> acc[TM][TN];
 #pragma unroll
     for (int u = 0; u < TM; ++u)
 #pragma unroll
         for (int v = 0; v < TN; ++v) acc[u][v] = c_zero<T>();
 
+    load(0);
+    store(sbuf);
+    __syncthreads();
+    int cur = 0;
     for (int k0 = 0; k0 < a.m; k0 += BK) {
-        for (int idx = threadIdx.x; idx < BM * BK; idx += NT) {
-            const int ii = idx / BK, kk = idx - (idx / BK) * BK;
-            const int i = i0 + ii, k = k0 + kk;
-            cx<T> vf = c_zero<T>(), vg = c_zero<T>();
-            if (i < a.r && k < a.m) {
-                const cx<T> za = xf[(int64_t)i * a.m + k], zb = xg[(int64_t)i * a.m + k];
-                vf = split_real(za, zb, wf);
-                vg = split_real(zb, za, wg);
-            }
-            Xs[kk * XLD + ii] = vf;
-            Xs[(BK + kk) * XLD + ii] = vg;
-        }
-        for (int idx = threadIdx.x; idx < BK * BN; idx += NT) {
-            const int kk = idx / BN, jj = idx - (idx / BN) * BN;
-            const int k = k0 + kk, jx = j0 + jj;
-            cx<T> vf = c_zero<T>(), vg = c_zero<T>();
-            if (k < a.m && jx < a.c) {
-                const cx<T> za = yf[(int64_t)k * a.c + jx], zb = yg[(int64_t)k * a.c + jx];
-                vf = split_real(za, zb, wf);
-                vg = split_real(zb, za, wg);
-            }
-            const int pc = pm2_ycol<NTX, TN>(jj);
-            Ys[kk * YLD + pc] = vf;
-            Ys[(BK + kk) * YLD + pc] = vg;
-        }
-        __syncthreads();
+        const bool more = k0 + BK < a.m;
+        if (more) load(k0 + BK);  // in flight while this tile is multiplied
+        const cx<T> *Xs = sbuf + cur * TILE, *Ys = Xs + 2 * BK * XLD;
         const cx<T> *xb = Xs + fq * BK * XLD + ty * TM;
         const cx<T> *yb = Ys + fq * BK * YLD + 2 * tx;
 #pragma unroll 4
@@ -769,7 +794,9 @@ __global__ void __launch_bounds__(2 * (BM / TM) * (BN / TN), 2) pairmul2_kernel(
 #pragma unroll
                 for (int v = 0; v < TN; ++v) c_mac(acc[u][v], xa[u], ya[v]);
         }
+        if (more) store(sbuf + (cur ^ 1) * TILE);  // the other buffer: last read two tiles ago
         __syncthreads();
+        cur ^= 1;
     }
 
     // C(g) to shared memory, then the f half merges both
