@@ -16,6 +16,9 @@ Every function follows a definition in Kordalis & Trevezas (arXiv 2605.30379):
 * ``first_entrance`` -- Eqs. (first-entrance-mass), (first-entrance-cdf)
 * ``occupation``     -- A_B(k) = alpha P(k) 1_{E,B} (Table 2; availability)
 * ``renewal_visits`` -- Eq. (renewal-visits)
+* ``mean_value_terms`` / ``mre_solve`` -- the endpoint mean-value rule and
+                        Eq. (mre-solution) for K = L + Q * K in continuous time
+* ``process_discretization`` -- Eq. (process-discretization)
 * ``norm1_frob`` / ``norm1_spec`` -- the horizon norm ||.||_{1,N} of Section 2
 
 Parity pins for each of these live in ``tests/test_oracle_pins.py``.
@@ -228,3 +231,44 @@ def spectral_norm(M):
     M = _f64(M)
     r, c = M.shape
     return float(_load().orc_spectral_norm(r, c, _ptr(M)))
+
+
+def mean_value_terms(Qs):
+    """The endpoint mean-value rule of Section 4: from the kernel samples
+    Q_h(m) = Q(mh), m = 0 .. n (the extra value Q_h(n) serves Delta+ at
+    n - 1), the increments Delta Q_h(0) = O, Delta Q_h(m) = Q_h(m) - Q_h(m-1),
+    Delta+ Q_h(m) = Delta Q_h(m+1) and Qbar_h(m) = (Delta Q_h(m) +
+    Delta+ Q_h(m)) / 2 for m = 0 .. n-1.  Returns (dQ, dQplus, Qbar)."""
+    Qs = _f64(Qs)
+    n = Qs.shape[0] - 1
+    dQ = np.zeros((n + 1,) + Qs.shape[1:])
+    dQ[1:] = Qs[1:] - Qs[:-1]
+    dQplus = dQ[1:n + 1]
+    Qbar = 0.5 * (dQ[:n] + dQplus)
+    return dQ[:n], dQplus, Qbar
+
+
+def mre_solve(Qs, L):
+    """Eq. (mre-solution): K_h = (e0 - Qbar_h)^(-1) * [L_h - (1/2) Delta+ Q_h *
+    (L_h(0) e0)], the mean-value discretisation Eq. (mre-discrete) of
+    K = L + Q * K.  Qs: Q_h(m), m = 0 .. n; L: [n][d][c].  The term
+    Delta+ Q_h * (L_h(0) e0) is Delta+ Q_h(k) L_h(0) at every k."""
+    _, dQplus, Qbar = mean_value_terms(Qs)
+    L = _f64(L)
+    n, d = L.shape[0], L.shape[1]
+    A = -Qbar
+    A[0] += np.eye(d)
+    psi = inverse_left(A)
+    R = L - 0.5 * np.einsum("kij,jc->kic", dQplus, L[0])
+    return convolve(psi, R)
+
+
+def process_discretization(Qs, L):
+    """Eq. (process-discretization) with a general right-hand side:
+    (e0 - Delta Q_h)^(-1) * L_h (L = Hbar_h gives the transition function)."""
+    dQ, _, _ = mean_value_terms(Qs)
+    L = _f64(L)
+    d = L.shape[1]
+    A = -dQ
+    A[0] += np.eye(d)
+    return convolve(inverse_left(A), L)

@@ -166,6 +166,55 @@ def lognormal_model(d, N, seed=0, h=0.05, alpha=1.0, sigma=(1.0, 2.0), mu=(0.0, 
 
 
 # ----------------------------------------------------------------------------
+# Continuous-time inputs (raw samples only: the mean-value rule itself is
+# computed by the oracle and by the library, each on its own)
+# ----------------------------------------------------------------------------
+def lognormal_samples(d, n, seed=0, h=0.05, alpha=1.0, sigma=(1.0, 2.0), mu=(0.0, 3.0)):
+    """Samples of a Lognormal semi-Markov kernel on the grid t = m h:
+    Q_h(m) = Q(mh) for m = 0 .. n (n + 1 values, [n+1][d][d]) and the
+    survival matrix Hbar(mh) = diag(1 - sum_j Q_ij(mh)) for m = 0 .. n-1."""
+    rng = np.random.default_rng(seed)
+    P = dirichlet_zero_diag(rng, d, alpha)
+    sig = rng.uniform(sigma[0], sigma[1], size=(d, d))
+    m_u = rng.uniform(mu[0], mu[1], size=(d, d))
+    Qs = _lognormal_Q(P, m_u, sig, h * np.arange(n + 1, dtype=np.float64))
+    Hbar = np.zeros((n, d, d))
+    idx = np.arange(d)
+    Hbar[:, idx, idx] = 1.0 - Qs[:n].sum(axis=2)
+    return Qs, Hbar
+
+
+# The four-state exponential benchmark of the continuous-time example
+# (Section 5, Eq. (generator)): states 0 clean, 1 acquisition, 2 infection,
+# 3 fraud complete; up states U = {0, 1, 2}, down state D = {3}.
+GENERATOR_4STATE = np.array([[-0.2, 0.2, 0.0, 0.0],
+                             [0.01, -0.11, 0.1, 0.0],
+                             [0.15, 0.3, -0.85, 0.4],
+                             [0.0, 0.0, 0.5, -0.5]])
+
+
+def exponential_benchmark(h, n):
+    """Samples of the exponential semi-Markov kernel of Eq. (generator) on
+    t = m h: exit rates a_i = -G_ii, embedded chain P_ij = G_ij / a_i
+    (Eq. (embedded-continuous)), Q_ij(t) = P_ij (1 - exp(-a_i t)).
+    Returns Q_h(m) for m = 0 .. n, Hbar(mh) = diag(exp(-a_i mh)) and the
+    up-state survival column L_U(mh) = exp(-a_i mh) (i in U) for m = 0 .. n-1,
+    with the generator, U and the initial distribution (1, 0, 0, 0)."""
+    G = GENERATOR_4STATE
+    a = -np.diag(G)
+    P = G / a[:, None]
+    np.fill_diagonal(P, 0.0)
+    t = h * np.arange(n + 1, dtype=np.float64)
+    surv = np.exp(-np.outer(t, a))                       # [n+1][4]
+    Qs = P[None, :, :] * (1.0 - surv)[:, :, None]
+    Hbar = np.zeros((n, 4, 4))
+    Hbar[:, np.arange(4), np.arange(4)] = surv[:n]
+    U = [0, 1, 2]
+    LU = surv[:n, U][:, :, None].copy()                  # [n][3][1]
+    return {"Q": Qs, "Hbar": Hbar, "LU": LU, "G": G, "U": U, "alpha": np.array([1.0, 0.0, 0.0, 0.0])}
+
+
+# ----------------------------------------------------------------------------
 # The paper's own small examples (parameters printed in Section 5 / Appendix E)
 # ----------------------------------------------------------------------------
 P_EMB_3STATE = np.array([[0.0, 1.0, 0.0], [0.2, 0.0, 0.8], [1.0, 0.0, 0.0]])

@@ -389,3 +389,56 @@ def test_paper_table4_residual_scale(N):
     fro = np.sqrt((psi ** 2).sum(axis=(1, 2)))
     dN = np.max(np.sqrt(((psir - psi) ** 2).sum(axis=(1, 2))) / np.maximum(fro, 2 ** -26.5))
     assert dN <= 4 * gold[N]["newton_dN"]
+
+
+def _exponential_errors(h, T=40.0):
+    """Max errors of the mean-value scheme against exp(G t) on [0, T] for the
+    exponential benchmark: transition matrix (Frobenius), reliability and
+    availability (Section 5, Table 5)."""
+    import scipy.linalg as sl
+    n = int(round(T / h)) + 1
+    b = synth.exponential_benchmark(h, n)
+    G, U, al = b["G"], b["U"], b["alpha"]
+    K = oracle.mre_solve(b["Q"], b["Hbar"])
+    KU = oracle.mre_solve(b["Q"][:, :3, :3], b["LU"])
+    oneU = np.array([1.0, 1.0, 1.0, 0.0])
+    EP = ER = EA = 0.0
+    for m in range(n):
+        Pex = sl.expm(G * m * h)  # the exact Markov solution (library matrix exponential)
+        EP = max(EP, np.linalg.norm(Pex - K[m]))
+        EA = max(EA, abs(al @ Pex @ oneU - al @ K[m] @ oneU))
+        Rex = al[U] @ sl.expm(G[np.ix_(U, U)] * m * h) @ np.ones(3)
+        ER = max(ER, abs(Rex - (al[U] @ KU[m])[0]))
+    return EP, ER, EA
+
+
+def test_paper_table5_mean_value_convergence():
+    """Table 5: the mean-value discretisation Eq. (mre-discrete), solved as
+    Eq. (mre-solution), of the exponential benchmark has the printed maximum
+    errors on [0, 40] against exp(G t) for h = 0.4 .. 0.025 -- transition
+    matrix, reliability (the up-state equation K_U = L_U + Q_UU * K_U with
+    L_U = 1 - H_i) and availability -- and the printed observed orders."""
+    gold = json.load(open(os.path.join(GOLDEN, "paper_table5.json")))
+    errs = [_exponential_errors(h) for h in gold["h"]]
+    for (EP, ER, EA), gp, gr, ga in zip(errs, gold["E_P"], gold["E_R"], gold["E_A"]):
+        assert abs(EP / gp - 1) < 1e-3 and abs(ER / gr - 1) < 1e-3 and abs(EA / ga - 1) < 1e-3
+    for i in range(1, len(errs)):
+        for j, key in enumerate(("order_P", "order_R", "order_A")):
+            assert abs(np.log2(errs[i - 1][j] / errs[i][j]) - gold[key][i]) < 2e-3
+
+
+def test_mean_value_terms_and_row_sums():
+    """The mean-value terms of a linear kernel Q(t) = t C are Qbar_h(0) = hC/2,
+    Qbar_h(m) = hC (m >= 1), Delta+ Q_h = hC; and the mean-value transition
+    function K_h (L = Hbar_h) is stochastic: [Hbar_h - (1/2) Delta+ Q_h] 1 =
+    ((e0 - Qbar_h) * s0) 1 with s0 the unit step, so K_h(k) 1 = 1 exactly."""
+    h, n = 0.1, 7
+    C = np.array([[0.0, 0.3], [0.2, 0.1]])
+    Qs = h * np.arange(n + 1)[:, None, None] * C[None]
+    _, dQp, Qbar = oracle.mean_value_terms(Qs)
+    assert np.allclose(Qbar[0], h * C / 2) and np.allclose(Qbar[1:], h * C) and np.allclose(dQp, h * C)
+    Qs, Hbar = synth.lognormal_samples(5, 400, seed=3, h=0.05)
+    K = oracle.mre_solve(Qs, Hbar)
+    assert np.abs(K.sum(axis=2) - 1.0).max() < 1e-12
+    Pp = oracle.process_discretization(Qs, Hbar)
+    assert np.abs(Pp.sum(axis=2) - 1.0).max() < 1e-12
