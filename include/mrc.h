@@ -117,6 +117,35 @@ mrc_status mrc_inverse(mrc_ctx *ctx, int d, int64_t N, const double *A, double *
                        const mrc_options *opt, void *stream, mrc_report *report);
 
 /*
+ * mrc_mre_solve -- the continuous-time Markov renewal equation
+ * K = L + Q (Stieltjes-convolved) K on the grid t = m h (Section 4),
+ * discretised by the endpoint mean-value rule (scheme 0, Eq. (mre-discrete)),
+ *     K_h = (e0 - Qbar_h)^(-1) * [L_h - (1/2) Delta+ Q_h * (L_h(0) e0)]
+ *                                                      (Eq. (mre-solution)),
+ * with Delta Q_h(0) = O, Delta Q_h(m) = Q_h(m) - Q_h(m-1), Delta+ Q_h(m) =
+ * Delta Q_h(m+1), Qbar_h = (Delta Q_h + Delta+ Q_h) / 2; or by the
+ * process discretisation (scheme 1, Eq. (process-discretization)),
+ *     K_h = (e0 - Delta Q_h)^(-1) * L_h.
+ * L = Hbar (diag(1 - H_i)) gives the transition function P; the up-state
+ * block of Q with L_i = 1 - H_i (i up) gives reliability; A(t) = alpha P 1_U
+ * availability.
+ *   d, c   : kernel dimension and number of right-hand-side columns (<= 512).
+ *   N      : number of output coefficients m = 0 .. N-1.
+ *   Q      : device, [N+1][d][d] doubles: Q_h(m) = Q(m h), m = 0 .. N (the
+ *            extra sample feeds Delta+ Q_h(N-1)); Q(0) = O expected.
+ *   L      : device, [N][d][c] doubles: L_h(m) = L(m h).
+ *   scheme : 0 mean-value rule, 1 process discretisation.
+ *   K      : device, [N][d][c] doubles, receives K_h.
+ *   opt    : as mrc_inverse (MRC_MIXED: FP32 Newton levels, double-float
+ *            residual sweep and product).
+ * Errors: MRC_ERR_INVALID_ARG, MRC_ERR_NO_MEMORY, MRC_ERR_CUDA; a singular
+ * e0 - Qbar_h(0) shows in the status word (mrc_sync_status).
+ */
+mrc_status mrc_mre_solve(mrc_ctx *ctx, int d, int c, int64_t N, const double *Q, const double *L, int scheme,
+                         double *K, const mrc_options *opt, void *stream);
+
+/*
+ * mrc_inverse_host/*
  * mrc_inverse_host -- the same inverse as mrc_inverse (same kernels, same
  * results) for a sequence that lives in host memory, with the transfers in
  * the call: A is uploaded in the row ranges the Newton doubling consumes

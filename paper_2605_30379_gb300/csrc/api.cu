@@ -1050,6 +1050,46 @@ mrc_status mrc_reward(mrc_ctx *c, int d, int cc, int64_t N, const double *psi, c
     return conv_product(c, ar, p, psi, N, r, N, d, d, cc, N, V, 1.0, 0, 0, false, st);
 }
 
+mrc_status mrc_mre_solve(mrc_ctx *c, int d, int cc, int64_t N, const double *Q, const double *L, int scheme,
+                         double *K, const mrc_options *opt, void *stream)
+{
+    if (!c || !Q || !L || !K || !valid_dN(d, N) || cc < 1 || cc > 512 || (scheme != 0 && scheme != 1))
+        return MRC_ERR_INVALID_ARG;
+    const int prec = opt ? opt->prec : MRC_FP64;
+    if (prec != MRC_FP64 && prec != MRC_MIXED) return MRC_ERR_INVALID_ARG;
+    int sweeps = opt ? opt->refine_sweeps : 1;
+    if (prec == MRC_MIXED && sweeps <= 0) sweeps = 1;
+    if (sweeps > 4) return MRC_ERR_INVALID_ARG;
+    TuneScope tscope(c, opt);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaSetDevice(c->device);
+    const int p = prec == MRC_FP64 ? PREC_F64 : PREC_DD;
+    mrc_status s;
+    if ((s = ensure_tw(c, prec == MRC_FP64 ? PREC_F64 : PREC_F32, st)) != MRC_OK) return s;
+    if (prec == MRC_MIXED && (s = ensure_tw(c, PREC_DD, st)) != MRC_OK) return s;
+    const size_t E = (size_t)d * d, EL = (size_t)d * cc;
+    const size_t fixed = 2 * align_up(sizeof(double) * N * E) + align_up(sizeof(double) * N * EL);
+    if ((s = ensure_ws(c, fixed + std::max(ws_inverse(d, N, prec), ws_product(pow2ceil(N), E, EL, EL, p)))) != MRC_OK)
+        return s;
+    Arena ar{(char *)c->ws};
+    double *A = (double *)ar.take(sizeof(double) * N * E);
+    double *psi = (double *)ar.take(sizeof(double) * N * E);
+    double *R = (double *)ar.take(sizeof(double) * N * EL);
+    const size_t mark = ar.off;
+    // e0 - Qbar_h (or e0 - Delta Q_h) and its inverse
+    CK(mrc_mre_operator(Q, A, d, N, scheme, st));
+    s = inverse_impl(c, ar, d, N, A, psi, prec, sweeps, nullptr, st);
+    if (s != MRC_OK) return s;
+    ar.off = mark;
+    // right-hand side: L_h - (1/2) Delta+ Q_h L_h(0) (mean-value rule) or L_h, then K = psi * R
+    const double *rhs = L;
+    if (scheme == 0) {
+        CK(mrc_mre_rhs(Q, L, R, d, cc, N, st));
+        rhs = R;
+    }
+    return conv_product(c, ar, p, psi, N, rhs, N, d, d, cc, N, K, 1.0, 0, 0, false, st);
+}
+
 mrc_status mrc_renewal_visits(mrc_ctx *c, int d, int64_t N, const double *psi, const double *alpha, const int *B,
                               int nB, double *out, void *stream)
 {

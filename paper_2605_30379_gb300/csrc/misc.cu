@@ -267,6 +267,40 @@ __global__ void one_minus_kernel(const double *__restrict__ x, double *__restric
         y[t] = 1.0 - x[t];
 }
 
+// Endpoint mean-value rule (Section 4): from the kernel samples Q_h(m),
+// m = 0 .. N, with Delta Q_h(0) = O, Delta Q_h(m) = Q_h(m) - Q_h(m-1) and
+// Delta+ Q_h(m) = Delta Q_h(m+1): A(m) = delta(m) I - Qbar_h(m) with
+// Qbar_h = (Delta Q_h + Delta+ Q_h) / 2 (scheme 0, Eq. (mre-solution)), or
+// A(m) = delta(m) I - Delta Q_h(m) (scheme 1, Eq. (process-discretization)).
+__global__ void mre_operator_kernel(const double *__restrict__ Q, double *__restrict__ A, int d, int64_t N,
+                                    int scheme)
+{
+    const int64_t E = (int64_t)d * d, n = N * E;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = t / E, e = t - m * E;
+        const double dQ = m > 0 ? Q[m * E + e] - Q[(m - 1) * E + e] : 0.0;
+        const double v = scheme == 0 ? 0.5 * (dQ + (Q[(m + 1) * E + e] - Q[m * E + e])) : dQ;
+        const int i = (int)(e / d), j = (int)(e - (e / d) * d);
+        A[t] = (m == 0 && i == j ? 1.0 : 0.0) - v;
+    }
+}
+
+// Right-hand side of Eq. (mre-solution): R(m) = L_h(m) - (1/2) Delta+ Q_h(m) L_h(0)
+// ([d][c] per m; Delta+ Q_h * (L_h(0) e0) is Delta+ Q_h(m) L_h(0) at every m).
+__global__ void mre_rhs_kernel(const double *__restrict__ Q, const double *__restrict__ L, double *__restrict__ R,
+                               int d, int c, int64_t N)
+{
+    const int64_t E = (int64_t)d * d, EL = (int64_t)d * c, n = N * EL;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = t / EL, e = t - m * EL;
+        const int i = (int)(e / c), j = (int)(e - (e / c) * c);
+        const double *q1 = Q + (m + 1) * E + (int64_t)i * d, *q0 = Q + m * E + (int64_t)i * d;
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) s += (q1[k] - q0[k]) * L[(int64_t)k * c + j];
+        R[t] = L[t] - 0.5 * s;
+    }
+}
+
 inline unsigned grid_for(int64_t n, int bs = 256)
 {
     int64_t b = (n + bs - 1) / bs;
@@ -360,6 +394,22 @@ cudaError_t mrc_occupation_k(const double *P, int d, int64_t N, const double *al
         if (inB[j]) B.idx[B.n++] = j;
     mrc_prof_pre(7, st);
     occupation_kernel<<<grid_for(N), 256, 0, st>>>(P, d, N, alpha, B, out);
+    mrc_prof_post(7, st, 0, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t mrc_mre_operator(const double *Q, double *A, int d, int64_t N, int scheme, cudaStream_t st)
+{
+    mrc_prof_pre(7, st);
+    mre_operator_kernel<<<grid_for(N * (int64_t)d * d), 256, 0, st>>>(Q, A, d, N, scheme);
+    mrc_prof_post(7, st, 0, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t mrc_mre_rhs(const double *Q, const double *L, double *R, int d, int c, int64_t N, cudaStream_t st)
+{
+    mrc_prof_pre(7, st);
+    mre_rhs_kernel<<<grid_for(N * (int64_t)d * c), 256, 0, st>>>(Q, L, R, d, c, N);
     mrc_prof_post(7, st, 0, 0);
     return cudaGetLastError();
 }

@@ -140,3 +140,5 @@ cudaError_t mrc_weighted_rowsum(const double *g, int nC, int nD, int64_t N, cons
 cudaError_t mrc_occupation_k(const double *P, int d, int64_t N, const double *alpha, const int *inB, double *out,
                              cudaStream_t st);
 cudaError_t mrc_one_minus(const double *x, double *y, int64_t n, cudaStream_t st);
+cudaError_t mrc_mre_operator(const double *Q, double *A, int d, int64_t N, int scheme, cudaStream_t st);
+cudaError_t mrc_mre_rhs(const double *Q, const double *L, double *R, int d, int c, int64_t N, cudaStream_t st);

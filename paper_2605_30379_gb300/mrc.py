@@ -71,6 +71,7 @@ def load():
         lib.mrc_inverse_workspace_bytes.argtypes = [I, I64, I]
         lib.mrc_inverse_workspace_bytes.restype = SZ
         lib.mrc_inverse.argtypes = [P, I, I64, P, P, ctypes.POINTER(_Options), P, ctypes.POINTER(_Report)]
+        lib.mrc_mre_solve.argtypes = [P, I, I, I64, P, P, I, P, ctypes.POINTER(_Options), P]
         lib.mrc_inverse_host.argtypes = [P, I, I64, P, P, ctypes.POINTER(_Options), P, ctypes.POINTER(_Report)]
         lib.mrc_inverse_batched.argtypes = [P, I, P, P, P, P, ctypes.POINTER(_Options), P, ctypes.POINTER(_Report)]
         lib.mrc_residual.argtypes = [P, I, I64, P, P, I, P, P, I, P, ctypes.POINTER(_Report)]
@@ -173,6 +174,22 @@ def inverse_host(A, prec="fp64", sweeps=1, target_residual=0.0, report=False, ou
                                  ctypes.byref(rep) if report else None)
     _check(st, "mrc_inverse_host")
     return (psi, rep.as_dict()) if report else psi
+
+
+def mre_solve(Q, L, scheme="mean_value", prec="fp64", sweeps=1, stream=None):
+    """K_h for the continuous-time equation K = L + Q * K (mrc_mre_solve).
+    Q: CUDA float64 [N+1, d, d] kernel samples Q(mh), m = 0..N; L: [N, d, c];
+    scheme "mean_value" (Eq. (mre-solution)) or "process" (Eq.
+    (process-discretization))."""
+    Q, L = _seq(Q, "Q"), _seq(L, "L")
+    N, d, c = L.shape
+    if Q.shape != (N + 1, d, d):
+        raise ValueError("Q must be [N+1, d, d] for L of shape [N, d, c]")
+    K = torch.empty_like(L)
+    sc = {"mean_value": 0, "process": 1}[scheme]
+    _check(load().mrc_mre_solve(context(L.device.index), d, c, N, _ptr(Q), _ptr(L), sc, _ptr(K),
+                                ctypes.byref(_opts(prec, sweeps, 0.0)), _stream(stream)), "mrc_mre_solve")
+    return K
 
 
 def inverse_batched(As, prec="fp64", sweeps=1, outs=None, report=False, stream=None, autotune=False):

@@ -387,6 +387,58 @@ def test_inverse_from_host_buffers_matches_device_call(mrc, prec, pinned):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("scheme", ["mean_value", "process"])
+def test_mre_solve_matches_oracle(mrc, prec, scheme):
+    """mrc_mre_solve (Section 4: Eq. (mre-solution) or Eq.
+    (process-discretization)) against the oracle on Lognormal kernel samples:
+    the transition function (L = Hbar, square) and a rectangular right-hand
+    side, N = 700 (a partial last Newton level)."""
+    Qs, Hbar = synth.lognormal_samples(6, 700, seed=91, h=0.05)
+    rng = np.random.default_rng(92)
+    Lr = rng.uniform(0, 1, (700, 6, 2))
+    for L in (Hbar, Lr):
+        ref = (oracle.mre_solve if scheme == "mean_value" else oracle.process_discretization)(Qs, L)
+        got = mrc.mre_solve(dev(Qs), dev(L), scheme=scheme, prec=prec).cpu().numpy()
+        mrc.sync_status()
+        tol = 1e-11 if prec == "fp64" else 1e-10
+        assert np.abs(got - ref).max() <= tol * max(1.0, np.abs(ref).max())
+
+
+def test_mre_exponential_benchmark_n32768(mrc):
+    """The exponential benchmark of Section 5 at N = 2^15, h = 0.005 on the
+    GPU: maximum availability and reliability errors of the mean-value scheme
+    against exp(G t) near the printed 2.53e-8 and 7.77e-8, of the process
+    discretisation near 6.41e-5 and 1.86e-4 (tests/golden, three printed
+    digits)."""
+    n, h = 2 ** 15, 0.005
+    b = synth.exponential_benchmark(h, n)
+    G, U, al = b["G"], b["U"], b["alpha"]
+    import scipy.linalg as sl
+    # exact solution by repeated multiplication with exp(G h) (error ~ n u)
+    step, stepU = sl.expm(G * h), sl.expm(G[np.ix_(U, U)] * h)
+    Pex = np.empty((n, 4, 4)); Rex = np.empty(n)
+    P, PU = np.eye(4), np.eye(3)
+    for m in range(n):
+        Pex[m] = P; Rex[m] = al[U] @ PU @ np.ones(3)
+        P = P @ step; PU = PU @ stepU
+    oneU = np.array([1.0, 1.0, 1.0, 0.0])
+    Aex = np.einsum("i,mij,j->m", al, Pex, oneU)
+    out = {}
+    for scheme in ("mean_value", "process"):
+        K = mrc.mre_solve(dev(b["Q"]), dev(b["Hbar"]), scheme=scheme, prec="fp64").cpu().numpy()
+        KU = mrc.mre_solve(dev(b["Q"][:, :3, :3]), dev(b["LU"]), scheme=scheme, prec="fp64").cpu().numpy()
+        out[scheme] = (np.abs(np.einsum("i,mij,j->m", al, K, oneU) - Aex).max(),
+                       np.abs(np.einsum("i,mic->m", al[U], KU) - Rex).max())
+    import json, os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_exponential_benchmark.json")))
+    for scheme in ("mean_value", "process"):
+        ea, er = out[scheme]
+        # three printed digits: within their rounding (0.5 %)
+        assert abs(ea / gold[scheme]["availability"] - 1) < 5e-3, (scheme, ea)
+        assert abs(er / gold[scheme]["reliability"] - 1) < 5e-3, (scheme, er)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_reward_matches_oracle(mrc, prec):
     """V = psi * r with a rectangular reward sequence (Eq. (reward)); the oracle
     side is its direct convolution, and V must solve V = r + q * V."""
