@@ -49,6 +49,9 @@ WORKLOADS = {
     # 256 independent models, d ~ U{3..48}, N = round(2^U[10,16]), half discrete Weibull,
     # half Lognormal mean-value (h = 0.05), one captured batch
     "batch256": (0, 0, "batch", {"n": 256}),
+    # continuous-time Markov renewal equation (mrc_mre_solve, mean-value rule):
+    # the paper's four-state exponential benchmark, N = 2^15, h = 0.005, transition function
+    "mre_exponential_N32768": (4, 1 << 15, "mre", {"h": 0.005}),
 }
 DEFAULT_WORKLOAD = "lognormal_d64_N262144"
 
@@ -228,6 +231,99 @@ def cpu_oracle_sample(A_host, d, budget_s=15.0):
     return n, dt, oracle.num_threads()
 
 
+def run_mre(args, rank, world, local):
+    """One step = mrc_mre_solve (Eq. (mre-solution)) of the transition
+    function on the exponential benchmark; metric: K_h coefficients (N d^2)
+    per second, inputs resident; roofline of the dominant kernel class;
+    the oracle's mre_solve timed on a prefix as the CPU baseline."""
+    import ctypes
+    import torch
+    from paper_2605_30379_gb300 import mrc, synth
+    torch.cuda.set_device(local)
+    d, N, _, extra = WORKLOADS[args.workload]
+    b = synth.exponential_benchmark(extra["h"], N)
+    Q = torch.from_numpy(b["Q"]).cuda()
+    L = torch.from_numpy(b["Hbar"]).cuda()
+    lib = mrc.load()
+    lib.mrc_launch_count.restype = ctypes.c_ulonglong
+    lib.mrc_profile_begin.argtypes = [ctypes.c_int]
+    lib.mrc_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return mrc.mre_solve(Q, L, scheme="mean_value", prec=args.prec)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    breakdown = {}
+    for kc in KCLASS:
+        lib.mrc_profile_begin(kc)
+        step()
+        ms, n, bb, ff = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+        lib.mrc_profile_end(ctypes.byref(ms), ctypes.byref(n), ctypes.byref(bb), ctypes.byref(ff))
+        if n.value:
+            breakdown[KCLASS[kc]] = {"ms": ms.value, "launches": n.value}
+    dominant = max((kc for kc in KCLASS if KCLASS[kc] in breakdown), key=lambda kc: breakdown[KCLASS[kc]]["ms"])
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize()
+    lib.mrc_profile_begin(dominant)
+    l0 = lib.mrc_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        K = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = lib.mrc_launch_count() - l0
+    pms, pn, pb, pf = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+    lib.mrc_profile_end(ctypes.byref(pms), ctypes.byref(pn), ctypes.byref(pb), ctypes.byref(pf))
+    clocks = sampler.stop()
+    ms_step = e0.elapsed_time(e1) / args.steps
+    coeffs = N * d * d
+    peaks, peak_kind = load_peaks()
+    roof = roofline_for(dominant, pms.value, pn.value, pb.value, pf.value, peaks, clocks["sm_mhz"] if clocks else None)
+    if roof:
+        roof["peak_kind"] = peak_kind
+        roof["traffic"], roof["traffic_source"] = measured_traffic(args.workload, roof["kernel"])
+    # accuracy: availability against the exact solution (exp(G h) powers)
+    import scipy.linalg as sl
+    step_m = sl.expm(b["G"] * extra["h"])
+    Kh = K.cpu().numpy()
+    P = np.eye(4)
+    one_u = np.array([1.0, 1.0, 1.0, 0.0])
+    err = 0.0
+    for m in range(N):
+        err = max(err, abs(b["alpha"] @ (P - Kh[m]) @ one_u))
+        P = P @ step_m
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        n = 512
+        while True:
+            t0 = time.perf_counter()
+            oracle.mre_solve(b["Q"][:n + 1], b["Hbar"][:n])
+            dt = time.perf_counter() - t0
+            if dt >= 4.0 or 2 * n > N:
+                break
+            n *= 2
+        cpu = {"value": n * d * d / dt, "unit": "coefficients/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"oracle mre_solve on the prefix m < {n} of the same benchmark ({dt:.1f} s)"}
+    line = {"metric": "K_h coefficients/s (N*d^2), continuous-time transition function, mean-value rule",
+            "value": coeffs / (ms_step * 1e-3), "unit": "coefficients/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+dd" if args.prec == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "d": d, "N": N, "h": extra["h"], "prec": args.prec,
+                       "l2": "inputs below L2 size (latency-bound case)", "parallelism": "single"},
+            "accuracy": {"max_abs_availability_error_vs_exact": err, "paper": 2.53e-8},
+            "gpu_launches": int(launches), "stage_ms": breakdown, "roofline": roof, "clocks": clocks,
+            "e2e": None, "cpu_baseline": cpu}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def run_reference(args, rank, world):
     """The oracle timed on the host cores (rank 0 only)."""
     if rank != 0:
@@ -236,6 +332,27 @@ def run_reference(args, rank, world):
     d, N, kind, _ = WORKLOADS[name]
     from paper_2605_30379_gb300 import synth
     # prefix of the same seeded workload (the generator is prefix-consistent)
+    if kind == "mre":
+        import oracle
+        b = synth.exponential_benchmark(WORKLOADS[name][3]["h"], 2048)
+        times = []
+        for it in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            oracle.mre_solve(b["Q"], b["Hbar"])
+            if it >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        ms = 1e3 * float(np.mean(times))
+        value = 2048 * d * d / (ms * 1e-3)
+        cpu = {"value": value, "unit": "coefficients/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"oracle mre_solve on the prefix m < 2048 of the {name} workload"}
+        print(json.dumps({"impl": "reference", "metric": "K_h coefficients/s (N*d^2), continuous-time transition "
+                          "function, mean-value rule", "value": value, "unit": "coefficients/s", "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": name, "d": d, "N": N}, "cpu_baseline": cpu,
+                          "e2e": {"value": value, "unit": "coefficients/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return
     if kind == "batch":
         A = synth.batch_models(n=1, seed=0)[0]["A"]
         d, N = A.shape[1], A.shape[0]
@@ -288,6 +405,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if WORKLOADS[args.workload][2] == "mre":
+        run_mre(args, rank, world, local)
         return
 
     import torch
