@@ -76,12 +76,25 @@ DD_INSTR_PER_FLOP = 7.5
 FP64_TFLOPS_MEASURED = 1.19
 
 
-def roofline_for(kclass, ms_total, launches, bytes_, flops, peaks, sm_mhz):
+def dd_product_on_tensor_cores(d):
+    """The double-float products run as exact digit products on the tensor
+    cores for 32 <= d <= 512 unless MRC_DD_PRODUCT=simt picks the FP32-pipe
+    kernel; there the FP32 lanes do not bound them and their bytes do."""
+    return d is not None and 32 <= d <= 512 and os.environ.get("MRC_DD_PRODUCT") != "simt"
+
+
+def roofline_for(kclass, ms_total, launches, bytes_, flops, peaks, sm_mhz, d=None):
     if not launches:
         return None
     per_ms = ms_total / launches
     name = KCLASS[kclass]
     clk = (sm_mhz or 2070.0) * 1e6
+    if name == "pairmul_dd" and dd_product_on_tensor_cores(d):
+        ach = bytes_ / launches / (per_ms * 1e-3) / 1e9
+        peak = peaks["hbm_gbs"]
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": None, "launches": launches, "avg_ms": per_ms,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured); tensor-core digit products"}
     if name.startswith("fft_f32") or name == "misc":
         ach = bytes_ / launches / (per_ms * 1e-3) / 1e9
         peak = peaks["hbm_gbs"]
@@ -284,7 +297,8 @@ def run_mre(args, rank, world, local):
     ms_step = e0.elapsed_time(e1) / args.steps
     coeffs = N * d * d
     peaks, peak_kind = load_peaks()
-    roof = roofline_for(dominant, pms.value, pn.value, pb.value, pf.value, peaks, clocks["sm_mhz"] if clocks else None)
+    roof = roofline_for(dominant, pms.value, pn.value, pb.value, pf.value, peaks, clocks["sm_mhz"] if clocks else None,
+                        d=d)
     if roof:
         roof["peak_kind"] = peak_kind
         roof["traffic"], roof["traffic_source"] = measured_traffic(args.workload, roof["kernel"])
@@ -474,7 +488,7 @@ def main():
         if n:
             breakdown[KCLASS[kc]] = {"ms": ms, "launches": n}
     dominant = max((kc for kc in KCLASS if KCLASS[kc] in breakdown), key=lambda kc: breakdown[KCLASS[kc]]["ms"],
-                   default=6 if args.prec == "mixed" else 4)
+                   default=2 if args.prec == "mixed" else 4)
 
     # ---- timed region (device-resident inputs)
     sampler = ClockSampler(local)
@@ -542,7 +556,7 @@ def main():
 
     peaks, peak_kind = load_peaks()
     roof = roofline_for(dominant, pms.value, pn.value, pb.value, pf.value, peaks,
-                        clocks["sm_mhz"] if clocks else None)
+                        clocks["sm_mhz"] if clocks else None, d=None if batch else d)
     if roof:
         roof["peak_kind"] = peak_kind
         roof["traffic"], roof["traffic_source"] = measured_traffic(args.workload, roof["kernel"])

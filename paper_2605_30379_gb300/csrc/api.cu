@@ -190,9 +190,10 @@ size_t ws_product(int64_t Mr, size_t EX, size_t EY, size_t EC, int prec)
 }
 
 // Mixed inverse layout: [Gauss-Jordan work | double-float spectrum of A |
-// its FFT scratch | then either the FP32 Newton buffers or, afterwards,
-// rho_L followed by the residual's two other double-float spectra or the
-// FP32 correction's product buffers].
+// its FFT scratch | psi_0 in binary32 | then either A in binary32 and the
+// FP32 Newton buffers or, afterwards, rho_L (binary32) followed by the
+// residual's two other double-float spectra or the FP32 correction's
+// product buffers].
 size_t ws_inverse(int d, int64_t N, int prec)
 {
     const size_t E = (size_t)d * d;
@@ -200,14 +201,18 @@ size_t ws_inverse(int d, int64_t N, int prec)
     const int64_t Mr = pow2ceil(N);
     const size_t gj = align_up(sizeof(double) * 2 * E);
     const size_t ahat = align_up((size_t)Mr * E * 16) + align_up(mrc_fft_scratch_elems(Mr, (int)E) * 16);
-    const size_t newton = ws_newton(d, N, PREC_F32) - gj;
-    // rho_L, the FP32 spectrum of psi_0 (hi parts of its double-float one),
-    // then the residual's spectra of psi_0 and of the product (double-float)
-    // or the correction's FP32 spectrum of rho, product and FFT scratch
-    const size_t refine = align_up((size_t)N * E * sizeof(double)) + align_up((size_t)Mr * E * 8) +
+    // psi_0 in binary32 (the FP32 Newton levels' output), kept to the end
+    const size_t psi32 = align_up((size_t)N * E * sizeof(float));
+    // the FP32 Newton levels: their binary32 copy of A and their buffers
+    const size_t newton = align_up((size_t)N * E * sizeof(float)) + ws_newton(d, N, PREC_F32) - gj;
+    // rho_L (binary32), the FP32 spectrum of psi_0 (hi parts of its
+    // double-float one), then the residual's spectra of psi_0 and of the
+    // product (double-float) or the correction's FP32 spectrum of rho,
+    // product and FFT scratch
+    const size_t refine = align_up((size_t)N * E * sizeof(float)) + align_up((size_t)Mr * E * 8) +
                           std::max(2 * align_up((size_t)Mr * E * 16),
                                    2 * align_up((size_t)Mr * E * 8) + align_up(mrc_fft_scratch_elems(Mr, (int)E) * 8));
-    return gj + ahat + std::max(newton, refine);
+    return gj + ahat + psi32 + std::max(newton, refine);
 }
 
 // Square products on the tensor cores: double-float with 32 <= d <= 64 as
@@ -313,10 +318,13 @@ cudaError_t pairmul_any(mrc_ctx *cx, int prec, const void *zx, const void *zy, v
 // Mr, EX entries, this precision) and the FFT scratch to use instead of a new
 // one; y_hi (double-float only, optional): also write the hi parts of Y's
 // spectrum there as FP32 complex values.
-mrc_status conv_product(mrc_ctx *c, Arena &ar, int prec, const double *X, int64_t NX, const double *Y, int64_t NY,
-                        int r, int m, int cc, int64_t N, double *out, double sign, int eye_d, int add,
+// y_mode: SRC_REAL64 or SRC_REAL32 rows of Y; out_mode >= 0 overrides the
+// destination (DST_REAL32, or DST_REAL64_BASE32 with out_base).
+mrc_status conv_product(mrc_ctx *c, Arena &ar, int prec, const double *X, int64_t NX, const void *Y, int64_t NY,
+                        int r, int m, int cc, int64_t N, void *out, double sign, int eye_d, int add,
                         bool diag, cudaStream_t st, void *preX = nullptr, void *preT = nullptr,
-                        void *y_hi = nullptr)
+                        void *y_hi = nullptr, int y_mode = SRC_REAL64, int out_mode = -1,
+                        const float *out_base = nullptr)
 {
     const PrecOps &op = OPS[prec];
     const int64_t Mr = pow2ceil(N);
@@ -330,7 +338,7 @@ mrc_status conv_product(mrc_ctx *c, Arena &ar, int prec, const double *X, int64_
     void *bT = preT ? preT : ar.take(mrc_fft_scratch_elems(Mr, (int)emax) * op.cxb);
     const void *tw = c->tw[prec];
     FftSrc sx{SRC_REAL64, X, 0, std::min(NX, N), (int)EX, 0};
-    FftSrc sy{SRC_REAL64, Y, 0, std::min(NY, N), (int)EY, 0};
+    FftSrc sy{y_mode, Y, 0, std::min(NY, N), (int)EY, 0};
     FftDst dx{DST_CPLX, bX, (int)EX, 0, 0, 0, 1.0, 0};
     FftDst dy{DST_CPLX, bY, (int)EY, 0, 0, 0, 1.0, 0, y_hi};
     if (!preX) CK(op.fft(sx, dx, Mr, (int)EX, -1, bT, tw, MRC_TW_LOG, st));
@@ -338,7 +346,8 @@ mrc_status conv_product(mrc_ctx *c, Arena &ar, int prec, const double *X, int64_
     if (diag) CK(op.pairdiag(bX, bY, bC, Mr, r, cc, tw, MRC_TW_LOG, st));
     else CK(pairmul_any(c, prec, bX, bY, bC, Mr, r, m, cc, tw, st));
     FftSrc sc{SRC_CPLX, bC, 0, Mr, (int)EC, 0};
-    FftDst dc{add ? DST_REAL64_ADD : DST_REAL64, out, (int)EC, 0, N, 0, sign / (double)Mr, eye_d};
+    FftDst dc{out_mode >= 0 ? out_mode : (add ? DST_REAL64_ADD : DST_REAL64), out, (int)EC, 0, N, 0,
+              sign / (double)Mr, eye_d, nullptr, out_base};
     CK(op.fft(sc, dc, Mr, (int)EC, +1, bT, tw, MRC_TW_LOG, st));
     return MRC_OK;
 }
@@ -346,8 +355,12 @@ mrc_status conv_product(mrc_ctx *c, Arena &ar, int prec, const double *X, int64_
 // Newton doubling levels in working precision `prec`: psi rows [0, m0) are
 // already correct; each level m -> min(2m, N) follows Eq. (newton) with the
 // middle product (L = 2m): E = A*B (cyclic), R = -E[m, 2m), B[m, 2m) = (B*R)[0, m).
+// With A32 / psi32 (FP32 levels of the mixed path) the levels read A from
+// its binary32 copy, converted here row range by row range as the levels
+// reach it, and read and write psi in binary32 (rows [0, m0) already there).
 mrc_status newton_levels(mrc_ctx *c, Arena &ar, int prec, int d, int64_t N, const double *A, double *psi,
-                         int64_t m0, int *levels, cudaStream_t st, const RowWait *rw = nullptr)
+                         int64_t m0, int *levels, cudaStream_t st, const RowWait *rw = nullptr,
+                         float *A32 = nullptr, float *psi32 = nullptr)
 {
     const PrecOps &op = OPS[prec];
     const int E = d * d;
@@ -358,12 +371,18 @@ mrc_status newton_levels(mrc_ctx *c, Arena &ar, int prec, int d, int64_t N, cons
     void *b2 = ar.take((size_t)Mmax * E * op.cxb);
     void *bt = ar.take(mrc_fft_scratch_elems(Mmax, E) * op.cxb);
     const void *tw = c->tw[prec];
+    const bool f32 = A32 && psi32;
+    int64_t conv = 0;  // rows of A32 converted so far
     int lv = 0;
     for (int64_t m = m0; m < N; m <<= 1, ++lv) {
         const int64_t M = m, m2 = std::min<int64_t>(2 * m, N);
         if (rw) CK(rw->wait(st, m2));  // this level reads A[0, 2m)
-        FftSrc sA{SRC_REAL64, A, 0, std::min<int64_t>(2 * m, N), E, 0};
-        FftSrc sB{SRC_REAL64, psi, 0, m, E, 0};
+        if (f32 && conv < m2) {
+            CK(mrc_f64_to_f32(A + conv * E, A32 + conv * E, (m2 - conv) * E, st));
+            conv = m2;
+        }
+        FftSrc sA{f32 ? SRC_REAL32 : SRC_REAL64, f32 ? (const void *)A32 : A, 0, m2, E, 0};
+        FftSrc sB{f32 ? SRC_REAL32 : SRC_REAL64, f32 ? (const void *)psi32 : psi, 0, m, E, 0};
         FftDst to0{DST_CPLX, b0, E, 0, 0, 0, 1.0, 0};
         FftDst to1{DST_CPLX, b1, E, 0, 0, 0, 1.0, 0};
         CK(op.fft(sA, to0, M, E, -1, bt, tw, MRC_TW_LOG, st));               // A-hat
@@ -377,7 +396,7 @@ mrc_status newton_levels(mrc_ctx *c, Arena &ar, int prec, int d, int64_t N, cons
         CK(op.fft(sR, to2, M, E, -1, bt, tw, MRC_TW_LOG, st));               // R-hat
         CK(pairmul_any(c, prec, b1, b2, b0, M, d, d, d, tw, st, true));     // (B R)-hat
         FftSrc s0{SRC_CPLX, b0, 0, M, E, 0};
-        FftDst toP{DST_REAL64, psi, E, 0, m2 - m, m, 1.0 / (double)M, 0};
+        FftDst toP{f32 ? DST_REAL32 : DST_REAL64, f32 ? (void *)psi32 : psi, E, 0, m2 - m, m, 1.0 / (double)M, 0};
         CK(op.fft(s0, toP, M, E, +1, bt, tw, MRC_TW_LOG, st));               // B[m, m2)
     }
     if (levels) *levels = lv;
@@ -420,12 +439,18 @@ mrc_status inverse_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A
         CK(OPS[PREC_DD].fft(sx, dx, Mr, (int)E, -1, ascr, c->tw[PREC_DD], MRC_TW_LOG, sa));
         if (split) CK(cudaEventRecord(c->ev_join, c->aux));
     }
+    // mixed: psi_0 is kept in binary32 (every entry the FP32 levels write is
+    // a binary32 number; the first m0 rows are rounded to it)
+    float *psi32 = prec == MRC_MIXED ? (float *)ar.take((size_t)N * E * sizeof(float)) : nullptr;
     const int64_t m0 = base_size(d, N);
     if (rw) CK(rw->wait(sn, m0));
     CK(mrc_gauss_jordan(A, psi, gjw, d, status ? status : c->d_status, sn));
     CK(mrc_base_case(A, psi, d, m0, sn));
+    if (psi32) CK(mrc_f64_to_f32(psi, psi32, m0 * (int64_t)E, sn));
     const size_t mark = ar.off;
-    mrc_status s = newton_levels(c, ar, prec == MRC_FP64 ? PREC_F64 : PREC_F32, d, N, A, psi, m0, levels, sn, rw);
+    float *A32 = psi32 ? (float *)ar.take((size_t)N * E * sizeof(float)) : nullptr;
+    mrc_status s = newton_levels(c, ar, prec == MRC_FP64 ? PREC_F64 : PREC_F32, d, N, A, psi, m0, levels, sn, rw,
+                                 A32, psi32);
     if (s != MRC_OK) return s;
     ar.off = mark;
     if (prec == MRC_MIXED) {
@@ -434,19 +459,26 @@ mrc_status inverse_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A
             CK(cudaStreamWaitEvent(st, c->ev_join2, 0));
             CK(cudaStreamWaitEvent(st, c->ev_join, 0));
         }
-        double *rho = (double *)ar.take(sizeof(double) * (size_t)N * E);
+        float *rho32 = (float *)ar.take(sizeof(float) * (size_t)N * E);
         void *psi_hat32 = ar.take((size_t)pow2ceil(N) * E * 8);
         const size_t mark2 = ar.off;
         for (int sw = 0; sw < sweeps; ++sw) {
             ar.off = mark2;
-            // rho_L = e0 - A * psi in double-float (Proposition 2.6); the FFT
-            // of psi also leaves the FP32 spectrum the correction needs
-            s = conv_product(c, ar, PREC_DD, A, N, psi, N, d, d, d, N, rho, -1.0, d, 0, false, st, ahat, ascr,
-                             psi_hat32);
+            // rho_L = e0 - A * psi in double-float (Proposition 2.6), stored
+            // in binary32 (the precision the FP32 correction reads it in);
+            // the FFT of psi also leaves the FP32 spectrum the correction
+            // needs.  The first sweep reads psi_0 from its binary32 copy.
+            const bool first = sw == 0;
+            s = conv_product(c, ar, PREC_DD, A, N, first ? (const void *)psi32 : psi, N, d, d, d, N, rho32, -1.0, d,
+                             0, false, st, ahat, ascr, psi_hat32, first ? SRC_REAL32 : SRC_REAL64, DST_REAL32);
             if (s != MRC_OK) return s;
             ar.off = mark2;
-            // psi <- psi + psi * rho_L (Eq. (newton) from a full-length approximation), FP32 product
-            s = conv_product(c, ar, PREC_F32, psi, N, rho, N, d, d, d, N, psi, 1.0, 0, 1, false, st, psi_hat32);
+            // psi <- psi + psi * rho_L (Eq. (newton) from a full-length
+            // approximation), FP32 product; the first sweep writes
+            // psi = psi_0 + psi_0 * rho_L in FP64 from the binary32 psi_0
+            s = conv_product(c, ar, PREC_F32, psi, N, rho32, N, d, d, d, N, psi, 1.0, 0, 1, false, st, psi_hat32,
+                             nullptr, nullptr, SRC_REAL32, first ? DST_REAL64_BASE32 : DST_REAL64_ADD,
+                             first ? psi32 : nullptr);
             if (s != MRC_OK) return s;
         }
     }

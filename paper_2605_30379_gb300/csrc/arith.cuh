@@ -117,7 +117,7 @@ __device__ __forceinline__ float f64_to_f32_rn(double x)
     const int ex = (int)((hw >> 20) & 0x7ffu);
     const unsigned m23 = ((hw & 0xfffffu) << 3) | (lw >> 29);
     const unsigned rem = lw & 0x1fffffffu;
-    const unsigned up = ((rem > 0x10000000u) | ((rem == 0x10000000u) & m23)) & 1u;
+    const unsigned up = (rem + 0x0fffffffu + (m23 & 1u)) >> 29;  // round half to even: rem > 2^28, or = 2^28 and m23 odd
     unsigned fb = sg | ((((unsigned)(ex - 896)) << 23) + m23 + up);  // a carry may round up to infinity
     const unsigned big = sg | 0x7f800000u | ((ex == 2047 && ((hw & 0xfffffu) | lw)) ? 0x00400000u : 0u);
     fb = ex < 897 ? sg : fb;
@@ -135,7 +135,7 @@ __device__ __forceinline__ dd dd_from_double(double x)
     const int ex = (int)((hw >> 20) & 0x7ffu);
     const unsigned m23 = ((hw & 0xfffffu) << 3) | (lw >> 29);
     const unsigned rem = lw & 0x1fffffffu;
-    const unsigned up = ((rem > 0x10000000u) | ((rem == 0x10000000u) & m23)) & 1u;
+    const unsigned up = (rem + 0x0fffffffu + (m23 & 1u)) >> 29;  // round half to even: rem > 2^28, or = 2^28 and m23 odd
     unsigned fb = sg | ((((unsigned)(ex - 896)) << 23) + m23 + up);
     // x - hi = (rem - up 2^29) 2^(ex - 1075), with the sign of x
     const int r = (int)rem - (int)(up << 29);
@@ -181,6 +181,8 @@ struct Ar<double> {
     static __device__ __forceinline__ double scal_f(double a, float s) { return a * (double)s; }
     static __device__ __forceinline__ double from_d(double x) { return x; }
     static __device__ __forceinline__ double to_d(double x) { return x; }
+    static __device__ __forceinline__ double from_f(float x) { return f32_to_f64(x); }
+    static __device__ __forceinline__ float to_f(double x) { return f64_to_f32_rn(x); }
     static __device__ __forceinline__ double zero() { return 0.0; }
     static __device__ __forceinline__ double one() { return 1.0; }
     static __device__ __forceinline__ double add_nn(double a, double b) { return a + b; }
@@ -200,6 +202,8 @@ struct Ar<float> {
     static __device__ __forceinline__ float scal_f(float a, float s) { return a * s; }
     static __device__ __forceinline__ float from_d(double x) { return f64_to_f32_rn(x); }
     static __device__ __forceinline__ double to_d(float x) { return f32_to_f64(x); }
+    static __device__ __forceinline__ float from_f(float x) { return x; }
+    static __device__ __forceinline__ float to_f(float x) { return x; }
     static __device__ __forceinline__ float zero() { return 0.0f; }
     static __device__ __forceinline__ float one() { return 1.0f; }
     static __device__ __forceinline__ float add_nn(float a, float b) { return a + b; }
@@ -223,6 +227,8 @@ struct Ar<dd> {
     static __device__ __forceinline__ dd scal_f(dd a, float f) { return {a.hi * f, a.lo * f}; }
     static __device__ __forceinline__ dd from_d(double x) { return dd_from_double(x); }
     static __device__ __forceinline__ double to_d(dd x) { return dd_to_double(x); }
+    static __device__ __forceinline__ dd from_f(float x) { return {x, 0.0f}; }
+    static __device__ __forceinline__ float to_f(dd x) { return x.hi + x.lo; }
     static __device__ __forceinline__ dd zero() { return {0.0f, 0.0f}; }
     static __device__ __forceinline__ dd one() { return {1.0f, 0.0f}; }
     static __device__ __forceinline__ dd add_nn(dd a, dd b) { return dd_add_nn(a, b); }
@@ -280,3 +286,5 @@ __device__ __forceinline__ cx<T> c_mul_i(cx<T> a) { return {Ar<T>::neg(a.im), a.
 
 template <class T>
 __device__ __forceinline__ cx<T> c_from_d(double re, double im) { return {Ar<T>::from_d(re), Ar<T>::from_d(im)}; }
+template <class T>
+__device__ __forceinline__ cx<T> c_from_f(float re, float im) { return {Ar<T>::from_f(re), Ar<T>::from_f(im)}; }

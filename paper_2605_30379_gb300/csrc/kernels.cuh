@@ -39,6 +39,14 @@ __device__ __forceinline__ cx<T> fft_load(const FftArgs &a, int64_t k, int e)
         const cx<T> *s = reinterpret_cast<const cx<T> *>(a.src);
         cx<T> v = s[(a.src_row0 + k) * (int64_t)a.src_ld + e];
         return a.src_neg ? c_neg(v) : v;
+    } else if constexpr (SRC == SRC_REAL32) {
+        // packed pair of binary32 rows 2k, 2k+1 (no conversion for the FP32 path)
+        const float *s = reinterpret_cast<const float *>(a.src);
+        const int64_t r0 = 2 * k, r1 = 2 * k + 1;
+        const float x0 = (r0 < a.src_nvalid) ? s[(a.src_row0 + r0) * (int64_t)a.src_ld + e] : 0.0f;
+        const float x1 = (r1 < a.src_nvalid) ? s[(a.src_row0 + r1) * (int64_t)a.src_ld + e] : 0.0f;
+        cx<T> v = c_from_f<T>(x0, x1);
+        return a.src_neg ? c_neg(v) : v;
     } else {
         // packed pair of real rows 2k, 2k+1
         const double *s = reinterpret_cast<const double *>(a.src);
@@ -75,7 +83,6 @@ __device__ __forceinline__ void fft_store(const FftArgs &a, int64_t k, int e, cx
         // real rows 2k (re) and 2k+1 (im), window [lo, hi); the power-of-two
         // scale and the identity of row 0 are applied in the working
         // precision before the conversion
-        double *d = reinterpret_cast<double *>(a.dst);
         v = scale_out(a, v);
         const T vals[2] = {v.re, v.im};
 #pragma unroll
@@ -84,10 +91,17 @@ __device__ __forceinline__ void fft_store(const FftArgs &a, int64_t k, int e, cx
             if (r < a.dst_lo || r >= a.dst_hi) continue;
             T y = vals[h];
             if (a.dst_eye_d > 0 && r == 0 && (e % (a.dst_eye_d + 1)) == 0) y = Ar<T>::add(y, Ar<T>::one());
-            const double x = Ar<T>::to_d(y);
-            double *p = d + (a.dst_row0 + (r - a.dst_lo)) * (int64_t)a.dst_ld + e;
-            if constexpr (DST == DST_REAL64_ADD) *p += x;
-            else *p = x;
+            const int64_t off = (a.dst_row0 + (r - a.dst_lo)) * (int64_t)a.dst_ld + e;
+            if constexpr (DST == DST_REAL32) {
+                reinterpret_cast<float *>(a.dst)[off] = Ar<T>::to_f(y);
+            } else {
+                const double x = Ar<T>::to_d(y);
+                double *p = reinterpret_cast<double *>(a.dst) + off;
+                if constexpr (DST == DST_REAL64_ADD) *p += x;
+                else if constexpr (DST == DST_REAL64_BASE32)
+                    *p = f32_to_f64(reinterpret_cast<const float *>(a.dst_base)[off]) + x;
+                else *p = x;
+            }
         }
     }
 }
@@ -177,6 +191,9 @@ __device__ __forceinline__ void dft_r(cx<T> *v)
 #ifndef MRC_DD_EC
 #define MRC_DD_EC 8
 #endif
+#ifndef MRC_FFT_TWLATE
+#define MRC_FFT_TWLATE 1
+#endif
 template <class T>
 constexpr int fft_default_ec() { return sizeof(cx<T>) == 8 ? MRC_F32_EC : MRC_DD_EC; }
 
@@ -202,10 +219,10 @@ struct FftPlan {
 // fft_pipe_prefetch (complex rows [R][EC], or for a real source the two real
 // rows of each packed point, [R][2][EC] doubles; inter-pass twiddles in spt
 // not yet conjugated).
-template <class T, int LOGR, int EC, int S, bool INV, bool PIPE = false>
+template <class T, int LOGR, int EC, int S, bool INV, bool PIPE = false, bool PRE = false>
 __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<T> *stw, const cx<T> *spt,
                                           int64_t j, int e0, int ecount, int64_t base_out, bool staged,
-                                          const void *stg = nullptr)
+                                          const void *stg = nullptr, const cx<T> *pre = nullptr)
 {
     using P = FftPlan<T, LOGR, EC>;
     constexpr int R = P::R, NT = P::NT;
@@ -234,9 +251,10 @@ __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<
             }
         }
     };
-    if constexpr (FIRST && !PIPE) {
+    if constexpr (FIRST && !PIPE && !PRE) {
         if (!staged) {
             if (a.src_mode == SRC_CPLX) load_global(std::integral_constant<int, SRC_CPLX>{});
+            else if (a.src_mode == SRC_REAL32) load_global(std::integral_constant<int, SRC_REAL32>{});
             else load_global(std::integral_constant<int, SRC_REAL64>{});
         }
     }
@@ -247,7 +265,11 @@ __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<
 #pragma unroll
         for (int q = 0; q < r; ++q) {
             const int rho = b + q * (R / r);
-            if constexpr (FIRST && PIPE) {
+            if constexpr (FIRST && PRE) {
+                cx<T> x = pre[u * r + q];  // loaded before the twiddle tables were filled
+                if (a.Ns > 1) x = c_mul(x, spt[rho]);
+                v[u][q] = x;
+            } else if constexpr (FIRST && PIPE) {
                 cx<T> x;
                 if (a.src_mode == SRC_CPLX) {
                     x = reinterpret_cast<const cx<T> *>(stg)[rho * EC + e];
@@ -296,6 +318,8 @@ __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<
     if constexpr (LAST) {
         if (a.dst_mode == DST_CPLX) store_global(std::integral_constant<int, DST_CPLX>{});
         else if (a.dst_mode == DST_REAL64) store_global(std::integral_constant<int, DST_REAL64>{});
+        else if (a.dst_mode == DST_REAL32) store_global(std::integral_constant<int, DST_REAL32>{});
+        else if (a.dst_mode == DST_REAL64_BASE32) store_global(std::integral_constant<int, DST_REAL64_BASE32>{});
         else store_global(std::integral_constant<int, DST_REAL64_ADD>{});
     } else {
 #pragma unroll
@@ -307,6 +331,26 @@ __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<
             for (int q = 0; q < r; ++q) sm[(ob + q * Ns) * EC + e] = v[u][q];
         }
         __syncthreads();
+    }
+}
+
+// The first stage's global loads on their own (no inter-pass twiddle), issued
+// before the twiddle tables are filled so that both latencies overlap.
+template <class T, int LOGR, int EC, int SRC>
+__device__ __forceinline__ void fft_preload(const FftArgs &a, cx<T> *pre, int64_t j, int e0, int ecount)
+{
+    using P = FftPlan<T, LOGR, EC>;
+    constexpr int R = P::R, NT = P::NT, r = 1 << P::FIRST, UPT = P::EPT / r;
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int u = 0; u < UPT; ++u) {
+        const int unit = tid + u * NT;
+        const int e = unit & (EC - 1), b = unit >> P::LEC;
+#pragma unroll
+        for (int q = 0; q < r; ++q) {
+            const int rho = b + q * (R / r);
+            pre[u * r + q] = (e < ecount) ? fft_load<T, SRC>(a, j + (int64_t)rho * (a.M >> LOGR), e0 + e) : c_zero<T>();
+        }
     }
 }
 
@@ -380,10 +424,22 @@ __device__ __forceinline__ void fft_pass_body(const FftArgs &a)
     cx<T> *spt = stw + R;                             // [R]  inter-pass twiddles
     const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
     const int tid = threadIdx.x;
-    const int64_t j = blockIdx.x;
-    const int e0 = blockIdx.y * EC;
+    const int64_t j = a.chunk_fast ? blockIdx.y : blockIdx.x;
+    const int e0 = (a.chunk_fast ? blockIdx.x : blockIdx.y) * EC;
     const int ecount = min(EC, a.E - e0);
     const int64_t jm = j & (a.Ns - 1);
+#if MRC_FFT_TWLATE
+    constexpr bool PRE = true;
+    cx<T> pre[P::EPT];
+    if (!a.tma) {
+        if (a.src_mode == SRC_CPLX) fft_preload<T, LOGR, EC, SRC_CPLX>(a, pre, j, e0, ecount);
+        else if (a.src_mode == SRC_REAL32) fft_preload<T, LOGR, EC, SRC_REAL32>(a, pre, j, e0, ecount);
+        else fft_preload<T, LOGR, EC, SRC_REAL64>(a, pre, j, e0, ecount);
+    }
+#else
+    constexpr bool PRE = false;
+    const cx<T> *pre = nullptr;
+#endif
     if constexpr (P::NSTAGE > 1)
         for (int t = tid; t < R; t += P::NT) {
             cx<T> w = tw[(int64_t)t << (a.tw_log - LOGR)];
@@ -400,7 +456,10 @@ __device__ __forceinline__ void fft_pass_body(const FftArgs &a)
     if (staged) fft_stage_in_tma<T, LOGR, EC>(a, sm, j, e0);
     __syncthreads();
     const int64_t base_out = (j >> a.logNs << (a.logNs + LOGR)) + jm;
-    fft_stage<T, LOGR, EC, 0, INV>(a, sm, stw, spt, j, e0, ecount, base_out, staged);
+    if (PRE && !staged)
+        fft_stage<T, LOGR, EC, 0, INV, false, PRE>(a, sm, stw, spt, j, e0, ecount, base_out, staged, nullptr, pre);
+    else
+        fft_stage<T, LOGR, EC, 0, INV>(a, sm, stw, spt, j, e0, ecount, base_out, staged);
     if constexpr (P::NSTAGE > 1) fft_stage<T, LOGR, EC, 1, INV>(a, sm, stw, spt, j, e0, ecount, base_out, staged);
     if constexpr (P::NSTAGE > 2) fft_stage<T, LOGR, EC, 2, INV>(a, sm, stw, spt, j, e0, ecount, base_out, staged);
     if constexpr (P::NSTAGE > 3) fft_stage<T, LOGR, EC, 3, INV>(a, sm, stw, spt, j, e0, ecount, base_out, staged);

@@ -3,6 +3,7 @@
 // diagonal scans, residual norms, block gathers for first-entrance kernels and
 // the occupation / first-entrance reductions.
 #include <math.h>
+#include "arith.cuh"
 #include "mrc_internal.h"
 
 #define MRC_ST_SINGULAR 2
@@ -411,6 +412,32 @@ cudaError_t mrc_mre_rhs(const double *Q, const double *L, double *R, int d, int 
     mrc_prof_pre(7, st);
     mre_rhs_kernel<<<grid_for(N * (int64_t)d * c), 256, 0, st>>>(Q, L, R, d, c, N);
     mrc_prof_post(7, st, 0, 0);
+    return cudaGetLastError();
+}
+
+// y = x rounded to binary32 (nearest, ties to even; integer operations only),
+// for the FP32 Newton levels' copy of A.  Four independent elements per
+// thread and iteration, consecutive across the warp.
+__global__ void f64_to_f32_kernel(const double *__restrict__ x, float *__restrict__ y, int64_t n)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = x[i + u * stride];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) y[i + u * stride] = f64_to_f32_rn(v[u]);
+    }
+    for (; i < n; i += stride) y[i] = f64_to_f32_rn(x[i]);
+}
+
+cudaError_t mrc_f64_to_f32(const double *x, float *y, int64_t n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    mrc_prof_pre(7, st);
+    f64_to_f32_kernel<<<grid_for(n), 256, 0, st>>>(x, y, n);
+    mrc_prof_post(7, st, (double)n * 12.0, 0);
     return cudaGetLastError();
 }
 

@@ -4,8 +4,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-enum { SRC_CPLX = 0, SRC_REAL64 = 1 };
-enum { DST_CPLX = 0, DST_REAL64 = 1, DST_REAL64_ADD = 2 };
+// Real sources and destinations hold pairs of rows (2k, 2k+1) per packed
+// complex point.  REAL32: binary32 rows.  DST_REAL64_BASE32: out = base + x
+// with base the binary32 rows of FftArgs::dst_base (same indexing as out).
+enum { SRC_CPLX = 0, SRC_REAL64 = 1, SRC_REAL32 = 2 };
+enum { DST_CPLX = 0, DST_REAL64 = 1, DST_REAL64_ADD = 2, DST_REAL32 = 3, DST_REAL64_BASE32 = 4 };
 enum { PREC_F64 = 0, PREC_F32 = 1, PREC_DD = 2 };
 
 struct FftArgs {
@@ -36,7 +39,9 @@ struct FftArgs {
     int dst_scaled;         // dst_scale != 1 (decided on the host: no FP64 compare in the kernels)
     int dst_eye_d;          // REAL64*: if > 0 add 1 to the diagonal of real row 0 (d = this)
     void *dst2;             // double-float DST_CPLX only: also write the hi parts here as FP32 complex (or null)
+    const void *dst_base;   // DST_REAL64_BASE32: binary32 rows added to the result
     int tma;                // CPLX source staged into shared memory by bulk copies (first stage)
+    int chunk_fast;         // grid order: 1 = entry chunk in blockIdx.x, row offset j in blockIdx.y
     int *status;            // device status word: MRC_ERR_TIMEOUT (6) if a bounded wait gives up
 };
 
@@ -67,6 +72,7 @@ struct FftDst {
     double scale;
     int eye_d;
     void *ptr2 = nullptr;  // double-float DST_CPLX: FP32 copy of the hi parts (FftArgs::dst2)
+    const void *base = nullptr;  // DST_REAL64_BASE32: binary32 rows (FftArgs::dst_base)
 };
 
 // prof.cu: device status word that bounded in-kernel waits report timeouts to
@@ -140,5 +146,6 @@ cudaError_t mrc_weighted_rowsum(const double *g, int nC, int nD, int64_t N, cons
 cudaError_t mrc_occupation_k(const double *P, int d, int64_t N, const double *alpha, const int *inB, double *out,
                              cudaStream_t st);
 cudaError_t mrc_one_minus(const double *x, double *y, int64_t n, cudaStream_t st);
+cudaError_t mrc_f64_to_f32(const double *x, float *y, int64_t n, cudaStream_t st);
 cudaError_t mrc_mre_operator(const double *Q, double *A, int d, int64_t N, int scheme, cudaStream_t st);
 cudaError_t mrc_mre_rhs(const double *Q, const double *L, double *R, int d, int c, int64_t N, cudaStream_t st);
