@@ -214,6 +214,67 @@ struct FftPlan {
     static constexpr int LEC = EC == 1 ? 0 : EC == 2 ? 1 : EC == 4 ? 2 : EC == 8 ? 3 : 4;
 };
 
+// Element offsets of the first-stage loads and last-stage stores: a CTA's
+// points sit at offset o0 + q * dq from a per-CTA base pointer (q the point
+// index inside a thread's butterfly), so each point costs one multiply-add
+// and one address formation.  With OFF32 (every offset of the launch below
+// 2^32 elements, decided on the host) the offsets are 32-bit.
+template <bool OFF32>
+using fft_off_t = typename std::conditional<OFF32, unsigned, int64_t>::type;
+
+// The first stage's global loads: x[u * r + q] = point rho = b + q R / r of
+// unit u, i.e. packed row k = j + rho M / R (a complex row, or the real rows
+// 2k and 2k + 1); zero past the valid rows and past the entry count.
+template <class T, int LOGR, int EC, int SRC, bool OFF32>
+__device__ __forceinline__ void fft_gather(const FftArgs &a, cx<T> *x, int64_t j, int e0, int ecount)
+{
+    using P = FftPlan<T, LOGR, EC>;
+    using Off = fft_off_t<OFF32>;
+    using Elt = typename std::conditional<SRC == SRC_CPLX, cx<T>,
+                                          typename std::conditional<SRC == SRC_REAL32, float, double>::type>::type;
+    constexpr int R = P::R, NT = P::NT, r = 1 << P::FIRST, UPT = P::EPT / r;
+    constexpr int ROWS = SRC == SRC_CPLX ? 1 : 2;  // stored rows per packed point
+    const int tid = threadIdx.x;
+    const int S = (int)(a.M >> LOGR);
+    const int ld = a.src_ld;
+    const int nv = (int)(a.src_nvalid < 0x7fffffff ? a.src_nvalid : 0x7fffffff);
+    const Elt *base = reinterpret_cast<const Elt *>(a.src) + a.src_row0 * (int64_t)ld + e0;
+    const Off dq = (Off)((int64_t)ROWS * (R / r) * S * ld);
+#pragma unroll
+    for (int u = 0; u < UPT; ++u) {
+        const int unit = tid + u * NT;
+        const int e = unit & (EC - 1), b = unit >> P::LEC;
+        const bool live = e < ecount;
+        const int k0 = (int)j + b * S;
+        const Off o0 = (Off)((int64_t)ROWS * k0 * ld + e);
+#pragma unroll
+        for (int q = 0; q < r; ++q) {
+            const int k = k0 + q * (R / r) * S;
+            const Off o = o0 + (Off)q * dq;
+            cx<T> v;
+            if constexpr (SRC == SRC_CPLX) {
+                v = (live && k < nv) ? base[o] : c_zero<T>();
+            } else if constexpr (SRC == SRC_REAL32) {
+                const float x0 = (live && 2 * k < nv) ? base[o] : 0.0f;
+                const float x1 = (live && 2 * k + 1 < nv) ? base[o + (Off)ld] : 0.0f;
+                v = c_from_f<T>(x0, x1);
+            } else {
+                const double x0 = (live && 2 * k < nv) ? base[o] : 0.0;
+                const double x1 = (live && 2 * k + 1 < nv) ? base[o + (Off)ld] : 0.0;
+                v = c_from_d<T>(x0, x1);
+            }
+            x[u * r + q] = a.src_neg ? c_neg(v) : v;
+        }
+    }
+}
+
+template <class T, int LOGR, int EC, int SRC>
+__device__ __forceinline__ void fft_gather_any(const FftArgs &a, cx<T> *x, int64_t j, int e0, int ecount)
+{
+    if (a.src_off32) fft_gather<T, LOGR, EC, SRC, true>(a, x, j, e0, ecount);
+    else fft_gather<T, LOGR, EC, SRC, false>(a, x, j, e0, ecount);
+}
+
 // One in-CTA stage S.  Stage 0 reads its points from global memory, from sm
 // (bulk-copy staging) or, with PIPE, from the staging buffer stg filled by
 // fft_pipe_prefetch (complex rows [R][EC], or for a real source the two real
@@ -237,17 +298,13 @@ __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<
     // first stage from global memory: one loop per source mode
     auto load_global = [&](auto src_tag) {
         constexpr int SRC = decltype(src_tag)::value;
+        fft_gather_any<T, LOGR, EC, SRC>(a, &v[0][0], j, e0, ecount);
+        if (a.Ns > 1) {
 #pragma unroll
-        for (int u = 0; u < UPT; ++u) {
-            const int unit = tid + u * NT;
-            const int e = unit & (EC - 1), b = unit >> P::LEC;
+            for (int u = 0; u < UPT; ++u) {
+                const int b = (tid + u * NT) >> P::LEC;
 #pragma unroll
-            for (int q = 0; q < r; ++q) {
-                const int rho = b + q * (R / r);
-                cx<T> x = c_zero<T>();
-                if (e < ecount) x = fft_load<T, SRC>(a, j + (int64_t)rho * (a.M >> LOGR), e0 + e);
-                if (a.Ns > 1) x = c_mul(x, spt[rho]);
-                v[u][q] = x;
+                for (int q = 0; q < r; ++q) v[u][q] = c_mul(v[u][q], spt[b + q * (R / r)]);
             }
         }
     };
@@ -303,24 +360,76 @@ __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<
         }
         dft_r<T, INV, LR>(v[u]);
     }
-    auto store_global = [&](auto dst_tag) {
+    // Output point q of unit u goes to row k = k0 + q Ns a.Ns.  Complex rows
+    // sit at k ld + e; the real rows 2k + h (kept in the window [lo, hi)) at
+    // (row0 - lo + 2k + h) ld + e, offsets relative to the CTA's entry e0.
+    auto store_global = [&](auto dst_tag, auto off_tag) {
         constexpr int DST = decltype(dst_tag)::value;
+        constexpr bool OFF32 = decltype(off_tag)::value;
+        using Off = fft_off_t<OFF32>;
+        const int ld = a.dst_ld;
+        const int64_t kst = (int64_t)Ns * a.Ns;
 #pragma unroll
         for (int u = 0; u < UPT; ++u) {
             const int unit = tid + u * NT;
             const int e = unit & (EC - 1), b = unit >> P::LEC;
+            if (e >= ecount) continue;
             const int ob = ((b >> LNS) << (LNS + LR)) + (b & (Ns - 1));
+            const int64_t k0 = base_out + (int64_t)ob * a.Ns;
+            if constexpr (DST == DST_CPLX) {
+                cx<T> *d = reinterpret_cast<cx<T> *>(a.dst) + e0;
+                const Off o0 = (Off)(k0 * ld + e), dq = (Off)(kst * ld);
 #pragma unroll
-            for (int q = 0; q < r; ++q)
-                if (e < ecount) fft_store<T, DST>(a, base_out + (int64_t)(ob + q * Ns) * a.Ns, e0 + e, v[u][q]);
+                for (int q = 0; q < r; ++q) {
+                    cx<T> y = v[u][q];
+                    if (a.dst_scaled) y = scale_out(a, y);
+                    d[o0 + (Off)q * dq] = y;
+                    if constexpr (__is_same(T, dd))
+                        if (a.dst2)
+                            (reinterpret_cast<cx<float> *>(a.dst2) + e0)[o0 + (Off)q * dq] = {y.re.hi, y.im.hi};
+                }
+            } else {
+                const int lo = (int)a.dst_lo, hi = (int)a.dst_hi;
+                const Off o0 = (Off)((a.dst_row0 - a.dst_lo + 2 * k0) * ld + e), dq = (Off)(2 * kst * ld);
+                const bool eye_e = a.dst_eye_d > 0 && (e0 + e) % (a.dst_eye_d + 1) == 0;
+#pragma unroll
+                for (int q = 0; q < r; ++q) {
+                    const cx<T> y = scale_out(a, v[u][q]);
+                    const T vals[2] = {y.re, y.im};
+                    const int r0 = (int)(k0 + q * kst) * 2;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int rr = r0 + h;
+                        if (rr < lo || rr >= hi) continue;
+                        T z = vals[h];
+                        if (eye_e && rr == 0) z = Ar<T>::add(z, Ar<T>::one());
+                        const Off o = o0 + (Off)q * dq + (Off)(h * ld);
+                        if constexpr (DST == DST_REAL32) {
+                            (reinterpret_cast<float *>(a.dst) + e0)[o] = Ar<T>::to_f(z);
+                        } else {
+                            const double xz = Ar<T>::to_d(z);
+                            double *pz = reinterpret_cast<double *>(a.dst) + e0 + o;
+                            if constexpr (DST == DST_REAL64_ADD) *pz += xz;
+                            else if constexpr (DST == DST_REAL64_BASE32)
+                                *pz = f32_to_f64((reinterpret_cast<const float *>(a.dst_base) + e0)[o]) + xz;
+                            else *pz = xz;
+                        }
+                    }
+                }
+            }
         }
     };
+    auto store_mode = [&](auto off_tag) {
+        if (a.dst_mode == DST_CPLX) store_global(std::integral_constant<int, DST_CPLX>{}, off_tag);
+        else if (a.dst_mode == DST_REAL64) store_global(std::integral_constant<int, DST_REAL64>{}, off_tag);
+        else if (a.dst_mode == DST_REAL32) store_global(std::integral_constant<int, DST_REAL32>{}, off_tag);
+        else if (a.dst_mode == DST_REAL64_BASE32)
+            store_global(std::integral_constant<int, DST_REAL64_BASE32>{}, off_tag);
+        else store_global(std::integral_constant<int, DST_REAL64_ADD>{}, off_tag);
+    };
     if constexpr (LAST) {
-        if (a.dst_mode == DST_CPLX) store_global(std::integral_constant<int, DST_CPLX>{});
-        else if (a.dst_mode == DST_REAL64) store_global(std::integral_constant<int, DST_REAL64>{});
-        else if (a.dst_mode == DST_REAL32) store_global(std::integral_constant<int, DST_REAL32>{});
-        else if (a.dst_mode == DST_REAL64_BASE32) store_global(std::integral_constant<int, DST_REAL64_BASE32>{});
-        else store_global(std::integral_constant<int, DST_REAL64_ADD>{});
+        if (a.dst_off32) store_mode(std::true_type{});
+        else store_mode(std::false_type{});
     } else {
 #pragma unroll
         for (int u = 0; u < UPT; ++u) {
@@ -339,19 +448,7 @@ __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<
 template <class T, int LOGR, int EC, int SRC>
 __device__ __forceinline__ void fft_preload(const FftArgs &a, cx<T> *pre, int64_t j, int e0, int ecount)
 {
-    using P = FftPlan<T, LOGR, EC>;
-    constexpr int R = P::R, NT = P::NT, r = 1 << P::FIRST, UPT = P::EPT / r;
-    const int tid = threadIdx.x;
-#pragma unroll
-    for (int u = 0; u < UPT; ++u) {
-        const int unit = tid + u * NT;
-        const int e = unit & (EC - 1), b = unit >> P::LEC;
-#pragma unroll
-        for (int q = 0; q < r; ++q) {
-            const int rho = b + q * (R / r);
-            pre[u * r + q] = (e < ecount) ? fft_load<T, SRC>(a, j + (int64_t)rho * (a.M >> LOGR), e0 + e) : c_zero<T>();
-        }
-    }
+    fft_gather_any<T, LOGR, EC, SRC>(a, pre, j, e0, ecount);
 }
 
 // Bulk-copy staging of a complex source (TMA, cp.async.bulk): warp 0 copies

@@ -150,6 +150,15 @@ cudaError_t fft_run(const FftSrc &src, const FftDst &dst, int64_t M, int E, int 
             a.dst_mode = DST_CPLX; a.dst = scratch; a.dst_ld = sld; a.dst_lo = 0; a.dst_hi = 0; a.dst_row0 = 0;
             a.dst_scale = 1.0; a.dst_eye_d = 0;
         }
+        // 32-bit element offsets when every offset a pass forms fits
+        {
+            const int64_t lim = (int64_t)1 << 32;
+            const int64_t src_span = (a.src_mode == SRC_CPLX ? M : 2 * M + 1) * (int64_t)a.src_ld + ec;
+            const int64_t dst_span = a.dst_mode == DST_CPLX ? M * (int64_t)a.dst_ld + ec
+                                                            : (a.dst_row0 + (a.dst_hi - a.dst_lo) + 1) * a.dst_ld + ec;
+            a.src_off32 = src_span < lim;
+            a.dst_off32 = dst_span < lim && a.dst_row0 >= 0 && a.dst_hi >= a.dst_lo;
+        }
         a.dst_scale_f = (float)a.dst_scale;
         a.dst_scaled = a.dst_scale != 1.0;
         // bulk-copy staging of a complex source: 16-byte aligned row segments

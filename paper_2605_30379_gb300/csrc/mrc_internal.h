@@ -40,6 +40,7 @@ struct FftArgs {
     int dst_eye_d;          // REAL64*: if > 0 add 1 to the diagonal of real row 0 (d = this)
     void *dst2;             // double-float DST_CPLX only: also write the hi parts here as FP32 complex (or null)
     const void *dst_base;   // DST_REAL64_BASE32: binary32 rows added to the result
+    int src_off32, dst_off32; // every source / destination element offset of the pass fits 32 bits
     int tma;                // CPLX source staged into shared memory by bulk copies (first stage)
     int chunk_fast;         // grid order: 1 = entry chunk in blockIdx.x, row offset j in blockIdx.y
     int *status;            // device status word: MRC_ERR_TIMEOUT (6) if a bounded wait gives up
