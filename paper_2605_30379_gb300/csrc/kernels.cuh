@@ -180,13 +180,16 @@ __device__ __forceinline__ void dft_r(cx<T> *v)
     }
 }
 
-// Entries per CTA of the passes: for 8-byte complex values (FP32) 8, i.e.
-// 64-byte row segments -- at d = 64, N = 2^18 the FP32 FFT took 103.5 ms
-// with 8, 111.6 ms with 16 and 163 ms with 4 (smaller CTAs overlap loads
-// and compute better; 32-byte segments halve the useful bytes per request);
-// for 16-byte values (FP64, double-float) 8.
+// Entries per CTA of the passes: for 8-byte complex values (FP32) 16, i.e.
+// 128-byte row segments and 16 points per thread in the radix-2^9 and 2^10
+// passes.  At d = 64, N = 2^18, once the passes' index arithmetic was
+// strength-reduced, the FP32 FFT took 55.4 ms with 16 against 74.9 ms with 8
+// (with 8 the passes were bound by the L1 / shared-memory pipe at 86 % of
+// peak); before that, 8 had been the faster (103.5 against 111.6 ms).  For
+// 16-byte values (FP64, double-float) 8: double-float with 16 went
+// 50.9 -> 59.8 ms.
 #ifndef MRC_F32_EC
-#define MRC_F32_EC 8
+#define MRC_F32_EC 16
 #endif
 #ifndef MRC_DD_EC
 #define MRC_DD_EC 8
