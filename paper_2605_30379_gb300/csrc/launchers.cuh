@@ -104,6 +104,14 @@ int fft_chunk_fast()
     return (v && v[0] == '0') ? 0 : 1;
 }
 
+// MRC_FFT_OFF64=1 makes every pass use 64-bit element offsets (the path
+// large transforms take), so that a test can compare it with the 32-bit one.
+inline bool fft_force_off64()
+{
+    const char *v = getenv("MRC_FFT_OFF64");
+    return v && v[0] == '1';
+}
+
 // Radix plan: one pass up to 2^10, else two passes of sizes 2^ceil(l/2), 2^floor(l/2).
 inline int fft_plan(int logM, int *logRs)
 {
@@ -156,8 +164,9 @@ cudaError_t fft_run(const FftSrc &src, const FftDst &dst, int64_t M, int E, int 
             const int64_t src_span = (a.src_mode == SRC_CPLX ? M : 2 * M + 1) * (int64_t)a.src_ld + ec;
             const int64_t dst_span = a.dst_mode == DST_CPLX ? M * (int64_t)a.dst_ld + ec
                                                             : (a.dst_row0 + (a.dst_hi - a.dst_lo) + 1) * a.dst_ld + ec;
-            a.src_off32 = src_span < lim;
-            a.dst_off32 = dst_span < lim && a.dst_row0 >= 0 && a.dst_hi >= a.dst_lo;
+            const bool off64 = fft_force_off64();
+            a.src_off32 = !off64 && src_span < lim;
+            a.dst_off32 = !off64 && dst_span < lim && a.dst_row0 >= 0 && a.dst_hi >= a.dst_lo;
         }
         a.dst_scale_f = (float)a.dst_scale;
         a.dst_scaled = a.dst_scale != 1.0;

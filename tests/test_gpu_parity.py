@@ -334,6 +334,35 @@ def test_fft_pipelined_pass_matches_plain_pass(mrc):
             assert np.abs(got - out["0"]).max() <= 1e-13, (d, mode)
 
 
+def test_fft_64bit_offsets_match_32bit(mrc):
+    """The passes address their first-stage loads and last-stage stores in
+    32-bit element offsets when every offset of a launch fits, else in 64-bit
+    ones (large E x M).  MRC_FFT_OFF64=1 forces the 64-bit path: only the
+    address arithmetic differs, so both precisions' inverses must agree
+    exactly, and stay within the parity gate.  N = 5000 (two-pass transforms,
+    a ragged valid-row range), d = 12 (E = 144 = 9 chunks of 16) and d = 5
+    (E = 25, a partial chunk)."""
+    import os
+    for d in (12, 5):
+        q, _ = synth.weibull_model(d, 5000, seed=71 + d)
+        A = synth.identity_minus(q)
+        ref = oracle.inverse_left(A)
+        for prec, tol in (("fp64", None), ("mixed", TOL_REL)):
+            got = {}
+            for flag in ("0", "1"):
+                os.environ["MRC_FFT_OFF64"] = flag
+                try:
+                    got[flag] = mrc.inverse(dev(A), prec=prec).cpu().numpy()
+                    mrc.sync_status()
+                finally:
+                    del os.environ["MRC_FFT_OFF64"]
+            assert np.array_equal(got["0"], got["1"]), (d, prec)
+            if tol is None:
+                assert np.abs(got["0"] - ref).max() <= TOL64, d
+            else:
+                assert e_rel(got["0"], ref) <= tol, d
+
+
 @pytest.mark.parametrize("d,N", [(64, 700), (40, 1500), (70, 300)])
 def test_fp32_pair_product_split_matches_unsplit(mrc, d, N):
     """The FP32 64 x 64-tile product puts the two frequencies of a pair on two
