@@ -302,6 +302,12 @@ def run_mre(args, rank, world, local):
     if roof:
         roof["peak_kind"] = peak_kind
         roof["traffic"], roof["traffic_source"] = measured_traffic(args.workload, roof["kernel"])
+    # the same roofline for every kernel class of the untimed breakdown step
+    by_class = {}
+    for kc, (cms, cn, cb, cf) in class_work.items():
+        r_ = roofline_for(kc, cms, cn, cb, cf, peaks, clocks["sm_mhz"] if clocks else None, d=None if batch else d)
+        if r_ and KCLASS[kc] != "misc":
+            by_class[r_["kernel"]] = {k_: r_[k_] for k_ in ("bound", "achieved", "peak", "unit", "frac", "avg_ms")}
     # accuracy: availability against the exact solution (exp(G h) powers)
     import scipy.linalg as sl
     step_m = sl.expm(b["G"] * extra["h"])
@@ -483,10 +489,12 @@ def main():
 
     # per-class device time of one step (untimed), to pick the dominant kernel
     breakdown = {}
+    class_work = {}
     for kc in ([] if (args.no_breakdown or batch) else KCLASS):
         ms, n, b, f = prof(kc, step)
         if n:
             breakdown[KCLASS[kc]] = {"ms": ms, "launches": n}
+            class_work[kc] = (ms, n, b, f)
     dominant = max((kc for kc in KCLASS if KCLASS[kc] in breakdown), key=lambda kc: breakdown[KCLASS[kc]]["ms"],
                    default=2 if args.prec == "mixed" else 4)
 
@@ -560,6 +568,12 @@ def main():
     if roof:
         roof["peak_kind"] = peak_kind
         roof["traffic"], roof["traffic_source"] = measured_traffic(args.workload, roof["kernel"])
+    # the same roofline for every kernel class of the untimed breakdown step
+    by_class = {}
+    for kc, (cms, cn, cb, cf) in class_work.items():
+        r_ = roofline_for(kc, cms, cn, cb, cf, peaks, clocks["sm_mhz"] if clocks else None, d=None if batch else d)
+        if r_ and KCLASS[kc] != "misc":
+            by_class[r_["kernel"]] = {k_: r_[k_] for k_ in ("bound", "achieved", "peak", "unit", "frac", "avg_ms")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -587,6 +601,7 @@ def main():
             "gpu_launches": int(launches),
             "stage_ms": breakdown,
             "roofline": roof,
+            "roofline_by_class": by_class or None,
             "clocks": clocks,
             "e2e": None if ms_e2e is None else {
                 "value": job_throughput(coeffs, ms_e2e, world), "unit": "coefficients/s",
