@@ -45,6 +45,8 @@ WORKLOADS = {
     "weibull_d16_N65536": (16, 1 << 16, "weibull", {}),
     "weibull_d4_N1024": (4, 1024, "weibull", {}),
     "lognormal_d64_N65536": (64, 1 << 16, "lognormal", {}),
+    # the default workload's transform lengths with E = 256 (small profiler captures)
+    "lognormal_d16_N262144": (16, 1 << 18, "lognormal", {}),
     "weibull_d256_N32768": (256, 1 << 15, "weibull", {"alpha": 0.5, "shape": (0.5, 3.0)}),
     # 256 independent models, d ~ U{3..48}, N = round(2^U[10,16]), half discrete Weibull,
     # half Lognormal mean-value (h = 0.05), one captured batch
