@@ -144,6 +144,37 @@ def test_residual_matches_oracle(mrc, prec):
     assert abs(rep["res_max_abs"] - np.abs(rl_ref).max()) <= 1e-12
 
 
+@pytest.mark.parametrize("prec,u", [("fp64", 2.0 ** -53), ("mixed", 2.0 ** -46)])
+def test_fft_product_within_prop_2_1_bound(mrc, prec, u):
+    """Prop 2.1 (Eq. (fft-forward-error)): a product C = A * B formed by
+    zero-padded FFTs, per-frequency matrix products and an inverse FFT obeys
+    ||C - C_fl||_{G,L} <= sqrt(L) ||A||_{G,L} ||B||_{G,L} delta_{L,s}.
+    mrc_residual forms rho = e0 - A * B that way (L = 2 pow2ceil(N)), so
+    rho's error bounds the product's on [0, N).  Small integer entries make
+    the oracle's direct sum exact.  Readings of the model constants:
+    sigma_L = 7 u log2 L (radix-2 FFT with accurately rounded twiddles),
+    gamma_s = sqrt(2) (s + 2) u; u = 2^-53 for FP64 and 2^-46 for the
+    double-float residual (a few 2^-48 roundings per operation).  The
+    measured error must also stay far below the bound's order u sqrt(L)
+    log2 L, so the check is not vacuous."""
+    rng = np.random.default_rng(23)
+    d, N = 7, 1000
+    A = rng.integers(-8, 9, size=(N, d, d)).astype(np.float64)
+    B = rng.integers(-8, 9, size=(N, d, d)).astype(np.float64)
+    rl_ref, _ = oracle.residuals(A, B)  # exact: integers below 2^53
+    rl, _, _ = mrc.residual(dev(A), dev(B), sides=1, prec=prec)
+    err = np.sqrt(((rl.cpu().numpy() - rl_ref) ** 2).sum())
+    L = 2 * (1 << (N - 1).bit_length())
+    sig = 7 * u * np.log2(L)
+    gam = np.sqrt(2.0) * (d + 2) * u
+    beta = 2 * sig + sig ** 2 + gam * (1 + sig) ** 2
+    delta = beta + sig * (1 + beta)
+    norm_g = lambda X: np.sqrt((X ** 2).sum())
+    bound = np.sqrt(L) * norm_g(A) * norm_g(B) * delta
+    assert err <= bound, (err, bound)
+    assert err <= 1e-2 * bound, (err, bound)
+
+
 # ---------------------------------------------------------- derived outputs
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_transition_matches_oracle(mrc, prec):
