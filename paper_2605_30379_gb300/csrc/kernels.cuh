@@ -30,33 +30,8 @@
 // radix 2/4 then 8 with the points of each butterfly in registers and one
 // shared-memory exchange per stage, and writes element f to
 // (j/Ns)*Ns*R + (j mod Ns) + f*Ns.  After the last pass the output is in
-// natural frequency order.
-template <class T, int SRC>
-__device__ __forceinline__ cx<T> fft_load(const FftArgs &a, int64_t k, int e)
-{
-    if constexpr (SRC == SRC_CPLX) {
-        if (k >= a.src_nvalid) return c_zero<T>();
-        const cx<T> *s = reinterpret_cast<const cx<T> *>(a.src);
-        cx<T> v = s[(a.src_row0 + k) * (int64_t)a.src_ld + e];
-        return a.src_neg ? c_neg(v) : v;
-    } else if constexpr (SRC == SRC_REAL32) {
-        // packed pair of binary32 rows 2k, 2k+1 (no conversion for the FP32 path)
-        const float *s = reinterpret_cast<const float *>(a.src);
-        const int64_t r0 = 2 * k, r1 = 2 * k + 1;
-        const float x0 = (r0 < a.src_nvalid) ? s[(a.src_row0 + r0) * (int64_t)a.src_ld + e] : 0.0f;
-        const float x1 = (r1 < a.src_nvalid) ? s[(a.src_row0 + r1) * (int64_t)a.src_ld + e] : 0.0f;
-        cx<T> v = c_from_f<T>(x0, x1);
-        return a.src_neg ? c_neg(v) : v;
-    } else {
-        // packed pair of real rows 2k, 2k+1
-        const double *s = reinterpret_cast<const double *>(a.src);
-        const int64_t r0 = 2 * k, r1 = 2 * k + 1;
-        const double x0 = (r0 < a.src_nvalid) ? s[(a.src_row0 + r0) * (int64_t)a.src_ld + e] : 0.0;
-        const double x1 = (r1 < a.src_nvalid) ? s[(a.src_row0 + r1) * (int64_t)a.src_ld + e] : 0.0;
-        cx<T> v = c_from_d<T>(x0, x1);
-        return a.src_neg ? c_neg(v) : v;
-    }
-}
+// natural frequency order.  The global loads and stores of a pass are in
+// fft_gather and fft_stage's store_global below.
 
 // multiply by the (signed power of two) output scale in the working precision
 template <class T>
@@ -64,46 +39,6 @@ __device__ __forceinline__ cx<T> scale_out(const FftArgs &a, cx<T> v)
 {
     if constexpr (sizeof(T) == 8 && sizeof(cx<T>) == 16 && !__is_same(T, dd)) return c_scal(v, a.dst_scale);
     else return {Ar<T>::scal_f(v.re, a.dst_scale_f), Ar<T>::scal_f(v.im, a.dst_scale_f)};
-}
-
-// Store of one output point; DST is the destination mode, fixed per launch
-// (the stage branches on it once, outside its per-point loop).  No FP64
-// instruction is issued here for the FP32-based precisions except the add
-// of DST_REAL64_ADD and the final FP64 add of a double-float value.
-template <class T, int DST>
-__device__ __forceinline__ void fft_store(const FftArgs &a, int64_t k, int e, cx<T> v)
-{
-    if constexpr (DST == DST_CPLX) {
-        cx<T> *d = reinterpret_cast<cx<T> *>(a.dst);
-        if (a.dst_scaled) v = scale_out(a, v);
-        d[k * (int64_t)a.dst_ld + e] = v;
-        if constexpr (__is_same(T, dd))
-            if (a.dst2) reinterpret_cast<cx<float> *>(a.dst2)[k * (int64_t)a.dst_ld + e] = {v.re.hi, v.im.hi};
-    } else {
-        // real rows 2k (re) and 2k+1 (im), window [lo, hi); the power-of-two
-        // scale and the identity of row 0 are applied in the working
-        // precision before the conversion
-        v = scale_out(a, v);
-        const T vals[2] = {v.re, v.im};
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t r = 2 * k + h;
-            if (r < a.dst_lo || r >= a.dst_hi) continue;
-            T y = vals[h];
-            if (a.dst_eye_d > 0 && r == 0 && (e % (a.dst_eye_d + 1)) == 0) y = Ar<T>::add(y, Ar<T>::one());
-            const int64_t off = (a.dst_row0 + (r - a.dst_lo)) * (int64_t)a.dst_ld + e;
-            if constexpr (DST == DST_REAL32) {
-                reinterpret_cast<float *>(a.dst)[off] = Ar<T>::to_f(y);
-            } else {
-                const double x = Ar<T>::to_d(y);
-                double *p = reinterpret_cast<double *>(a.dst) + off;
-                if constexpr (DST == DST_REAL64_ADD) *p += x;
-                else if constexpr (DST == DST_REAL64_BASE32)
-                    *p = f32_to_f64(reinterpret_cast<const float *>(a.dst_base)[off]) + x;
-                else *p = x;
-            }
-        }
-    }
 }
 
 // Small DFTs in registers, natural order in and out.  INV selects the sign
@@ -203,6 +138,8 @@ __device__ __forceinline__ void dft_r(cx<T> *v)
 #ifndef MRC_DD_STAGE_NORM
 #define MRC_DD_STAGE_NORM 0
 #endif
+// First-stage global loads issued before the CTA fills its twiddle tables,
+// so that both latencies overlap (1, the default); 0 loads after the fill.
 #ifndef MRC_FFT_TWLATE
 #define MRC_FFT_TWLATE 1
 #endif
