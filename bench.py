@@ -45,9 +45,12 @@ WORKLOADS = {
     "weibull_d16_N65536": (16, 1 << 16, "weibull", {}),
     "weibull_d4_N1024": (4, 1024, "weibull", {}),
     "lognormal_d64_N65536": (64, 1 << 16, "lognormal", {}),
+    # the default workload's d with a device footprint of a few GB (profiler captures)
+    "lognormal_d64_N16384": (64, 1 << 14, "lognormal", {}),
     # the default workload's transform lengths with E = 256 (small profiler captures)
     "lognormal_d16_N262144": (16, 1 << 18, "lognormal", {}),
-    "weibull_d256_N32768": (256, 1 << 15, "weibull", {"alpha": 0.5, "shape": (0.5, 3.0)}),
+    # dense precision stress: iterative refinement with two sweeps
+    "weibull_d256_N32768": (256, 1 << 15, "weibull", {"alpha": 0.5, "shape": (0.5, 3.0), "sweeps": 2}),
     # 256 independent models, d ~ U{3..48}, N = round(2^U[10,16]), half discrete Weibull,
     # half Lognormal mean-value (h = 0.05), one captured batch
     "batch256": (0, 0, "batch", {"n": 256}),
@@ -56,6 +59,8 @@ WORKLOADS = {
     "mre_exponential_N32768": (4, 1 << 15, "mre", {"h": 0.005}),
 }
 DEFAULT_WORKLOAD = "lognormal_d64_N262144"
+# the metric both arms report (mrc and the oracle reference arm)
+METRIC = "\u03c8 coefficients/s (N\u00b7d\u00b2) mixed-precision vs FP64 GPU at \u22641e-10 residual"
 
 # kernel classes of the library's profiler (include/mrc.h MRC_K_*)
 KCLASS = {1: "fft_f64", 2: "fft_f32", 3: "fft_dd", 4: "pairmul_f64", 5: "pairmul_f32", 6: "pairmul_dd", 7: "misc"}
@@ -69,53 +74,38 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-# FP32 instruction issue: 152 SMs x 128 lanes per clock.  A double-float
-# complex multiply-accumulate (4 dd fma, 15 FP32 instructions each) is 8
-# dd-flops, i.e. 7.5 FP32 instructions per dd-flop.  FP64 DFMA rate measured
-# on this machine's GB300 by a dependent-chain-free FMA loop: 1.19 TFLOP/s.
+# FP64 DFMA rate measured on this machine's GB300 by a dependent-chain-free FMA
+# loop (1.19 TFLOP/s); FP32 FFMA: 152 SMs x 128 lanes x 2 flops per clock.
 FP32_LANES = 152 * 128
-DD_INSTR_PER_FLOP = 7.5
 FP64_TFLOPS_MEASURED = 1.19
 
 
-def dd_product_on_tensor_cores(d):
-    """The double-float products run as exact digit products on the tensor
-    cores for 32 <= d <= 512 unless MRC_DD_PRODUCT=simt picks the FP32-pipe
-    kernel; there the FP32 lanes do not bound them and their bytes do."""
-    return d is not None and 32 <= d <= 512 and os.environ.get("MRC_DD_PRODUCT") != "simt"
-
-
 def roofline_for(kclass, ms_total, launches, bytes_, flops, peaks, sm_mhz, d=None):
+    """Roofline of one kernel class from its timed launches: achieved =
+    algorithmic bytes (or flops) per launch / average launch time.  FFT
+    passes, the tensor-core digit products (whose FP32 and tensor pipes are
+    not the binding resource at d <= 64) and the small kernels are reported
+    against the measured HBM copy bandwidth; FP64 products against the
+    measured DFMA rate, FP32-pipe products against the FFMA peak."""
     if not launches:
         return None
     per_ms = ms_total / launches
     name = KCLASS[kclass]
     clk = (sm_mhz or 2070.0) * 1e6
-    if name == "pairmul_dd" and dd_product_on_tensor_cores(d):
+    on_tc = name in ("pairmul_dd", "pairmul_f32") and d is not None and 32 <= d <= (512 if name == "pairmul_dd" else 64)
+    if name.startswith("fft_") or name == "misc" or on_tc:
         ach = bytes_ / launches / (per_ms * 1e-3) / 1e9
         peak = peaks["hbm_gbs"]
+        src = "MEASURED_PEAKS.json hbm_gbs (of measured)" + ("; tensor-core digit products" if on_tc else "")
         return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "traffic": None, "launches": launches, "avg_ms": per_ms,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured); tensor-core digit products"}
-    if name.startswith("fft_f32") or name == "misc":
-        ach = bytes_ / launches / (per_ms * 1e-3) / 1e9
-        peak = peaks["hbm_gbs"]
-        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "traffic": None, "launches": launches, "avg_ms": per_ms,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    if name.endswith("_dd"):
-        ach = flops / launches / (per_ms * 1e-3) / 1e12
-        peak = FP32_LANES * clk / DD_INSTR_PER_FLOP / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None, "launches": launches, "avg_ms": per_ms,
-                "peak_source": f"double-float flops: 152x128 FP32 lanes x {clk/1e6:.0f} MHz / 7.5 instr per dd-flop"}
+                "frac": ach / peak, "traffic": None, "launches": launches, "avg_ms": per_ms, "peak_source": src}
     if name.endswith("_f64"):
         ach = flops / launches / (per_ms * 1e-3) / 1e12
         peak = FP64_TFLOPS_MEASURED
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None, "launches": launches, "avg_ms": per_ms,
                 "peak_source": "FP64 DFMA loop measured on GB300 (1.19 TFLOP/s)"}
-    # pairmul_f32: FP32 FFMA bound at d >= 16 (intensity d/3 flop/B above the FFMA/HBM ridge)
+    # FP32-pipe or double-float SIMT products: FP32 FFMA bound at d >= 16
     ach = flops / launches / (per_ms * 1e-3) / 1e12
     peak = FP32_LANES * 2 * clk / 1e12
     return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
@@ -123,34 +113,53 @@ def roofline_for(kclass, ms_total, launches, bytes_, flops, peaks, sm_mhz, d=Non
             "peak_source": f"FP32 FFMA: 152x128 lanes x 2 x {clk/1e6:.0f} MHz"}
 
 
-def sources_digest():
-    """sha256 over the kernel sources (csrc/ and the C header), as recorded
-    beside an ncu traffic capture."""
+# Sources each kernel class is built from: a committed DRAM-traffic capture
+# of a class stays valid while these files are unchanged.
+_CLASS_SOURCES = {
+    "fft": ["kernels.cuh", "launchers.cuh", "arith.cuh", "mrc_internal.h"],
+    "tc": ["pair_tc.cu", "ozaki_tc.cu", "tcgen05.cuh", "digits.cuh", "kernels.cuh", "arith.cuh", "mrc_internal.h"],
+    "simt": ["kernels.cuh", "launchers.cuh", "arith.cuh", "mrc_internal.h"],
+}
+
+
+def class_sources(kernel):
+    if kernel.startswith("fft_"):
+        prec = kernel[4:]
+        return _CLASS_SOURCES["fft"] + [f"k_{prec}_fft_lo.cu", f"k_{prec}_fft_hi.cu", f"k_{prec}.cu"]
+    if kernel in ("pairmul_dd", "pairmul_f32"):
+        return _CLASS_SOURCES["tc"]
+    return _CLASS_SOURCES["simt"] + ["k_f64.cu", "k_f32.cu", "k_dd.cu", "misc.cu"]
+
+
+def sources_digest(kernel):
+    """sha256 over the sources of one kernel class, as recorded beside an ncu
+    traffic capture of that class."""
     import hashlib
     h = hashlib.sha256()
-    csrc = os.path.join(HERE, "paper_2605_30379_gb300", "csrc")
-    files = [os.path.join("paper_2605_30379_gb300/csrc", f) for f in sorted(os.listdir(csrc))] + ["include/mrc.h"]
-    for f in files:
-        h.update(f.encode())
-        with open(os.path.join(HERE, f), "rb") as fh:
+    for f in class_sources(kernel):
+        rel = os.path.join("paper_2605_30379_gb300", "csrc", f)
+        h.update(rel.encode())
+        with open(os.path.join(HERE, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def measured_traffic(workload, kclass):
-    """DRAM bytes per launch of kernel class `kclass` (dram__bytes_read.sum +
-    dram__bytes_write.sum, averaged over the class's launches in one step)
-    from the committed ncu capture of this workload -- only while the kernel
-    sources are the ones the capture was taken on; else None."""
+def measured_traffic(workload, kernel):
+    """DRAM bytes per launch of one kernel class (dram__bytes_read.sum +
+    dram__bytes_write.sum) from the committed ncu capture of it, scaled from
+    the captured workload to this one by the units one launch processes --
+    only while that class's sources are the ones the capture was taken on;
+    else (None, None)."""
     path = os.path.join(HERE, "profiles", f"traffic_{workload}.json")
     try:
         with open(path) as fh:
             doc = json.load(fh)
     except (OSError, ValueError):
         return None, None
-    if doc.get("sources_sha256") != sources_digest() or kclass not in doc.get("classes", {}):
+    ent = doc.get("classes", {}).get(kernel)
+    if not ent or ent.get("sources_sha256") != sources_digest(kernel):
         return None, None
-    return doc["classes"][kclass]["dram_bytes_per_launch"], os.path.relpath(path, HERE)
+    return ent["dram_bytes_per_launch"], os.path.relpath(path, HERE)
 
 
 class ClockSampler:
@@ -206,7 +215,7 @@ def make_input(name):
     if kind == "lognormal":
         A, _ = synth.lognormal_model(d, N, seed=0, h=0.05)
     else:
-        q, _ = synth.weibull_model(d, N, seed=0, **extra)
+        q, _ = synth.weibull_model(d, N, seed=0, **{k: v for k, v in extra.items() if k != "sweeps"})
         A = synth.identity_minus(q)
     return A
 
@@ -230,7 +239,8 @@ def job_throughput(units_per_rank, ms_step, world):
 
 def cpu_oracle_sample(A_host, d, budget_s=15.0):
     """Time the FP64 oracle (direct recursion) on a prefix of the same input,
-    doubling the prefix until one call takes >= budget_s / 4 (then one timed call)."""
+    doubling the prefix until one call takes >= budget_s / 4 (then one timed
+    call).  Returns (n, seconds, threads, the oracle's inverse of the prefix)."""
     import oracle
     n = 64
     while True:
@@ -241,9 +251,39 @@ def cpu_oracle_sample(A_host, d, budget_s=15.0):
             break
         n *= 2
     t0 = time.perf_counter()
-    oracle.inverse_left(A_host[:n])
+    psi = oracle.inverse_left(A_host[:n])
     dt = time.perf_counter() - t0
-    return n, dt, oracle.num_threads()
+    return n, dt, oracle.num_threads(), psi
+
+
+def per_output_errors(mrc, A_host, psi_dev, psi_ref, prec):
+    """Errors of the library's outputs against the oracle's on the prefix
+    k < n that the oracle inverted (Proposition 2.3: a prefix of the inverse
+    depends only on the same prefix of A): psi; P = psi * Hbar (mrc_transition)
+    and the first-entrance distribution F_D and reliability S_D = 1 - F_D
+    (mrc_first_entrance, D = the last ceil(d/4) states, alpha_C = e_1), all
+    for the kernel q = e0 - A of the workload."""
+    import oracle
+    import torch
+    n, d = psi_ref.shape[0], psi_ref.shape[1]
+    got = psi_dev[:n].cpu().numpy()
+    num = np.sqrt(((got - psi_ref) ** 2).sum(axis=(1, 2))).sum()
+    den = np.sqrt((psi_ref ** 2).sum(axis=(1, 2))).sum()
+    out = {"prefix": n, "psi": {"max_abs": float(np.abs(got - psi_ref).max()), "e_rel": float(num / den)}}
+    q = -np.ascontiguousarray(A_host[:n])
+    q[0] += np.eye(d)
+    qd = torch.from_numpy(q).cuda()
+    P = mrc.transition(psi_dev[:n].contiguous(), qd, prec=prec).cpu().numpy()
+    out["P"] = {"max_abs": float(np.abs(P - oracle.transition(psi_ref, q)).max())}
+    nD = (d + 3) // 4
+    D = list(range(d - nD, d))
+    alpha = np.zeros(d - nD)
+    alpha[0] = 1.0
+    g, F, S = mrc.first_entrance(qd, D, torch.from_numpy(alpha), prec=prec)
+    _, F_ref, S_ref = oracle.first_entrance(q, D, alpha)
+    out["first_entrance_F"] = {"max_abs": float(np.abs(F.cpu().numpy() - F_ref).max())}
+    out["reliability_S"] = {"max_abs": float(np.abs(S.cpu().numpy() - S_ref).max())}
+    return out
 
 
 def run_mre(args, rank, world, local):
@@ -304,12 +344,6 @@ def run_mre(args, rank, world, local):
     if roof:
         roof["peak_kind"] = peak_kind
         roof["traffic"], roof["traffic_source"] = measured_traffic(args.workload, roof["kernel"])
-    # the same roofline for every kernel class of the untimed breakdown step
-    by_class = {}
-    for kc, (cms, cn, cb, cf) in class_work.items():
-        r_ = roofline_for(kc, cms, cn, cb, cf, peaks, clocks["sm_mhz"] if clocks else None, d=None if batch else d)
-        if r_ and KCLASS[kc] != "misc":
-            by_class[r_["kernel"]] = {k_: r_[k_] for k_ in ("bound", "achieved", "peak", "unit", "frac", "avg_ms")}
     # accuracy: availability against the exact solution (exp(G h) powers)
     import scipy.linalg as sl
     step_m = sl.expm(b["G"] * extra["h"])
@@ -381,10 +415,11 @@ def run_reference(args, rank, world):
     elif kind == "lognormal":
         A, _ = synth.lognormal_model(d, min(N, 8192), seed=0, h=0.05)
     else:
-        q, _ = synth.weibull_model(d, min(N, 8192), seed=0, **WORKLOADS[name][3])
+        q, _ = synth.weibull_model(d, min(N, 8192), seed=0,
+                                   **{k: v for k, v in WORKLOADS[name][3].items() if k != "sweeps"})
         A = synth.identity_minus(q)
     import oracle
-    n, dt, cores = cpu_oracle_sample(A, d, budget_s=8.0)
+    n, dt, cores, _ = cpu_oracle_sample(A, d, budget_s=8.0)
     for _ in range(args.warmup):
         oracle.inverse_left(A[:n])
     times = []
@@ -395,7 +430,7 @@ def run_reference(args, rank, world):
     ms = 1e3 * float(np.mean(times))
     value = n * d * d / (ms * 1e-3)
     sample = f"prefix k < {n} of the {name} workload (the oracle costs d^3 n^2 / 2, so its rate falls as 1/n)"
-    out = {"impl": "reference", "metric": "psi coefficients/s (N*d^2)", "value": value,
+    out = {"impl": "reference", "metric": METRIC, "value": value,
            "unit": "coefficients/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic", "config": {"workload": name, "d": d, "N": N},
@@ -467,12 +502,13 @@ def main():
     stream = torch.cuda.current_stream()
 
     tune = not args.no_autotune
+    sweeps = WORKLOADS[args.workload][3].get("sweeps", 1)
 
     def step(prec=args.prec):
         if batch:
-            mrc.inverse_batched(As, prec=prec, sweeps=1, outs=psis, autotune=tune)
+            mrc.inverse_batched(As, prec=prec, sweeps=sweeps, outs=psis, autotune=tune)
         else:
-            mrc.inverse(As[0], prec=prec, sweeps=1, out=psis[0], autotune=tune)
+            mrc.inverse(As[0], prec=prec, sweeps=sweeps, out=psis[0], autotune=tune)
 
     def prof(kclass, fn):
         lib.mrc_profile_begin(kclass)
@@ -536,6 +572,13 @@ def main():
         torch.cuda.synchronize()
         ms64 = max_over_ranks(e0.elapsed_time(e1) / args.fp64_steps)
         fp64 = {"value": job_throughput(coeffs, ms64, world), "ms_per_step": ms64, "steps": args.fp64_steps}
+        # the FP64 path's own residuals (double-float evaluation), beside the mixed path's below
+        r64 = {"res_max_abs": 0.0, "res_left_l1": 0.0, "res_right_l1": 0.0}
+        for a, p_ in zip(As, psis):
+            _, _, r = mrc.residual(a, p_, sides=3, prec="mixed", want_rho=False)
+            r64 = {k: max(r64[k], r[k]) for k in r64}
+        fp64["accuracy"] = {"max_abs_rho_L": r64["res_max_abs"], "rho_L_l1": r64["res_left_l1"],
+                            "rho_R_l1": r64["res_right_l1"]}
         step()  # leave the mixed result in psi for the accuracy check
         torch.cuda.synchronize()
 
@@ -559,7 +602,7 @@ def main():
                 for p_, q_ in zip(psi_pins, psis):
                     p_.copy_(q_, non_blocking=True)
             else:  # mrc_inverse_host: uploads in row ranges overlap the Newton levels
-                mrc.inverse_host(A_pins[0], prec=args.prec, sweeps=1, out=psi_pins[0], autotune=tune)
+                mrc.inverse_host(A_pins[0], prec=args.prec, sweeps=sweeps, out=psi_pins[0], autotune=tune)
         e1.record(stream)
         torch.cuda.synchronize()
         ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps)
@@ -578,26 +621,29 @@ def main():
             by_class[r_["kernel"]] = {k_: r_[k_] for k_ in ("bound", "achieved", "peak", "unit", "frac", "avg_ms")}
 
     cpu = None
+    outputs = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dc = A_host_np.shape[1]
-        n, dt, cores = cpu_oracle_sample(A_host_np, dc)
+        n, dt, cores, psi_ref = cpu_oracle_sample(A_host_np, dc)
         cpu = {"value": n * dc * dc / dt, "unit": "coefficients/s", "cores": cores, "kind": "oracle",
                "sample": f"one call on the prefix k < {n} of the same workload, {dt:.1f} s "
                          f"(direct recursion, cost d^3 n^2 / 2: its rate falls as 1/n)"}
+        if not batch:
+            outputs = per_output_errors(mrc, A_host_np, psis[0], psi_ref, args.prec)
 
     if rank == 0:
         out = {
-            "metric": "psi coefficients/s (N*d^2), mixed precision at <= 1e-10 residual",
+            "metric": METRIC,
             "value": value, "unit": "coefficients/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+dd" if args.prec == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "autotune": tune, "d": d if not batch else "3..48",
-                       "N": N if not batch else "round(2^U[10,16])", "models": len(As), "prec": args.prec, "sweeps": 1,
+                       "N": N if not batch else "round(2^U[10,16])", "models": len(As), "prec": args.prec, "sweeps": sweeps,
                        "l2": (f"inputs ({coeffs * 8 / 1e9:.1f} GB) larger than L2; no flush" if coeffs * 8 > 2e8
                               else "inputs smaller than L2: latency-bound, no flush"),
                        "parallelism": "replicas" if world > 1 else "single"},
             "accuracy": {"max_abs_rho_L": rep["res_max_abs"], "rho_L_l1": rep["res_left_l1"],
-                         "rho_R_l1": rep["res_right_l1"]},
+                         "rho_R_l1": rep["res_right_l1"], "vs_oracle": outputs},
             "fp64_path": fp64,
             "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
             "gpu_launches": int(launches),

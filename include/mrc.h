@@ -47,7 +47,7 @@ typedef enum {
     MRC_ERR_NO_MEMORY = 3,     /* workspace above the context cap or cudaMalloc failed */
     MRC_ERR_CUDA = 4,          /* a CUDA runtime call or kernel launch failed */
     MRC_ERR_NOT_CONVERGED = 5, /* refinement left max|rho| above target_residual */
-    MRC_ERR_TIMEOUT = 6,       /* reserved: a bounded device wait gave up */
+    MRC_ERR_TIMEOUT = 6,       /* a bounded device wait gave up (the tensor-core product's mbarrier waits) */
     MRC_ERR_UNIMPLEMENTED = 7
 } mrc_status;
 
@@ -145,7 +145,6 @@ mrc_status mrc_mre_solve(mrc_ctx *ctx, int d, int c, int64_t N, const double *Q,
                          double *K, const mrc_options *opt, void *stream);
 
 /*
- * mrc_inverse_host/*
  * mrc_inverse_host -- the same inverse as mrc_inverse (same kernels, same
  * results) for a sequence that lives in host memory, with the transfers in
  * the call: A is uploaded in the row ranges the Newton doubling consumes
@@ -258,29 +257,48 @@ mrc_status mrc_renewal_visits(mrc_ctx *ctx, int d, int64_t N, const double *psi,
                               const int *B, int nB, double *out, void *stream);
 
 /*
- * mrc_inverse_noalloc -- the FP64 inverse of mrc_inverse (same kernels, same
- * result) for callers that cannot let a library allocate device memory: a
- * process whose device memory is already owned by another allocator's pool,
- * code that forbids dynamic allocation after initialisation, or a plugin host
- * that only hands out fixed buffers.  The paper has no counterpart; this is
- * an interface variant only.
+ * mrc_inverse_noalloc -- the FP64 inverse of mrc_inverse for callers that
+ * cannot let a library allocate device memory: a process whose device memory
+ * is already owned by another allocator's pool, code that forbids dynamic
+ * allocation after initialisation, or a plugin host that only hands out
+ * fixed buffers.  The paper has no counterpart; this is an interface variant
+ * only.  It runs mrc_inverse's Newton schedule with the same FFT kernels and
+ * the default FP64 product kernel (never an autotuned one), so its results
+ * agree with mrc_inverse's to rounding.
  *   d, N, A, psi, stream : as mrc_inverse with prec = MRC_FP64.
- * Scratch: one fixed 64 MiB device array inside the library (held on every
- * GPU that loads the library until the process exits).  The call uses
+ * Scratch: one fixed 64 MiB device array inside the library.  The call uses
  * 256 B + 512 KiB (twiddles) + 16 d^2 + 4 * 16 d^2 * M bytes of it, M being
  * the largest Newton level (< N); N must be <= 2^14.  Larger requests return
  * MRC_ERR_NO_MEMORY at once, with the limit printed to stderr.
  * No cudaMalloc/cudaFree or allocating library routine is called.
- * The first call on a device resolves the array's device address
- * (cudaGetSymbolAddress) and fills the twiddle table, synchronously: make
- * that first call before any stream capture.  Every call then clears the
- * status word, enqueues the work on `stream`, synchronises `stream` and
- * returns MRC_OK or MRC_ERR_SINGULAR_A0.  All calls share the array and it
- * keeps the last call's contents: calls whose work overlaps on the GPU (two
- * host threads, or two streams) race on it and must be serialised by the
- * caller.
+ * Initialisation: under CUDA's default lazy module loading, the array (and
+ * the library's kernels) are mapped on a device only when first used there.
+ * The first call on each device is therefore the initialisation step: it
+ * resolves the array's device address (cudaGetSymbolAddress), which maps it,
+ * and fills the twiddle table, synchronously.  Make that first call before
+ * another allocator reserves the device's memory and before any stream
+ * capture (or set CUDA_MODULE_LOADING=EAGER, which maps the array when the
+ * library is loaded).  Once mapped, the array stays on that device until the
+ * process exits.
+ * Every call then clears the status word, enqueues the work on `stream`,
+ * synchronises `stream` and returns MRC_OK or MRC_ERR_SINGULAR_A0.  All calls
+ * share the array and it keeps the last call's contents: calls whose work
+ * overlaps on the GPU (two host threads, or two streams) race on it and must
+ * be serialised by the caller.
  */
 mrc_status mrc_inverse_noalloc(int d, int64_t N, const double *A, double *psi, void *stream);
+
+/*
+ * mrc_selftest_timeout -- failure-detection self-test (no counterpart in the
+ * paper).  Enqueues on `stream` one thread that runs the bounded mbarrier
+ * wait of the tensor-core product kernels on a barrier nothing arrives on;
+ * after `spins` rounds of try_wait (each suspending for at most about 1 us)
+ * it gives up and writes MRC_ERR_TIMEOUT to the context's status word, which
+ * the next mrc_sync_status (or call with a report) returns and clears.
+ * Nothing asynchronous is in flight in that kernel, so the context stays
+ * usable afterwards.  1 <= spins <= 2^20, else MRC_ERR_INVALID_ARG.
+ */
+mrc_status mrc_selftest_timeout(mrc_ctx *ctx, int spins, void *stream);
 
 /*
  * Instrumentation (no counterpart in the paper; used to report the roofline

@@ -11,7 +11,8 @@ Every function follows a definition in Kordalis & Trevezas (arXiv 2605.30379):
                         (Theorem 2.2; Eq. (renewal-sequence) when A = e0 - q)
 * ``inverse_right``  -- Eq. (inverse-recursion)
 * ``convolve``       -- Eq. (convolution)
-* ``residuals``      -- rho_L, rho_R of Proposition 2.6
+* ``residuals``      -- rho_L, rho_R of Proposition 2.6 (and one entry at one
+                        time index: ``residual_left_entry`` / ``_right_entry``)
 * ``transition``     -- P = psi * Hbar, Eq. (transition-discrete)
 * ``first_entrance`` -- Eqs. (first-entrance-mass), (first-entrance-cdf)
 * ``occupation``     -- A_B(k) = alpha P(k) 1_{E,B} (Table 2; availability)
@@ -66,6 +67,10 @@ def _load():
             lib.orc_inverse_right.argtypes = [c_int, i64, p, p]
             lib.orc_residuals.argtypes = [c_int, i64, p, p, p, p]
             lib.orc_residual_left_at.argtypes = [c_int, i64, p, p, p]
+            lib.orc_residual_left_entry.argtypes = [c_int, i64, c_int, c_int, p, p]
+            lib.orc_residual_left_entry.restype = c_dbl
+            lib.orc_residual_right_entry.argtypes = [c_int, i64, c_int, c_int, p, p]
+            lib.orc_residual_right_entry.restype = c_dbl
             lib.orc_hbar.argtypes = [c_int, i64, p, p]
             lib.orc_transition.argtypes = [c_int, i64, p, p, p]
             lib.orc_first_entrance.argtypes = [c_int, i64, p, p, p, p, p, p]
@@ -157,6 +162,30 @@ def residual_left_at(A, psi, k):
     out = np.empty((d, d))
     _load().orc_residual_left_at(d, k, _ptr(A), _ptr(psi), _ptr(out))
     return out
+
+
+def _prefix_view(X, k):
+    """X[: k + 1] as a C-contiguous float64 array, without copying when X
+    already is one (the sampled residuals of very long runs)."""
+    X = X[: k + 1]
+    if X.dtype == np.float64 and X.flags["C_CONTIGUOUS"]:
+        return X
+    return _f64(X)
+
+
+def residual_left_entry(A, psi, k, i, j):
+    """rho_L(k)_{ij} = delta(k) delta_{ij} - sum_{l<=k} (A(l) psi(k-l))_{ij}
+    (Proposition 2.6) for one entry and one time index (cost O(k d))."""
+    A, psi = _prefix_view(A, k), _prefix_view(psi, k)
+    d = A.shape[1]
+    return float(_load().orc_residual_left_entry(d, k, i, j, _ptr(A), _ptr(psi)))
+
+
+def residual_right_entry(A, psi, k, i, j):
+    """rho_R(k)_{ij} = delta(k) delta_{ij} - sum_{l<=k} (psi(l) A(k-l))_{ij}."""
+    A, psi = _prefix_view(A, k), _prefix_view(psi, k)
+    d = A.shape[1]
+    return float(_load().orc_residual_right_entry(d, k, i, j, _ptr(A), _ptr(psi)))
 
 
 def hbar(q):

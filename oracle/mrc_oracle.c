@@ -199,6 +199,29 @@ void orc_residual_left_at(int d, int64_t k, const double *A, const double *psi, 
 }
 
 /*
+ * One entry of each residual at one time index k (Proposition 2.6):
+ *   rho_L(k)_{ij} = delta(k) delta_{ij} - sum_{l=0..k} sum_u A(l)_{iu} psi(k-l)_{uj},
+ *   rho_R(k)_{ij} = delta(k) delta_{ij} - sum_{l=0..k} sum_u psi(l)_{iu} A(k-l)_{uj}.
+ * Cost O(k d) each: checks sampled outputs of runs far too long for the full
+ * residual.
+ */
+double orc_residual_left_entry(int d, int64_t k, int i, int j, const double *A, const double *psi)
+{
+    double s = (k == 0 && i == j) ? 1.0 : 0.0;
+    for (int64_t l = 0; l <= k; ++l)
+        for (int u = 0; u < d; ++u) s -= A[IDX(l, i, u, d, d)] * psi[IDX(k - l, u, j, d, d)];
+    return s;
+}
+
+double orc_residual_right_entry(int d, int64_t k, int i, int j, const double *A, const double *psi)
+{
+    double s = (k == 0 && i == j) ? 1.0 : 0.0;
+    for (int64_t l = 0; l <= k; ++l)
+        for (int u = 0; u < d; ++u) s -= psi[IDX(l, i, u, d, d)] * A[IDX(k - l, u, j, d, d)];
+    return s;
+}
+
+/*
  * Survival diagonal of the discrete kernel (Section 4.1):
  *   Hbar(k) = diag( 1 - sum_j sum_{l=1..k} q_ij(l) ),  stored as hbar[k*d + i].
  */

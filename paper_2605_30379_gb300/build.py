@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmrc.so")
-SOURCES = ["api.cu", "misc.cu", "prof.cu", "noalloc.cu", "ozaki.cu", "ozaki_tc.cu", "tf32x3.cu", "k_f64.cu", "k_f32.cu", "k_dd.cu",
+SOURCES = ["api.cu", "misc.cu", "prof.cu", "noalloc.cu", "ozaki_tc.cu", "pair_tc.cu", "k_f64.cu", "k_f32.cu", "k_dd.cu",
            "k_f64_fft_lo.cu", "k_f64_fft_hi.cu", "k_f32_fft_lo.cu", "k_f32_fft_hi.cu", "k_dd_fft_lo.cu",
            "k_dd_fft_hi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -58,6 +58,9 @@ struct mrc_ctx {
     bool autotune = false;   // the current call asked for it
     bool capturing = false;  // a batch graph is being captured: no timing
     bool tune_dirty = false;
+    // status word of the call being enqueued: d_status, or a batched model's
+    // own word (bounded device waits write MRC_ERR_TIMEOUT there)
+    int *cur_status = nullptr;
 };
 
 void mrc_prof_set_capturing(bool on);
@@ -103,21 +106,6 @@ struct Arena {
     }
 };
 
-// Row ranges of A still being uploaded (mrc_inverse_host): ranges
-// [end[i-1], end[i]) complete at ev[i]; wait(s, rows) makes stream s wait
-// until rows [0, rows) are on the device.  n == 0: everything is there.
-struct RowWait {
-    int n = 0;
-    int64_t end[32] = {};
-    cudaEvent_t ev[32] = {};
-    cudaError_t wait(cudaStream_t s, int64_t rows) const
-    {
-        for (int i = 0; i < n; ++i)
-            if (end[i] >= rows) return cudaStreamWaitEvent(s, ev[i], 0);
-        return n ? cudaStreamWaitEvent(s, ev[n - 1], 0) : cudaSuccess;
-    }
-};
-
 #define CK(call)                                          \
     do {                                                  \
         cudaError_t e_ = (call);                          \
@@ -159,18 +147,8 @@ mrc_status ensure_ws(mrc_ctx *c, size_t need)
 
 // ---------------------------------------------------------------------------
 // Workspace plans
-int64_t base_size(int d, int64_t N)
-{
-    int64_t m0 = d <= 8 ? 32 : (d <= 32 ? 8 : 2);
-    return std::min<int64_t>(m0, N);
-}
-
-int64_t newton_maxM(int d, int64_t N)
-{
-    int64_t m0 = base_size(d, N), M = 0;
-    for (int64_t m = m0; m < N; m <<= 1) M = m;
-    return M;
-}
+int64_t base_size(int d, int64_t N) { return mrc_base_size(d, N); }
+int64_t newton_maxM(int d, int64_t N) { return mrc_newton_maxM(d, N); }
 
 size_t ws_newton(int d, int64_t N, int prec)
 {
@@ -215,21 +193,28 @@ size_t ws_inverse(int d, int64_t N, int prec)
     return gj + ahat + psi32 + std::max(newton, refine);
 }
 
-// Square products on the tensor cores: double-float with 32 <= d <= 64 as
-// exact digit products (ozaki.cu; MRC_DD_PRODUCT=simt selects the FP32-pipe
-// kernel).  Opt-in: MRC_F32_PRODUCT=tf32x3 (Newton-level FP32 products as
-// three TF32 products, tf32x3.cu) or =tensor (every FP32 product as digit
-// products).
-bool env_is_simt(const char *name)
+// Product kernel choices: 0..2 the FP32-pipe tile configurations 16/32/64
+// (pairmul_cfg), 3 the tensor-core digit kernel: for square 32 <= d <= 64
+// the pipelined one (pair_tc.cu; double-float or FP32), for double-float
+// 64 < d <= 512 the tiled one (ozaki_tc.cu).
+bool tensor_choice_exists(int prec, int r, int m, int c)
 {
-    const char *v = getenv(name);
-    return v && strcmp(v, "simt") == 0;
+    if (prec == PREC_DD) return mrc_tc_supported(r, m, c);
+    return prec == PREC_F32 && mrc_tcp_supported(r, m, c);
 }
 
-cudaError_t launch_choice(int prec, int choice, const void *zx, const void *zy, void *zc, int64_t M, int r, int m,
-                          int c, const void *tw, cudaStream_t st)
+cudaError_t launch_tensor(mrc_ctx *cx, int prec, const void *zx, const void *zy, void *zc, int64_t M, int d,
+                          const void *tw, cudaStream_t st)
 {
-    if (choice == 3) return mrc_pairmul_dd_tc(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
+    if (prec == PREC_F32) return mrc_pairmul_f32_tcp(zx, zy, zc, M, d, tw, MRC_TW_LOG, cx->cur_status, st);
+    if (d <= 64) return mrc_pairmul_dd_tcp(zx, zy, zc, M, d, tw, MRC_TW_LOG, cx->cur_status, st);
+    return mrc_pairmul_dd_tc(zx, zy, zc, M, d, tw, MRC_TW_LOG, cx->cur_status, st);
+}
+
+cudaError_t launch_choice(mrc_ctx *cx, int prec, int choice, const void *zx, const void *zy, void *zc, int64_t M,
+                          int r, int m, int c, const void *tw, cudaStream_t st)
+{
+    if (choice == 3) return launch_tensor(cx, prec, zx, zy, zc, M, r, tw, st);
     return OPS[prec].pairmul_cfg(zx, zy, zc, M, r, m, c, choice, tw, MRC_TW_LOG, st);
 }
 
@@ -256,14 +241,14 @@ int tuned_choice(mrc_ctx *cx, int prec, const void *zx, const void *zy, void *zc
     if (it != cx->tune.end()) return it->second;
     if (cx->capturing) return -1;
     int cands[4] = {0, 1, 2, 3};
-    const int nc = (prec == PREC_DD && mrc_tc_supported(r, m, c)) ? 4 : 3;
+    const int nc = tensor_choice_exists(prec, r, m, c) ? 4 : 3;
     float best = 1e30f;
     int pick = -1;
     for (int k = 0; k < nc; ++k) {
-        if (launch_choice(prec, cands[k], zx, zy, zc, M, r, m, c, tw, st) != cudaSuccess) continue;
+        if (launch_choice(cx, prec, cands[k], zx, zy, zc, M, r, m, c, tw, st) != cudaSuccess) continue;
         cudaEventRecord(cx->ev0, st);
-        launch_choice(prec, cands[k], zx, zy, zc, M, r, m, c, tw, st);
-        launch_choice(prec, cands[k], zx, zy, zc, M, r, m, c, tw, st);
+        launch_choice(cx, prec, cands[k], zx, zy, zc, M, r, m, c, tw, st);
+        launch_choice(cx, prec, cands[k], zx, zy, zc, M, r, m, c, tw, st);
         cudaEventRecord(cx->ev1, st);
         if (cudaEventSynchronize(cx->ev1) != cudaSuccess) continue;
         float ms = 0.f;
@@ -278,35 +263,18 @@ int tuned_choice(mrc_ctx *cx, int prec, const void *zx, const void *zy, void *zc
     return pick;
 }
 
+// The per-frequency product of one precision: the autotuned choice when the
+// call asked for tuning, else the tensor-core digit kernels for square
+// double-float products with 32 <= d <= 512 and square FP32 products with
+// 32 <= d <= 64 on transforms of at least 256 points (fewer pairs than SMs
+// below that), the FP32-pipe tiles elsewhere.
 cudaError_t pairmul_any(mrc_ctx *cx, int prec, const void *zx, const void *zy, void *zc, int64_t M, int r, int m,
-                        int c, const void *tw, cudaStream_t st, bool newton_level = false)
+                        int c, const void *tw, cudaStream_t st)
 {
-    // MRC_F32_PRODUCT=tf32x3 runs the Newton-level FP32 products as three TF32
-    // tensor-core products.  Off by default: its psi_0 is a few times less
-    // accurate than with FP32 dot products, and after one sweep e_rel reached
-    // 1.4e-10 at d = 16 (gate 1e-10); the correction psi * rho always keeps
-    // FP32 dot products (with TF32x3 there max|rho_L| stayed near 1e-11).
-    const char *fv = getenv("MRC_F32_PRODUCT");
-    if (prec == PREC_F32 && newton_level && mrc_tf32x3_supported(r, m, c) && fv && strcmp(fv, "tf32x3") == 0)
-        return mrc_pairmul_f32_tf32x3(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
-    if (prec == PREC_F32 && mrc_tc_supported(r, m, c) && fv && strcmp(fv, "tc") == 0)
-        return mrc_pairmul_f32_tc(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
-    // FP32 products stay on the FP32 pipes unless MRC_F32_PRODUCT=tensor: at
-    // d <= 64 the per-entry digit work outweighs the tensor-core savings
-    // (d = 64, N = 2^18: 118 ms on the tensor cores against 54.5 ms)
-    if (prec == PREC_F32 && mrc_ozaki_supported(r, m, c) && fv && strcmp(fv, "tensor") == 0)
-        return mrc_pairmul_f32_ozaki(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
-    const bool dd_env = prec == PREC_DD && getenv("MRC_DD_PRODUCT");
-    if (!dd_env) {
-        const int ch = tuned_choice(cx, prec, zx, zy, zc, M, r, m, c, tw, st);
-        if (ch >= 0) return launch_choice(prec, ch, zx, zy, zc, M, r, m, c, tw, st);
-    }
-    if (prec == PREC_DD && mrc_tc_supported(r, m, c) && !env_is_simt("MRC_DD_PRODUCT")) {
-        const char *dv = getenv("MRC_DD_PRODUCT");
-        if (dv && strcmp(dv, "mma") == 0 && mrc_ozaki_supported(r, m, c))
-            return mrc_pairmul_dd_ozaki(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
-        return mrc_pairmul_dd_tc(zx, zy, zc, M, r, tw, MRC_TW_LOG, st);
-    }
+    const int ch = tuned_choice(cx, prec, zx, zy, zc, M, r, m, c, tw, st);
+    if (ch >= 0) return launch_choice(cx, prec, ch, zx, zy, zc, M, r, m, c, tw, st);
+    if (tensor_choice_exists(prec, r, m, c) && (prec == PREC_DD || M >= 256))
+        return launch_tensor(cx, prec, zx, zy, zc, M, r, tw, st);
     return OPS[prec].pairmul(zx, zy, zc, M, r, m, c, tw, MRC_TW_LOG, st);
 }
 
@@ -352,12 +320,15 @@ mrc_status conv_product(mrc_ctx *c, Arena &ar, int prec, const double *X, int64_
     return MRC_OK;
 }
 
-// Newton doubling levels in working precision `prec`: psi rows [0, m0) are
-// already correct; each level m -> min(2m, N) follows Eq. (newton) with the
-// middle product (L = 2m): E = A*B (cyclic), R = -E[m, 2m), B[m, 2m) = (B*R)[0, m).
-// With A32 / psi32 (FP32 levels of the mixed path) the levels read A from
-// its binary32 copy, converted here row range by row range as the levels
-// reach it, and read and write psi in binary32 (rows [0, m0) already there).
+// The level product through the context: autotuned or built-in choice.
+cudaError_t level_product(void *user, int prec, const void *zx, const void *zy, void *zc, int64_t M, int d,
+                          const void *tw, int, cudaStream_t st)
+{
+    return pairmul_any((mrc_ctx *)user, prec, zx, zy, zc, M, d, d, d, tw, st);
+}
+
+// Newton doubling levels in working precision `prec` over buffers taken
+// from the context workspace (the schedule itself is mrc_newton_levels).
 mrc_status newton_levels(mrc_ctx *c, Arena &ar, int prec, int d, int64_t N, const double *A, double *psi,
                          int64_t m0, int *levels, cudaStream_t st, const RowWait *rw = nullptr,
                          float *A32 = nullptr, float *psi32 = nullptr)
@@ -365,42 +336,15 @@ mrc_status newton_levels(mrc_ctx *c, Arena &ar, int prec, int d, int64_t N, cons
     const PrecOps &op = OPS[prec];
     const int E = d * d;
     const int64_t Mmax = newton_maxM(d, N);
+    if (levels) *levels = 0;
     if (Mmax == 0) return MRC_OK;
-    void *b0 = ar.take((size_t)Mmax * E * op.cxb);
-    void *b1 = ar.take((size_t)Mmax * E * op.cxb);
-    void *b2 = ar.take((size_t)Mmax * E * op.cxb);
-    void *bt = ar.take(mrc_fft_scratch_elems(Mmax, E) * op.cxb);
-    const void *tw = c->tw[prec];
-    const bool f32 = A32 && psi32;
-    int64_t conv = 0;  // rows of A32 converted so far
-    int lv = 0;
-    for (int64_t m = m0; m < N; m <<= 1, ++lv) {
-        const int64_t M = m, m2 = std::min<int64_t>(2 * m, N);
-        if (rw) CK(rw->wait(st, m2));  // this level reads A[0, 2m)
-        if (f32 && conv < m2) {
-            CK(mrc_f64_to_f32(A + conv * E, A32 + conv * E, (m2 - conv) * E, st));
-            conv = m2;
-        }
-        FftSrc sA{f32 ? SRC_REAL32 : SRC_REAL64, f32 ? (const void *)A32 : A, 0, m2, E, 0};
-        FftSrc sB{f32 ? SRC_REAL32 : SRC_REAL64, f32 ? (const void *)psi32 : psi, 0, m, E, 0};
-        FftDst to0{DST_CPLX, b0, E, 0, 0, 0, 1.0, 0};
-        FftDst to1{DST_CPLX, b1, E, 0, 0, 0, 1.0, 0};
-        CK(op.fft(sA, to0, M, E, -1, bt, tw, MRC_TW_LOG, st));               // A-hat
-        CK(op.fft(sB, to1, M, E, -1, bt, tw, MRC_TW_LOG, st));               // B-hat
-        CK(pairmul_any(c, prec, b0, b1, b2, M, d, d, d, tw, st, true));     // (A B)-hat
-        FftSrc s2{SRC_CPLX, b2, 0, M, E, 0};
-        FftDst t0s{DST_CPLX, b0, E, 0, 0, 0, 1.0 / (double)M, 0};
-        CK(op.fft(s2, t0s, M, E, +1, bt, tw, MRC_TW_LOG, st));               // A*B, packed time
-        FftSrc sR{SRC_CPLX, b0, M / 2, M / 2, E, 1};                          // R = -(A*B)[m, 2m)
-        FftDst to2{DST_CPLX, b2, E, 0, 0, 0, 1.0, 0};
-        CK(op.fft(sR, to2, M, E, -1, bt, tw, MRC_TW_LOG, st));               // R-hat
-        CK(pairmul_any(c, prec, b1, b2, b0, M, d, d, d, tw, st, true));     // (B R)-hat
-        FftSrc s0{SRC_CPLX, b0, 0, M, E, 0};
-        FftDst toP{f32 ? DST_REAL32 : DST_REAL64, f32 ? (void *)psi32 : psi, E, 0, m2 - m, m, 1.0 / (double)M, 0};
-        CK(op.fft(s0, toP, M, E, +1, bt, tw, MRC_TW_LOG, st));               // B[m, m2)
-    }
-    if (levels) *levels = lv;
-    return MRC_OK;
+    NewtonBufs b;
+    b.b0 = ar.take((size_t)Mmax * E * op.cxb);
+    b.b1 = ar.take((size_t)Mmax * E * op.cxb);
+    b.b2 = ar.take((size_t)Mmax * E * op.cxb);
+    b.bt = ar.take(mrc_fft_scratch_elems(Mmax, E) * op.cxb);
+    return (mrc_status)mrc_newton_levels(prec, d, N, A, psi, m0, b, c->tw[prec], MRC_TW_LOG, level_product, c, st,
+                                         rw, A32, psi32, levels);
 }
 
 bool valid_dN(int d, int64_t N) { return d >= 1 && d <= 512 && N >= 1 && N <= ((int64_t)1 << 20); }
@@ -418,6 +362,12 @@ mrc_status inverse_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A
                         const RowWait *rw = nullptr)
 {
     const size_t E = (size_t)d * d;
+    struct StatusScope {  // bounded waits of this model report to its own word
+        mrc_ctx *c;
+        int *old;
+        ~StatusScope() { c->cur_status = old; }
+    } sscope{c, c->cur_status};
+    c->cur_status = status ? status : c->d_status;
     double *gjw = (double *)ar.take(sizeof(double) * 2 * E);
     void *ahat = nullptr, *ascr = nullptr;
     cudaStream_t sn = st;  // Newton levels
@@ -592,6 +542,60 @@ void tune_save(mrc_ctx *cx)
 } // namespace
 
 // ===========================================================================
+// The Newton schedule shared by the inverse entry points.
+int64_t mrc_base_size(int d, int64_t N)
+{
+    int64_t m0 = d <= 8 ? 32 : (d <= 32 ? 8 : 2);
+    return std::min<int64_t>(m0, N);
+}
+
+int64_t mrc_newton_maxM(int d, int64_t N)
+{
+    int64_t m0 = mrc_base_size(d, N), M = 0;
+    for (int64_t m = m0; m < N; m <<= 1) M = m;
+    return M;
+}
+
+// Each level m -> min(2m, N) follows Eq. (newton) with the middle product
+// (L = 2m): E = A*B (cyclic), R = -E[m, 2m), B[m, 2m) = (B*R)[0, m).
+int mrc_newton_levels(int prec, int d, int64_t N, const double *A, double *psi, int64_t m0, const NewtonBufs &b,
+                      const void *tw, int tw_log, mrc_level_product_fn product, void *user, cudaStream_t st,
+                      const RowWait *rw, float *A32, float *psi32, int *levels)
+{
+    const PrecOps &op = OPS[prec];
+    const int E = d * d;
+    const bool f32 = A32 && psi32;
+    int64_t conv = 0;  // rows of A32 converted so far
+    int lv = 0;
+    for (int64_t m = m0; m < N; m <<= 1, ++lv) {
+        const int64_t M = m, m2 = std::min<int64_t>(2 * m, N);
+        if (rw) CK(rw->wait(st, m2));  // this level reads A[0, 2m)
+        if (f32 && conv < m2) {
+            CK(mrc_f64_to_f32(A + conv * E, A32 + conv * E, (m2 - conv) * E, st));
+            conv = m2;
+        }
+        FftSrc sA{f32 ? SRC_REAL32 : SRC_REAL64, f32 ? (const void *)A32 : A, 0, m2, E, 0};
+        FftSrc sB{f32 ? SRC_REAL32 : SRC_REAL64, f32 ? (const void *)psi32 : psi, 0, m, E, 0};
+        FftDst to0{DST_CPLX, b.b0, E, 0, 0, 0, 1.0, 0};
+        FftDst to1{DST_CPLX, b.b1, E, 0, 0, 0, 1.0, 0};
+        CK(op.fft(sA, to0, M, E, -1, b.bt, tw, tw_log, st));                  // A-hat
+        CK(op.fft(sB, to1, M, E, -1, b.bt, tw, tw_log, st));                  // B-hat
+        CK(product(user, prec, b.b0, b.b1, b.b2, M, d, tw, tw_log, st));      // (A B)-hat
+        FftSrc s2{SRC_CPLX, b.b2, 0, M, E, 0};
+        FftDst t0s{DST_CPLX, b.b0, E, 0, 0, 0, 1.0 / (double)M, 0};
+        CK(op.fft(s2, t0s, M, E, +1, b.bt, tw, tw_log, st));                  // A*B, packed time
+        FftSrc sR{SRC_CPLX, b.b0, M / 2, M / 2, E, 1};                         // R = -(A*B)[m, 2m)
+        FftDst to2{DST_CPLX, b.b2, E, 0, 0, 0, 1.0, 0};
+        CK(op.fft(sR, to2, M, E, -1, b.bt, tw, tw_log, st));                  // R-hat
+        CK(product(user, prec, b.b1, b.b2, b.b0, M, d, tw, tw_log, st));      // (B R)-hat
+        FftSrc s0{SRC_CPLX, b.b0, 0, M, E, 0};
+        FftDst toP{f32 ? DST_REAL32 : DST_REAL64, f32 ? (void *)psi32 : psi, E, 0, m2 - m, m, 1.0 / (double)M, 0};
+        CK(op.fft(s0, toP, M, E, +1, b.bt, tw, tw_log, st));                  // B[m, m2)
+    }
+    if (levels) *levels = lv;
+    return MRC_OK;
+}
+
 // the single-model mixed inverse's two internal streams (created on first use)
 static mrc_status ensure_split_streams(mrc_ctx *c)
 {
@@ -633,9 +637,7 @@ mrc_status mrc_create(mrc_ctx **out, int device, size_t max_workspace_bytes)
     if (cudaSetDevice(device) != cudaSuccess) return MRC_ERR_CUDA;
     for (int p = 0; p < 3; ++p)
         if (OPS[p].init() != cudaSuccess) return MRC_ERR_CUDA;
-    if (mrc_ozaki_init() != cudaSuccess) return MRC_ERR_CUDA;
-    if (mrc_tf32x3_init() != cudaSuccess) return MRC_ERR_CUDA;
-    if (mrc_tc_init() != cudaSuccess) return MRC_ERR_CUDA;
+    if (mrc_tc_init() != cudaSuccess || mrc_tcp_init() != cudaSuccess) return MRC_ERR_CUDA;
     mrc_ctx *c = new mrc_ctx();
     c->device = device;
     c->cap = max_workspace_bytes;
@@ -644,7 +646,7 @@ mrc_status mrc_create(mrc_ctx **out, int device, size_t max_workspace_bytes)
         return MRC_ERR_NO_MEMORY;
     }
     cudaMemset(c->d_status, 0, sizeof(int));
-    mrc_set_status_word(c->d_status);
+    c->cur_status = c->d_status;
     tune_load(c);
     cudaEventCreate(&c->ev0);
     cudaEventCreate(&c->ev1);
@@ -660,7 +662,6 @@ mrc_status mrc_destroy(mrc_ctx *c)
     tune_save(c);
     cudaFree(c->ws);
     for (int p = 0; p < 3; ++p) cudaFree(c->tw[p]);
-    if (mrc_status_word() == c->d_status) mrc_set_status_word(nullptr);
     cudaFree(c->d_status);
     cudaFree(c->d_acc);
     cudaEventDestroy(c->ev0);
@@ -1120,6 +1121,14 @@ mrc_status mrc_mre_solve(mrc_ctx *c, int d, int cc, int64_t N, const double *Q, 
         rhs = R;
     }
     return conv_product(c, ar, p, psi, N, rhs, N, d, d, cc, N, K, 1.0, 0, 0, false, st);
+}
+
+mrc_status mrc_selftest_timeout(mrc_ctx *c, int spins, void *stream)
+{
+    if (!c || spins < 1 || spins > (1 << 20)) return MRC_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    CK(mrc_tc_wait_selftest(c->d_status, spins, (cudaStream_t)stream));
+    return MRC_OK;
 }
 
 mrc_status mrc_renewal_visits(mrc_ctx *c, int d, int64_t N, const double *psi, const double *alpha, const int *B,

@@ -133,16 +133,8 @@ __device__ __forceinline__ void dft_r(cx<T> *v)
 // stage (before the store): the adds and dot products of the earlier stages
 // accept unnormalised operands, and the low parts stay within a few ulps of
 // the high parts (error a small multiple of 2^-48 |x|).  d = 64, N = 2^18:
-// double-float FFT 51.0 -> 49.6 ms, max |rho_L| 7.51e-14 either way.
-// 1 normalises after every stage.
-#ifndef MRC_DD_STAGE_NORM
-#define MRC_DD_STAGE_NORM 0
-#endif
-// First-stage global loads issued before the CTA fills its twiddle tables,
-// so that both latencies overlap (1, the default); 0 loads after the fill.
-#ifndef MRC_FFT_TWLATE
-#define MRC_FFT_TWLATE 1
-#endif
+// double-float FFT 51.0 -> 49.6 ms against normalising after every stage,
+// max |rho_L| 7.51e-14 either way.
 template <class T>
 constexpr int fft_default_ec() { return sizeof(cx<T>) == 8 ? MRC_F32_EC : MRC_DD_EC; }
 
@@ -232,15 +224,13 @@ __device__ __forceinline__ void fft_gather_any(const FftArgs &a, cx<T> *x, int64
     else fft_gather<T, LOGR, EC, SRC, false>(a, x, j, e0, ecount);
 }
 
-// One in-CTA stage S.  Stage 0 reads its points from global memory, from sm
-// (bulk-copy staging) or, with PIPE, from the staging buffer stg filled by
-// fft_pipe_prefetch (complex rows [R][EC], or for a real source the two real
-// rows of each packed point, [R][2][EC] doubles; inter-pass twiddles in spt
-// not yet conjugated).
-template <class T, int LOGR, int EC, int S, bool INV, bool PIPE = false, bool PRE = false>
+// One in-CTA stage S.  Stage 0 takes its points from `pre` (loaded from
+// global memory by fft_gather before the CTA filled its twiddle tables, so
+// that both latencies overlap) and applies the inter-pass twiddles of spt;
+// later stages read the previous stage's output from sm.
+template <class T, int LOGR, int EC, int S, bool INV>
 __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<T> *stw, const cx<T> *spt,
-                                          int64_t j, int e0, int ecount, int64_t base_out, bool staged,
-                                          const void *stg = nullptr, const cx<T> *pre = nullptr)
+                                          int e0, int ecount, int64_t base_out, const cx<T> *pre)
 {
     using P = FftPlan<T, LOGR, EC>;
     constexpr int R = P::R, NT = P::NT;
@@ -252,26 +242,6 @@ __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<
     constexpr bool FIRST = (S == 0), LAST = (S == P::NSTAGE - 1);
     const int tid = threadIdx.x;
     cx<T> v[UPT][r];
-    // first stage from global memory: one loop per source mode
-    auto load_global = [&](auto src_tag) {
-        constexpr int SRC = decltype(src_tag)::value;
-        fft_gather_any<T, LOGR, EC, SRC>(a, &v[0][0], j, e0, ecount);
-        if (a.Ns > 1) {
-#pragma unroll
-            for (int u = 0; u < UPT; ++u) {
-                const int b = (tid + u * NT) >> P::LEC;
-#pragma unroll
-                for (int q = 0; q < r; ++q) v[u][q] = c_mul(v[u][q], spt[b + q * (R / r)]);
-            }
-        }
-    };
-    if constexpr (FIRST && !PIPE && !PRE) {
-        if (!staged) {
-            if (a.src_mode == SRC_CPLX) load_global(std::integral_constant<int, SRC_CPLX>{});
-            else if (a.src_mode == SRC_REAL32) load_global(std::integral_constant<int, SRC_REAL32>{});
-            else load_global(std::integral_constant<int, SRC_REAL64>{});
-        }
-    }
 #pragma unroll
     for (int u = 0; u < UPT; ++u) {
         const int unit = tid + u * NT;
@@ -279,34 +249,16 @@ __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<
 #pragma unroll
         for (int q = 0; q < r; ++q) {
             const int rho = b + q * (R / r);
-            if constexpr (FIRST && PRE) {
-                cx<T> x = pre[u * r + q];  // loaded before the twiddle tables were filled
+            if constexpr (FIRST) {
+                cx<T> x = pre[u * r + q];
                 if (a.Ns > 1) x = c_mul(x, spt[rho]);
                 v[u][q] = x;
-            } else if constexpr (FIRST && PIPE) {
-                cx<T> x;
-                if (a.src_mode == SRC_CPLX) {
-                    x = reinterpret_cast<const cx<T> *>(stg)[rho * EC + e];
-                } else {
-                    const double *s2 = reinterpret_cast<const double *>(stg) + rho * 2 * EC;
-                    x = c_from_d<T>(s2[e], s2[EC + e]);
-                }
-                if (a.src_neg) x = c_neg(x);
-                if (a.Ns > 1) x = c_mul(x, INV ? c_conj(spt[rho]) : spt[rho]);
-                v[u][q] = x;
-            } else if constexpr (FIRST) {
-                if (staged) {
-                    cx<T> x = sm[rho * EC + e];  // rows past the valid range were zero-filled
-                    if (a.src_neg) x = c_neg(x);
-                    if (a.Ns > 1) x = c_mul(x, spt[rho]);
-                    v[u][q] = x;
-                }
             } else {
                 v[u][q] = sm[rho * EC + e];
             }
         }
     }
-    if (!FIRST || (staged && !PIPE)) __syncthreads();  // every read of sm done before the in-place writes
+    if (!FIRST) __syncthreads();  // every read of sm done before the in-place writes
 #pragma unroll
     for (int u = 0; u < UPT; ++u) {
         const int b = (tid + u * NT) >> P::LEC;
@@ -315,7 +267,7 @@ __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<
 #pragma unroll
             for (int q = 1; q < r; ++q) v[u][q] = c_mul(v[u][q], stw[(bm * q) << (LOGR - LNS - LR)]);
         }
-        dft_r<T, INV, LR, (LAST || MRC_DD_STAGE_NORM)>(v[u]);
+        dft_r<T, INV, LR, LAST>(v[u]);
     }
     // Output point q of unit u goes to row k = k0 + q Ns a.Ns.  Complex rows
     // sit at k ld + e; the real rows 2k + h (kept in the window [lo, hi)) at
@@ -400,73 +352,6 @@ __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<
     }
 }
 
-// The first stage's global loads on their own (no inter-pass twiddle), issued
-// before the twiddle tables are filled so that both latencies overlap.
-template <class T, int LOGR, int EC, int SRC>
-__device__ __forceinline__ void fft_preload(const FftArgs &a, cx<T> *pre, int64_t j, int e0, int ecount)
-{
-    fft_gather_any<T, LOGR, EC, SRC>(a, pre, j, e0, ecount);
-}
-
-// Bulk-copy staging of a complex source (TMA, cp.async.bulk): warp 0 copies
-// the R row segments j + rho M/R (EC entries each, EC * sizeof(cx<T>) bytes,
-// 16-byte aligned: checked on the host) into sm[rho][*], completing on one
-// mbarrier; the other warps zero-fill the segments of rows past the valid
-// range.  The wait is bounded: if it gives up, the status word is set to
-// MRC_ERR_TIMEOUT and a second bounded wait lets copies in flight land before
-// the CTA moves on.
-__device__ __forceinline__ bool mbar_try_wait(unsigned addr, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok) : "r"(addr), "r"(parity) : "memory");
-    return ok != 0;
-}
-
-template <class T, int LOGR, int EC>
-__device__ __forceinline__ void fft_stage_in_tma(const FftArgs &a, cx<T> *sm, int64_t j, int e0)
-{
-    using P = FftPlan<T, LOGR, EC>;
-    constexpr int R = P::R;
-    __shared__ alignas(8) unsigned long long mbar;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const unsigned mb = (unsigned)__cvta_generic_to_shared(&mbar);
-    const int64_t stride = a.M >> LOGR;
-    // valid rows: k = j + rho * stride < nvalid
-    const int64_t nv64 = a.src_nvalid > j ? (a.src_nvalid - j + stride - 1) / stride : 0;
-    const int nv = (int)(nv64 < R ? nv64 : R);
-    constexpr unsigned SEG = EC * sizeof(cx<T>);
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
-    __syncthreads();
-    if (tid < 32) {
-        if (lane == 0)
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mb), "r"(SEG * nv)
-                         : "memory");
-        __syncwarp();
-        const cx<T> *src = reinterpret_cast<const cx<T> *>(a.src);
-        for (int rho = lane; rho < nv; rho += 32) {
-            const cx<T> *g = src + (a.src_row0 + j + (int64_t)rho * stride) * (int64_t)a.src_ld + e0;
-            const unsigned s = (unsigned)__cvta_generic_to_shared(sm + rho * EC);
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(s),
-                "l"(g), "r"(SEG), "r"(mb)
-                : "memory");
-        }
-    } else {
-        for (int idx = nv * EC + (tid - 32); idx < R * EC; idx += P::NT - 32) sm[idx] = c_zero<T>();
-    }
-    bool done = false;
-    for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(mb, 0);
-    if (!done) {
-        if (a.status) atomicExch(a.status, 6);
-        for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(mb, 0);
-    }
-}
-
 template <class T, int LOGR, int EC, bool INV>
 __device__ __forceinline__ void fft_pass_body(const FftArgs &a)
 {
@@ -478,22 +363,15 @@ __device__ __forceinline__ void fft_pass_body(const FftArgs &a)
     cx<T> *spt = stw + R;                             // [R]  inter-pass twiddles
     const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
     const int tid = threadIdx.x;
-    const int64_t j = a.chunk_fast ? blockIdx.y : blockIdx.x;
-    const int e0 = (a.chunk_fast ? blockIdx.x : blockIdx.y) * EC;
+    const int64_t j = blockIdx.y;   // entry chunk fastest: CTAs launched together cover whole rows
+    const int e0 = blockIdx.x * EC;
     const int ecount = min(EC, a.E - e0);
     const int64_t jm = j & (a.Ns - 1);
-#if MRC_FFT_TWLATE
-    constexpr bool PRE = true;
+    // first-stage global loads before the twiddle tables are filled (both latencies overlap)
     cx<T> pre[P::EPT];
-    if (!a.tma) {
-        if (a.src_mode == SRC_CPLX) fft_preload<T, LOGR, EC, SRC_CPLX>(a, pre, j, e0, ecount);
-        else if (a.src_mode == SRC_REAL32) fft_preload<T, LOGR, EC, SRC_REAL32>(a, pre, j, e0, ecount);
-        else fft_preload<T, LOGR, EC, SRC_REAL64>(a, pre, j, e0, ecount);
-    }
-#else
-    constexpr bool PRE = false;
-    const cx<T> *pre = nullptr;
-#endif
+    if (a.src_mode == SRC_CPLX) fft_gather_any<T, LOGR, EC, SRC_CPLX>(a, pre, j, e0, ecount);
+    else if (a.src_mode == SRC_REAL32) fft_gather_any<T, LOGR, EC, SRC_REAL32>(a, pre, j, e0, ecount);
+    else fft_gather_any<T, LOGR, EC, SRC_REAL64>(a, pre, j, e0, ecount);
     if constexpr (P::NSTAGE > 1)
         for (int t = tid; t < R; t += P::NT) {
             cx<T> w = tw[(int64_t)t << (a.tw_log - LOGR)];
@@ -506,17 +384,12 @@ __device__ __forceinline__ void fft_pass_body(const FftArgs &a)
             spt[t] = INV ? c_conj(w) : w;
         }
     }
-    const bool staged = a.tma != 0;
-    if (staged) fft_stage_in_tma<T, LOGR, EC>(a, sm, j, e0);
     __syncthreads();
     const int64_t base_out = (j >> a.logNs << (a.logNs + LOGR)) + jm;
-    if (PRE && !staged)
-        fft_stage<T, LOGR, EC, 0, INV, false, PRE>(a, sm, stw, spt, j, e0, ecount, base_out, staged, nullptr, pre);
-    else
-        fft_stage<T, LOGR, EC, 0, INV>(a, sm, stw, spt, j, e0, ecount, base_out, staged);
-    if constexpr (P::NSTAGE > 1) fft_stage<T, LOGR, EC, 1, INV>(a, sm, stw, spt, j, e0, ecount, base_out, staged);
-    if constexpr (P::NSTAGE > 2) fft_stage<T, LOGR, EC, 2, INV>(a, sm, stw, spt, j, e0, ecount, base_out, staged);
-    if constexpr (P::NSTAGE > 3) fft_stage<T, LOGR, EC, 3, INV>(a, sm, stw, spt, j, e0, ecount, base_out, staged);
+    fft_stage<T, LOGR, EC, 0, INV>(a, sm, stw, spt, e0, ecount, base_out, pre);
+    if constexpr (P::NSTAGE > 1) fft_stage<T, LOGR, EC, 1, INV>(a, sm, stw, spt, e0, ecount, base_out, nullptr);
+    if constexpr (P::NSTAGE > 2) fft_stage<T, LOGR, EC, 2, INV>(a, sm, stw, spt, e0, ecount, base_out, nullptr);
+    if constexpr (P::NSTAGE > 3) fft_stage<T, LOGR, EC, 3, INV>(a, sm, stw, spt, e0, ecount, base_out, nullptr);
 }
 
 // One Stockham pass of radix R = 2^LOGR over EC entries per CTA.
@@ -547,125 +420,6 @@ __global__ void __launch_bounds__(FftPlan<T, LOGR, EC>::NT,
 {
     if (a.dir > 0) fft_pass_body<T, LOGR, EC, true>(a);
     else fft_pass_body<T, LOGR, EC, false>(a);
-}
-
-// ---------------------------------------------------------------------------
-// Persistent pipelined pass.  The same Stockham pass as fft_pass_kernel, but
-// each CTA loops over tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... with
-// the entry chunk fastest (CTAs running together read and write whole rows),
-// and while it computes tile t the row segments and inter-pass twiddles of
-// its next tile are already on their way into a staging buffer (cp.async,
-// 16-byte pieces; rows past the valid range are zero-filled by a copy of
-// source size 0).  Requires E % EC == 0, a 16-byte aligned source with a
-// row stride that is a multiple of 16 bytes, and two passes or more
-// (NSTAGE > 1: stage 0 ends with a barrier, after which the staging buffer is
-// free for the next tile).
-__device__ __forceinline__ void cp_async16(unsigned dst, const void *src, unsigned src_bytes)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-template <int BYTES>
-__device__ __forceinline__ void cp_async_small(unsigned dst, const void *src)
-{
-    static_assert(BYTES == 8 || BYTES == 16, "cp.async size");
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(dst), "l"(src), "n"(BYTES) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-// staging bytes per tile: complex source R*EC values, real source 2*R*EC doubles
-template <class T, int LOGR, int EC>
-struct FftPipeSmem {
-    static constexpr size_t R = (size_t)1 << LOGR;
-    static constexpr size_t head = (R * EC + 2 * R) * sizeof(cx<T>);  // sm, stw, spt
-    static constexpr size_t stg_cplx = R * EC * sizeof(cx<T>);
-    static constexpr size_t stg_real = 2 * R * EC * sizeof(double);
-};
-
-template <class T, int LOGR, int EC>
-__device__ __forceinline__ void fft_pipe_prefetch(const FftArgs &a, unsigned char *stg, cx<T> *spt, int64_t t,
-                                                  int nchunk)
-{
-    using P = FftPlan<T, LOGR, EC>;
-    constexpr int R = P::R, NT = P::NT;
-    const int tid = threadIdx.x;
-    const int64_t j = t / nchunk;
-    const int e0 = (int)(t - j * nchunk) * EC;
-    const int64_t stride = a.M >> LOGR;
-    const unsigned sb = (unsigned)__cvta_generic_to_shared(stg);
-    const char *g = reinterpret_cast<const char *>(a.src);
-    if (a.src_mode == SRC_CPLX) {
-        constexpr int CPR = EC * (int)sizeof(cx<T>) / 16;  // 16-byte pieces per row segment
-        static_assert(CPR >= 1, "row segment below 16 bytes");
-        for (int c = tid; c < R * CPR; c += NT) {
-            const int rho = c / CPR, q = c - (c / CPR) * CPR;
-            const int64_t k = j + (int64_t)rho * stride;
-            const bool ok = k < a.src_nvalid;
-            const char *src = ok ? g + ((a.src_row0 + k) * (int64_t)a.src_ld + e0) * (int64_t)sizeof(cx<T>) + q * 16 : g;
-            cp_async16(sb + 16u * c, src, ok ? 16u : 0u);
-        }
-    } else {
-        constexpr int CPR = EC * 8 / 16;  // pieces per real row segment
-        static_assert(CPR >= 1, "row segment below 16 bytes");
-        for (int c = tid; c < 2 * R * CPR; c += NT) {
-            const int rh = c / CPR, q = c - (c / CPR) * CPR;  // rh = 2 rho + h
-            const int64_t r = 2 * (j + (int64_t)(rh >> 1) * stride) + (rh & 1);
-            const bool ok = r < a.src_nvalid;
-            const char *src = ok ? g + ((a.src_row0 + r) * (int64_t)a.src_ld + e0) * 8 + q * 16 : g;
-            cp_async16(sb + 16u * c, src, ok ? 16u : 0u);
-        }
-    }
-    if (a.Ns > 1) {
-        const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
-        const int sh = a.tw_log - (a.logNs + LOGR);
-        const int64_t jm = j & (a.Ns - 1);
-        for (int k = tid; k < R; k += NT)
-            cp_async_small<(int)sizeof(cx<T>)>((unsigned)__cvta_generic_to_shared(spt + k), tw + ((jm * k) << sh));
-    }
-    cp_async_commit();
-}
-
-template <class T, int LOGR, int EC, bool INV>
-__device__ __forceinline__ void fft_pipe_body(const FftArgs &a)
-{
-    using P = FftPlan<T, LOGR, EC>;
-    static_assert(P::NSTAGE > 1, "pipelined pass needs a barrier after stage 0");
-    constexpr int R = P::R;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);  // [R][EC] exchange
-    cx<T> *stw = sm + R * EC;                         // [R]  W_R^t
-    cx<T> *spt = stw + R;                             // [R]  inter-pass twiddles of the staged tile
-    unsigned char *stg = smem_raw + FftPipeSmem<T, LOGR, EC>::head;
-    const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
-    const int tid = threadIdx.x;
-    const int nchunk = a.E / EC;
-    const int64_t ntiles = (a.M >> LOGR) * nchunk;
-    for (int k = tid; k < R; k += P::NT) {
-        cx<T> w = tw[(int64_t)k << (a.tw_log - LOGR)];
-        stw[k] = INV ? c_conj(w) : w;
-    }
-    int64_t t = blockIdx.x;
-    if (t < ntiles) fft_pipe_prefetch<T, LOGR, EC>(a, stg, spt, t, nchunk);
-    for (; t < ntiles; t += gridDim.x) {
-        cp_async_wait_all();
-        __syncthreads();
-        const int64_t j = t / nchunk;
-        const int e0 = (int)(t - j * nchunk) * EC;
-        const int64_t jm = j & (a.Ns - 1);
-        const int64_t base_out = (j >> a.logNs << (a.logNs + LOGR)) + jm;
-        fft_stage<T, LOGR, EC, 0, INV, true>(a, sm, stw, spt, j, e0, EC, base_out, false, stg);
-        if (t + gridDim.x < ntiles) fft_pipe_prefetch<T, LOGR, EC>(a, stg, spt, t + gridDim.x, nchunk);
-        fft_stage<T, LOGR, EC, 1, INV>(a, sm, stw, spt, j, e0, EC, base_out, false);
-        if constexpr (P::NSTAGE > 2) fft_stage<T, LOGR, EC, 2, INV>(a, sm, stw, spt, j, e0, EC, base_out, false);
-        if constexpr (P::NSTAGE > 3) fft_stage<T, LOGR, EC, 3, INV>(a, sm, stw, spt, j, e0, EC, base_out, false);
-    }
-}
-
-template <class T, int LOGR, int EC>
-__global__ void __launch_bounds__(FftPlan<T, LOGR, EC>::NT) fft_pipe_kernel(FftArgs a)
-{
-    if (a.dir > 0) fft_pipe_body<T, LOGR, EC, true>(a);
-    else fft_pipe_body<T, LOGR, EC, false>(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -980,22 +734,12 @@ __global__ void twiddle_kernel(cx<T> *tw, int log)
 // ---------------------------------------------------------------------------
 // Launch table of the FFT pass instantiations: entry [ec_index][logR], where
 // ec_index 0 is the default entries per CTA (MRC_F32_EC for 8-byte complex
-// values, 8 for 16-byte ones) and 1 is 4 entries per CTA.  Default entries of
-// radix 2^5 .. 2^10 in the FP32 and double-float precisions also carry the
-// persistent pipelined pass (pipe; null elsewhere).
+// values, MRC_DD_EC for 16-byte ones) and 1 is 4 entries per CTA.
 using FftKernel = void (*)(FftArgs);
 struct FftEntry {
     FftKernel fn;
     int nt;
-    FftKernel pipe;
 };
-
-template <class T, int L, int EC>
-constexpr FftKernel fft_pipe_or_null()
-{
-    if constexpr (L >= 5 && !__is_same(T, double)) return fft_pipe_kernel<T, L, EC>;
-    else return nullptr;
-}
 
 template <class T, int L, int EC>
 constexpr FftKernel fft_pass_or_mb()
@@ -1010,7 +754,6 @@ template <class T, int OFF, int... L>
 void fft_fill_shifted(FftEntry (*t)[11], std::integer_sequence<int, L...>)
 {
     constexpr int ECD = fft_default_ec<T>();
-    ((t[0][OFF + L] = FftEntry{fft_pass_or_mb<T, OFF + L, ECD>(), FftPlan<T, OFF + L, ECD>::NT,
-                               fft_pipe_or_null<T, OFF + L, ECD>()}), ...);
-    ((t[1][OFF + L] = FftEntry{fft_pass_kernel<T, OFF + L, 4>, FftPlan<T, OFF + L, 4>::NT, nullptr}), ...);
+    ((t[0][OFF + L] = FftEntry{fft_pass_or_mb<T, OFF + L, ECD>(), FftPlan<T, OFF + L, ECD>::NT}), ...);
+    ((t[1][OFF + L] = FftEntry{fft_pass_kernel<T, OFF + L, 4>, FftPlan<T, OFF + L, 4>::NT}), ...);
 }

@@ -2,7 +2,6 @@
 // k_<prec>.cu includes this file once with MRC_T / MRC_SUF defined.
 #pragma once
 #include <stdint.h>
-#include <stdlib.h>
 
 #include <algorithm>
 #include <type_traits>
@@ -47,70 +46,6 @@ size_t fft_smem_bytes(int logR, int ec)
 
 template <class T>
 int ec_index(int ec) { return ec == default_ec<T>() ? 0 : 1; }
-
-template <class T>
-size_t fft_pipe_smem_bytes(int logR, int ec, int src_mode)
-{
-    const size_t R = (size_t)1 << logR;
-    const size_t stg = src_mode == SRC_CPLX ? R * ec * sizeof(cx<T>) : 2 * R * ec * sizeof(double);
-    return (R * ec + 2 * R) * sizeof(cx<T>) + stg;
-}
-
-// The persistent pipelined pass (fft_pipe_kernel) runs a pass of a two-pass
-// transform when its instantiation exists, whole chunks cover E, the source
-// rows are 16-byte aligned for cp.async, and MRC_FFT_PIPE allows this
-// precision: "1" = FP32, "all" = FP32 and double-float, unset or "0" = never.
-// Off by default: at d = 64, N = 2^18 it measured slower than one tile per
-// CTA (FP32 FFT 104 -> 109 ms, double-float 113 -> 125 ms).
-template <class T>
-bool pipe_eligible(const FftArgs &a, const FftEntry &k, int np)
-{
-    const char *v = getenv("MRC_FFT_PIPE");
-    const int mode = (!v || !v[0] || v[0] == '0') ? 0 : v[0] == 'a' ? 2 : 1;
-    if (!k.pipe || np < 2 || a.tma || mode == 0 || a.src_mode == SRC_REAL32) return false;
-    if (sizeof(cx<T>) != 8 && mode < 2) return false;
-    if (a.ec != default_ec<T>() || (a.E % a.ec) != 0) return false;
-    if (fft_pipe_smem_bytes<T>(a.logR, a.ec, a.src_mode) > 200 * 1024) return false;
-    const size_t rowb = (size_t)a.src_ld * (a.src_mode == SRC_CPLX ? sizeof(cx<T>) : sizeof(double));
-    return (rowb % 16) == 0 && (((uintptr_t)a.src) % 16) == 0;
-}
-
-// CTAs of the pipelined pass resident on the whole device (occupancy x SMs),
-// cached per radix and source kind for the current device.
-template <class T>
-int64_t pipe_resident_ctas(const FftEntry &k, int logR, int src_mode, size_t smem)
-{
-    static int cache[11][2] = {};
-    int &c = cache[logR][src_mode == SRC_CPLX ? 0 : 1];
-    if (c == 0) {
-        int dev = 0, nsm = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k.pipe, k.nt, smem);
-        c = std::max(1, nsm * std::max(per, 1));
-    }
-    return c;
-}
-
-// Grid order of the pass kernels.  By default the entry chunk is in
-// blockIdx.x, so that CTAs launched together cover whole rows j + rho M/R:
-// at d = 64, N = 2^18 the double-float FFT went 67.9 -> 66.6 ms, the FP32
-// FFT did not change (84.1 / 84.0 ms).  MRC_FFT_ORDER=0 puts the row offset
-// j fastest.  (nrow = M / R <= 2^10 < 65536 in every plan.)
-template <class T>
-int fft_chunk_fast()
-{
-    const char *v = getenv("MRC_FFT_ORDER");
-    return (v && v[0] == '0') ? 0 : 1;
-}
-
-// MRC_FFT_OFF64=1 makes every pass use 64-bit element offsets (the path
-// large transforms take), so that a test can compare it with the 32-bit one.
-inline bool fft_force_off64()
-{
-    const char *v = getenv("MRC_FFT_OFF64");
-    return v && v[0] == '1';
-}
 
 // Radix plan: one pass up to 2^10, else two passes of sizes 2^ceil(l/2), 2^floor(l/2).
 inline int fft_plan(int logM, int *logRs)
@@ -164,24 +99,17 @@ cudaError_t fft_run(const FftSrc &src, const FftDst &dst, int64_t M, int E, int 
             const int64_t src_span = (a.src_mode == SRC_CPLX ? M : 2 * M + 1) * (int64_t)a.src_ld + ec;
             const int64_t dst_span = a.dst_mode == DST_CPLX ? M * (int64_t)a.dst_ld + ec
                                                             : (a.dst_row0 + (a.dst_hi - a.dst_lo) + 1) * a.dst_ld + ec;
-            const bool off64 = fft_force_off64();
-            a.src_off32 = !off64 && src_span < lim;
-            a.dst_off32 = !off64 && dst_span < lim && a.dst_row0 >= 0 && a.dst_hi >= a.dst_lo;
+            a.src_off32 = src_span < lim;
+            a.dst_off32 = dst_span < lim && a.dst_row0 >= 0 && a.dst_hi >= a.dst_lo;
         }
         a.dst_scale_f = (float)a.dst_scale;
         a.dst_scaled = a.dst_scale != 1.0;
-        // bulk-copy staging of a complex source: 16-byte aligned row segments
-        // of whole chunks, and at least one warp besides the copying warp
-        {
-            const FftEntry &kk = fft_table<T>()[ec_index<T>(ec)][a.logR];
-            const size_t rowb = (size_t)a.src_ld * sizeof(cx<T>);
-            a.tma = a.src_mode == SRC_CPLX && kk.nt >= 64 && (E % ec) == 0 && (rowb % 16) == 0 &&
-                    (((uintptr_t)a.src) % 16) == 0 && ((ec * sizeof(cx<T>)) % 16) == 0 && mrc_fft_tma_enabled();
-            a.status = mrc_status_word();
-        }
-        a.chunk_fast = fft_chunk_fast<T>();
+        // entry chunk in blockIdx.x, row offset j in blockIdx.y: CTAs launched
+        // together cover whole rows j + rho M / R (d = 64, N = 2^18: double-float
+        // FFT 67.9 -> 66.6 ms against the other order, FP32 unchanged);
+        // nrow = M / R <= 2^10 in every plan
         const unsigned nrow = (unsigned)(M >> a.logR), nchunk = (unsigned)((E + ec - 1) / ec);
-        const dim3 grid = a.chunk_fast ? dim3(nchunk, nrow) : dim3(nrow, nchunk);
+        const dim3 grid(nchunk, nrow);
         // algorithmic charge: the valid source rows read once, the kept output written once,
         // 5 M log2(R) real flops per entry (radix-2 convention)
         double rd, wr;
@@ -195,14 +123,7 @@ cudaError_t fft_run(const FftSrc &src, const FftDst &dst, int64_t M, int E, int 
         else wr = rows * 8.0 * (a.dst_mode == DST_REAL64_ADD ? 2.0 : 1.0);
         const FftEntry &k = fft_table<T>()[ec_index<T>(ec)][a.logR];
         mrc_prof_pre(kclass_fft<T>(), st);
-        if (pipe_eligible<T>(a, k, np)) {
-            const size_t smem = fft_pipe_smem_bytes<T>(a.logR, ec, a.src_mode);
-            const int64_t ntiles = (M >> a.logR) * (int64_t)(E / ec);
-            const int64_t g = std::min<int64_t>(ntiles, pipe_resident_ctas<T>(k, a.logR, a.src_mode, smem));
-            k.pipe<<<(unsigned)g, k.nt, smem, st>>>(a);
-        } else {
-            k.fn<<<grid, k.nt, fft_smem_bytes<T>(a.logR, ec), st>>>(a);
-        }
+        k.fn<<<grid, k.nt, fft_smem_bytes<T>(a.logR, ec), st>>>(a);
         mrc_prof_post(kclass_fft<T>(), st, rd + wr, 5.0 * (double)M * a.logR * E);
         logNs += a.logR;
     }
@@ -250,13 +171,10 @@ cudaError_t pairmul_run(const void *zx, const void *zy, void *zc, int64_t M, int
     if (cfg == 0) return pairmul_launch<T, 16, 16, 16, 2, 2>(a, st);
     if (cfg == 1) return pairmul_launch<T, 32, 32, 16, 2, 2>(a, st);
     // FP32, 64 x 64 tiles: the frequencies of a pair on two halves of the CTA
-    // (half the registers per thread, two CTAs per SM); MRC_PAIR_SPLIT=0 keeps
-    // both frequencies in every thread
-    if constexpr (std::is_same<T, float>::value) {
-        const char *v = getenv("MRC_PAIR_SPLIT");
-        if (!(v && v[0] == '0')) return pairmul2_launch<T, 64, 64, 8, 4, 4>(a, st);
-    }
-    return pairmul_launch<T, 64, 64, 8, 4, 4>(a, st);
+    // (half the registers per thread, two CTAs per SM: pairmul_f32 54.9 ->
+    // 49.4 ms at d = 64, N = 2^18 against both frequencies in every thread)
+    if constexpr (std::is_same<T, float>::value) return pairmul2_launch<T, 64, 64, 8, 4, 4>(a, st);
+    else return pairmul_launch<T, 64, 64, 8, 4, 4>(a, st);
 }
 
 template <class T>
@@ -294,10 +212,6 @@ cudaError_t init_run()
         for (int l = 0; l < 11; ++l) {
             cudaError_t e = cudaFuncSetAttribute(t[i][l].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             if (e != cudaSuccess) return e;
-            if (t[i][l].pipe) {
-                e = cudaFuncSetAttribute(t[i][l].pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-                if (e != cudaSuccess) return e;
-            }
         }
     return cudaSuccess;
 }

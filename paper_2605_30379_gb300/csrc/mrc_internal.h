@@ -41,9 +41,6 @@ struct FftArgs {
     void *dst2;             // double-float DST_CPLX only: also write the hi parts here as FP32 complex (or null)
     const void *dst_base;   // DST_REAL64_BASE32: binary32 rows added to the result
     int src_off32, dst_off32; // every source / destination element offset of the pass fits 32 bits
-    int tma;                // CPLX source staged into shared memory by bulk copies (first stage)
-    int chunk_fast;         // grid order: 1 = entry chunk in blockIdx.x, row offset j in blockIdx.y
-    int *status;            // device status word: MRC_ERR_TIMEOUT (6) if a bounded wait gives up
 };
 
 struct PairArgs {
@@ -76,13 +73,6 @@ struct FftDst {
     const void *base = nullptr;  // DST_REAL64_BASE32: binary32 rows (FftArgs::dst_base)
 };
 
-// prof.cu: device status word that bounded in-kernel waits report timeouts to
-// (the most recently created context's), and the FFT staging switch
-// (MRC_FFT_TMA=1 turns bulk-copy staging of complex sources on; measured
-// slower on the d = 64 workload, so off by default)
-int *mrc_status_word(void);
-void mrc_set_status_word(int *p);
-bool mrc_fft_tma_enabled(void);
 // elements of FFT scratch a transform of M points over E entries needs
 static inline size_t mrc_fft_scratch_elems(int64_t M, int E) { return (size_t)M * (size_t)E; }
 
@@ -111,27 +101,62 @@ MRC_DECLARE_PREC(dd)
 // Element sizes of one complex value per precision.
 static inline size_t mrc_cx_bytes(int prec) { return prec == PREC_F32 ? 8 : 16; }
 
-// ozaki.cu: double-float and FP32 square products (32 <= d <= 64) on BF16 tensor cores
-bool mrc_ozaki_supported(int r, int m, int c);
-cudaError_t mrc_ozaki_init(void);
-cudaError_t mrc_pairmul_dd_ozaki(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw,
-                                 int tw_log, cudaStream_t st);
-cudaError_t mrc_pairmul_f32_ozaki(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw,
-                                  int tw_log, cudaStream_t st);
-
-// ozaki_tc.cu: the same digit products on the tcgen05 tensor cores (TMEM accumulators)
+// ozaki_tc.cu: double-float square products (32 <= d <= 512) as exact digit
+// products on the tcgen05 tensor cores (TMEM accumulators); a bounded wait
+// that gives up writes MRC_ERR_TIMEOUT (6) to *status
 bool mrc_tc_supported(int r, int m, int c);
 cudaError_t mrc_tc_init(void);
 cudaError_t mrc_pairmul_dd_tc(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
-                              cudaStream_t st);
-cudaError_t mrc_pairmul_f32_tc(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
-                               cudaStream_t st);
+                              int *status, cudaStream_t st);
+// pair_tc.cu: the pipelined, warp-specialised tcgen05 digit products for
+// square 32 <= d <= 64, double-float (the residual) and FP32 (Newton levels
+// and correction); timeouts as above
+bool mrc_tcp_supported(int r, int m, int c);
+cudaError_t mrc_tcp_init(void);
+cudaError_t mrc_pairmul_dd_tcp(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
+                               int *status, cudaStream_t st);
+cudaError_t mrc_pairmul_f32_tcp(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
+                                int *status, cudaStream_t st);
+// the kernels' bounded mbarrier wait on a barrier nothing arrives on: writes 6 to *status
+cudaError_t mrc_tc_wait_selftest(int *status, int spins, cudaStream_t st);
 
-// tf32x3.cu: FP32 square products (16 <= d <= 64) as three TF32 tensor-core products
-bool mrc_tf32x3_supported(int r, int m, int c);
-cudaError_t mrc_tf32x3_init(void);
-cudaError_t mrc_pairmul_f32_tf32x3(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw,
-                                   int tw_log, cudaStream_t st);
+// api.cu: the Newton doubling schedule of Eq. (newton), shared by every
+// inverse entry point (mrc_inverse* and mrc_inverse_noalloc).
+//   mrc_base_size: the first m0 coefficients come from the direct recursion;
+//   mrc_newton_maxM: the largest level m (its transforms have M = m points).
+int64_t mrc_base_size(int d, int64_t N);
+int64_t mrc_newton_maxM(int d, int64_t N);
+// Row ranges of A still being uploaded (mrc_inverse_host): rows
+// [end[i-1], end[i]) complete at ev[i]; wait(s, rows) makes stream s wait
+// until rows [0, rows) are on the device.  n == 0: everything is there.
+struct RowWait {
+    int n = 0;
+    int64_t end[32] = {};
+    cudaEvent_t ev[32] = {};
+    cudaError_t wait(cudaStream_t s, int64_t rows) const
+    {
+        for (int i = 0; i < n; ++i)
+            if (end[i] >= rows) return cudaStreamWaitEvent(s, ev[i], 0);
+        return n ? cudaStreamWaitEvent(s, ev[n - 1], 0) : cudaSuccess;
+    }
+};
+// The per-frequency product a level uses: zc = zx * zy at the M/2 + 1
+// frequency pairs of (PREC_F64 or PREC_F32) spectra of length M, d x d.
+typedef cudaError_t (*mrc_level_product_fn)(void *user, int prec, const void *zx, const void *zy, void *zc,
+                                            int64_t M, int d, const void *tw, int tw_log, cudaStream_t st);
+// Buffers of the levels: three spectra and the FFT scratch, each
+// mrc_newton_maxM(d, N) * d^2 complex values of the working precision.
+struct NewtonBufs {
+    void *b0, *b1, *b2, *bt;
+};
+// Levels m0 -> N on `st`: psi rows [0, m0) are already correct.  With A32 /
+// psi32 (FP32 levels of the mixed path) A is read from its binary32 copy,
+// converted here row range by row range, and psi is read and written in
+// binary32.  rw (nullable) delays each level until its rows of A arrived.
+// Returns 0 or 4 (a CUDA error, printed); *levels (nullable) = levels run.
+int mrc_newton_levels(int prec, int d, int64_t N, const double *A, double *psi, int64_t m0, const NewtonBufs &b,
+                      const void *tw, int tw_log, mrc_level_product_fn product, void *user, cudaStream_t st,
+                      const RowWait *rw, float *A32, float *psi32, int *levels);
 
 // misc.cu
 cudaError_t mrc_gauss_jordan(const double *A0, double *out, double *work, int d, int *status, cudaStream_t st);

@@ -6,11 +6,19 @@
 // pool that has reserved the free memory), firmware-style or certified code
 // that forbids dynamic allocation once initialisation is over, or a plugin
 // host that hands its plugins fixed buffers only.  For them this entry point
-// runs the same FP64 FFT-Newton kernels as mrc_inverse, but its scratch (the
-// spectra of the Newton levels, the Gauss-Jordan work area, the twiddle table
-// and the status word) lives in one file-scope __device__ array of fixed
-// size, so nothing is allocated at call time.  The caller still passes A and
-// psi.
+// runs the FP64 FFT-Newton schedule of mrc_inverse (the same level loop, FFT
+// kernels and default FP64 product kernel), but its scratch (the spectra of
+// the Newton levels, the Gauss-Jordan work area, the twiddle table and the
+// status word) lives in one file-scope __device__ array of fixed size, so
+// nothing is allocated at call time.  The caller still passes A and psi.
+//
+// Under CUDA's default lazy module loading the array, like the library's
+// kernels, is mapped on a device only when this file's module is first used
+// there -- by the first call's cudaGetSymbolAddress.  That first call on each
+// device is therefore the initialisation step: make it before another
+// allocator reserves the device memory (or load modules eagerly with
+// CUDA_MODULE_LOADING=EAGER, which maps the array when the library is
+// loaded).
 #include <cuda_runtime.h>
 #include <stdio.h>
 
@@ -26,7 +34,7 @@ constexpr size_t kScratchBytes = (size_t)64 << 20;  // 64 MiB
 constexpr int kTwLog = 15;                           // transforms up to 2^14 points (N <= 2^14)
 constexpr int kMaxDevices = 64;
 
-// Every GPU that loads the library holds this array until the process exits.
+// Once mapped on a GPU (see above), the array stays there until the process exits.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 std::mutex g_mu;
@@ -40,17 +48,13 @@ constexpr size_t kTwOff = 256;
 constexpr size_t kTwBytes = (size_t)16 << kTwLog;
 constexpr size_t kWorkOff = kTwOff + kTwBytes;
 
-int64_t base_size(int d, int64_t N)
-{
-    int64_t m0 = d <= 8 ? 32 : (d <= 32 ? 8 : 2);
-    return std::min<int64_t>(m0, N);
-}
+int64_t max_level(int d, int64_t N) { return mrc_newton_maxM(d, N); }
 
-int64_t max_level(int d, int64_t N)
+// the level product: the default FP64 product kernel (no autotuning here)
+cudaError_t product_f64(void *, int, const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw,
+                        int tw_log, cudaStream_t st)
 {
-    int64_t M = 0;
-    for (int64_t m = base_size(d, N); m < N; m <<= 1) M = m;
-    return M;
+    return mrc_pairmul_f64(zx, zy, zc, M, d, d, d, tw, tw_log, st);
 }
 
 size_t need_bytes(int d, int64_t N)
@@ -126,28 +130,12 @@ extern "C" mrc_status mrc_inverse_noalloc(int d, int64_t N, const double *A, dou
     // the status word keeps the previous call's value: clear it first
     CKN(cudaMemsetAsync(status, 0, sizeof(int), st));
     CKN(mrc_gauss_jordan(A, psi, gjw, d, status, st));
-    const int64_t m0 = base_size(d, N);
+    const int64_t m0 = mrc_base_size(d, N);
     CKN(mrc_base_case(A, psi, d, m0, st));
-    for (int64_t m = m0; m < N; m <<= 1) {
-        const int64_t M = m, m2 = std::min<int64_t>(2 * m, N);
-        FftSrc sA{SRC_REAL64, A, 0, std::min<int64_t>(2 * m, N), E, 0};
-        FftSrc sB{SRC_REAL64, psi, 0, m, E, 0};
-        FftDst to0{DST_CPLX, b0, E, 0, 0, 0, 1.0, 0};
-        FftDst to1{DST_CPLX, b1, E, 0, 0, 0, 1.0, 0};
-        CKN(mrc_fft_f64(sA, to0, M, E, -1, bt, tw, kTwLog, st));
-        CKN(mrc_fft_f64(sB, to1, M, E, -1, bt, tw, kTwLog, st));
-        CKN(mrc_pairmul_f64(b0, b1, b2, M, d, d, d, tw, kTwLog, st));
-        FftSrc s2{SRC_CPLX, b2, 0, M, E, 0};
-        FftDst t0s{DST_CPLX, b0, E, 0, 0, 0, 1.0 / (double)M, 0};
-        CKN(mrc_fft_f64(s2, t0s, M, E, +1, bt, tw, kTwLog, st));
-        FftSrc sR{SRC_CPLX, b0, M / 2, M / 2, E, 1};
-        FftDst to2{DST_CPLX, b2, E, 0, 0, 0, 1.0, 0};
-        CKN(mrc_fft_f64(sR, to2, M, E, -1, bt, tw, kTwLog, st));
-        CKN(mrc_pairmul_f64(b1, b2, b0, M, d, d, d, tw, kTwLog, st));
-        FftSrc s0{SRC_CPLX, b0, 0, M, E, 0};
-        FftDst toP{DST_REAL64, psi, E, 0, m2 - m, m, 1.0 / (double)M, 0};
-        CKN(mrc_fft_f64(s0, toP, M, E, +1, bt, tw, kTwLog, st));
-    }
+    const NewtonBufs nb{b0, b1, b2, bt};
+    if (mrc_newton_levels(PREC_F64, d, N, A, psi, m0, nb, tw, kTwLog, product_f64, nullptr, st, nullptr, nullptr,
+                          nullptr, nullptr) != 0)
+        return MRC_ERR_CUDA;
     CKN(cudaStreamSynchronize(st));
     int h = 0;
     CKN(cudaMemcpy(&h, status, sizeof(int), cudaMemcpyDeviceToHost));

@@ -108,19 +108,34 @@ __device__ __forceinline__ void tc_commit(unsigned mbar)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 
-// bounded wait for the completion of phase `parity` of an mbarrier
-__device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity)
+// Bounded wait for the completion of phase `parity` of an mbarrier: at most
+// `spins` rounds of try_wait, each suspending the thread for at most about
+// TC_SUSPEND_NS nanoseconds, so the wait gives up after about spins x 1 us.
+constexpr unsigned TC_SUSPEND_NS = 1000;
+__device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity, int spins = TC_SPIN)
 {
-    for (int it = 0; it < TC_SPIN; ++it) {
+    for (int it = 0; it < spins; ++it) {
         unsigned ok;
         asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(ok)
-            : "r"(mbar), "r"(parity)
+            : "r"(mbar), "r"(parity), "r"(TC_SUSPEND_NS)
             : "memory");
         if (ok) return true;
     }
     return false;
+}
+
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing
+// arrives on (no asynchronous copy or MMA is in flight), gives up after
+// `spins` rounds and reports MRC_ERR_TIMEOUT (6) to *status.
+__global__ void tc_wait_selftest_kernel(int *status, int spins)
+{
+    __shared__ __align__(8) unsigned long long mbar;
+    const unsigned mb = smem_u32(&mbar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    if (!tc_wait(mb, 0, spins) && status) atomicExch(status, 6);
 }
 
 // 32 TMEM lanes x 8 consecutive 32-bit columns: thread `lane` of the warp
@@ -645,26 +660,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) oztc_tiled_kernel(PairArgs a, i
 
 bool mrc_tc_supported(int r, int m, int c) { return r == m && m == c && r >= 32 && r <= TC_DMAX; }
 
+cudaError_t mrc_tc_wait_selftest(int *status, int spins, cudaStream_t st)
+{
+    mrc_prof_pre(7, st);
+    tc_wait_selftest_kernel<<<1, 1, 0, st>>>(status, spins);
+    mrc_prof_post(7, st, 0, 0);
+    return cudaGetLastError();
+}
+
 cudaError_t mrc_tc_init(void)
 {
     cudaError_t e = cudaFuncSetAttribute(oztc_pairmul_kernel<dd>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)tc_small_smem<dd>());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(oztc_pairmul_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tc_small_smem<float>());
-    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(oztc_tiled_kernel<dd>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tc_smem<dd>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(oztc_tiled_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tc_smem<float>());
     return e;
 }
 
-template <class T>
-static cudaError_t tc_run(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
-                          cudaStream_t st, int kclass)
+cudaError_t mrc_pairmul_dd_tc(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
+                              int *status, cudaStream_t st)
 {
+    using T = dd;
     PairArgs a{};
     a.zx = zx; a.zy = zy; a.zc = zc; a.tw = tw; a.tw_log = tw_log; a.M = M;
     int l = 0;
@@ -682,21 +699,9 @@ static cudaError_t tc_run(const void *zx, const void *zy, void *zc, int64_t M, i
     const unsigned grid = (unsigned)std::min<int64_t>(a.npairs, nsm);
     const double bytes = (double)M * 3.0 * d * d * sizeof(cx<T>);
     const double flops = 8.0 * d * d * d * (double)(M + 1);
-    mrc_prof_pre(kclass, st);
-    if (d <= 64) oztc_pairmul_kernel<T><<<grid, TC_THREADS, tc_small_smem<T>(), st>>>(a, mrc_status_word());
-    else oztc_tiled_kernel<T><<<grid, TC_THREADS, tc_smem<T>(), st>>>(a, mrc_status_word());
-    mrc_prof_post(kclass, st, bytes, flops);
+    mrc_prof_pre(6, st);
+    if (d <= 64) oztc_pairmul_kernel<T><<<grid, TC_THREADS, tc_small_smem<T>(), st>>>(a, status);
+    else oztc_tiled_kernel<T><<<grid, TC_THREADS, tc_smem<T>(), st>>>(a, status);
+    mrc_prof_post(6, st, bytes, flops);
     return cudaGetLastError();
-}
-
-cudaError_t mrc_pairmul_dd_tc(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
-                              cudaStream_t st)
-{
-    return tc_run<dd>(zx, zy, zc, M, d, tw, tw_log, st, 6);
-}
-
-cudaError_t mrc_pairmul_f32_tc(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
-                               cudaStream_t st)
-{
-    return tc_run<float>(zx, zy, zc, M, d, tw, tw_log, st, 5);
 }

@@ -1,0 +1,603 @@
+// pair_tc.cu -- per-frequency complex matrix products of the FFT-Newton path
+// (Eq. (fft-convolution): C(phi) = X(phi) Y(phi) at every frequency of the
+// half spectrum, square d x d with 32 <= d <= 64) as exact digit products on
+// the tcgen05 tensor cores, for two working precisions:
+//
+//   double-float (the residual product of Proposition 2.6): six balanced
+//     base-256 digits per value, digit pairs of weight s + t >= 5 (21 pairs
+//     in 6 weight groups), about 2^-41 relative to the row and column bounds;
+//   FP32 (the Newton-level products of Eq. (newton) and the correction):
+//     four digits, pairs s + t >= 3 (10 pairs in 4 groups), about 2^-29.
+//
+// The rows of X are scaled by 2^-sigma_i and the columns of Y by 2^-tau_j
+// (powers of two from bounds over both frequencies of the pair), every value
+// is split into S digits (digits.cuh: exact BF16 integers, |q| <= 128), and
+// all digit pairs of one weight group g accumulate in one FP32 accumulator in
+// TMEM -- exactly, since a group holds at most 6 pairs of two 64-term dot
+// products of digits <= 128 (below 2^24).  One MMA of M = 128, N = 64 forms
+// [C_r; C_i] from the 192-row MN-major A tile [-X_i; X_r; X_i] of a digit:
+// D += [X_r; X_i] Y_r (rows 64..191) and D += [-X_i; X_r] Y_i (rows 0..127).
+//
+// The kernel is persistent (one CTA per SM, pairs p = blockIdx.x, + grid, ...)
+// and warp-specialised, with every hand-off on an mbarrier:
+//   warps 0-7  (split): per frequency pair the row / column bounds, then per
+//              frequency and K chunk of 16 the real-FFT split of the packed
+//              spectra (the fused split of kernels.cuh) and the digit tiles,
+//              into a ring of NSLOT chunk slots (full / empty barriers);
+//   warp 12    (MMA): one thread issues every kept digit pair's MMAs of a
+//              chunk and releases the slot with tcgen05.commit; after the
+//              last chunk of a frequency it signals the epilogue;
+//   warps 8-11 (epilogue): tcgen05.ld of the group accumulators, the fold
+//              top group first (compensated double-float for the top three
+//              groups of the residual product, FP32 below and for FP32),
+//              then, through a shared-memory transpose, the scaling by
+//              2^(sigma + tau), the real-FFT merge of the pair and coalesced
+//              stores of the packed output spectrum.
+// FP32 keeps two accumulator sets in TMEM (4 x 64 columns each), so the MMAs
+// of one frequency overlap the epilogue of the previous one; double-float
+// (6 x 64 columns) has one.
+//
+// Every wait is bounded: a wait that gives up sets MRC_ERR_TIMEOUT (6) in the
+// status word and a shared abort flag; all roles then leave their loops, the
+// MMA thread waits (bounded) for its MMAs in flight, and the TMEM is freed.
+#include "digits.cuh"
+#include "tcgen05.cuh"
+
+namespace {
+
+using namespace mrc_digits;
+using namespace mrc_tc;
+
+template <class T> struct TcP;
+template <> struct TcP<dd> { static constexpr int S = 6, GMIN = 5, NSLOT = 3, NTB = 1; };
+template <> struct TcP<float> { static constexpr int S = 4, GMIN = 3, NSLOT = 4, NTB = 2; };
+
+constexpr int KC = 16;                // K per chunk: one MMA K step
+constexpr int NCH = 64 / KC;          // chunks per frequency
+constexpr int SBO = (KC / 8) * 128;   // bytes between 8-row groups of a tile
+constexpr int A_TILE = 192 * KC * 2;  // bytes of one [-X_i; X_r; X_i] digit tile
+constexpr int B_TILE = 64 * KC * 2;   // bytes of one Y_r or Y_i digit tile
+// 13 warps: 8 split, 4 epilogue (TMEM lane quarters 0..3), 1 MMA; at most
+// four warps per SM sub-partition leaves each thread 128 registers
+constexpr int NSPLIT = 256, NEPI = 128;
+constexpr int WEPI0 = 8, WMMA = 12;
+constexpr int NTHREADS = 13 * 32;
+constexpr int XLD = 33;               // row length (values) of the epilogue transpose
+constexpr unsigned TMEM_COLS = 512;
+constexpr int BAR_SPLIT = 1, BAR_EPI = 2;
+constexpr unsigned IDESC = idesc_bf16<128, 64>();
+
+template <class T>
+struct TcL {
+    static constexpr int S = TcP<T>::S, GMIN = TcP<T>::GMIN, NG = 2 * (S - 1) - GMIN + 1;
+    static constexpr int NSLOT = TcP<T>::NSLOT, NTB = TcP<T>::NTB;
+    static constexpr int SLOT = S * (A_TILE + 2 * B_TILE);
+    static constexpr int XCH = 2 * 64 * XLD * (int)sizeof(T);
+    static constexpr int OFF_XCH = NSLOT * SLOT;
+    // per-pair row / column exponents sig[NB][64], tau[NB][64], then the bounds bx[64], by[64].  The split
+    // warps run at most NSLOT chunks ahead of the MMAs and those at most NTB frequencies ahead of the
+    // epilogue, so the epilogue is fewer than NB = 8 pairs behind the split warps.
+    static constexpr int NB = 8;
+    static constexpr int OFF_SIG = OFF_XCH + XCH;
+    static constexpr int SMEM = OFF_SIG + (2 * NB + 2) * 64 * 4;
+    static_assert(NTB * NG * 64 <= (int)TMEM_COLS, "accumulators fit in TMEM");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+__device__ __forceinline__ int mn_off(int m, int k) { return (m >> 3) * SBO + (k >> 3) * 128 + (k & 7) * 16 + (m & 7) * 2; }
+__device__ __forceinline__ int k_off(int n, int k) { return (n >> 3) * SBO + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2; }
+
+// 2 Xh(f) from the packed spectrum: Z(f) = a, conj-partner Z(M - f) = b,
+// w = W_L^f:  s + w (-i) dlt  with s = a + conj b, dlt = a - conj b (the
+// real-FFT split of kernels.cuh without its factor 1/2, which the output
+// scaling takes instead)
+template <class T>
+__device__ __forceinline__ cx<T> split2(cx<T> za, cx<T> zb, cx<T> w)
+{
+    const cx<T> s = {Ar<T>::add(za.re, zb.re), Ar<T>::sub(za.im, zb.im)};
+    const cx<T> dlt = {Ar<T>::sub(za.re, zb.re), Ar<T>::add(za.im, zb.im)};
+    const cx<T> o = {dlt.im, Ar<T>::neg(dlt.re)};
+    return c_add(s, c_mul(w, o));
+}
+
+__device__ __forceinline__ void digits(dd v, float sc, float (&q)[6]) { digits6(v.hi * sc, v.lo * sc, q); }
+// four balanced base-256 digits of an FP32 value, weights 2^-8 .. 2^-32
+// (the same rounding steps as digits6: t = (x + C) - C rounds x to a grid)
+__device__ __forceinline__ void digits(float v, float sc, float (&q)[4])
+{
+    float x = v * sc, t;
+    t = __fsub_rn(__fadd_rn(x, 49152.0f), 49152.0f);        // grid 2^-8
+    q[3] = t * 256.0f;
+    x = __fsub_rn(x, t);
+    t = __fsub_rn(__fadd_rn(x, 192.0f), 192.0f);            // grid 2^-16
+    q[2] = t * 65536.0f;
+    x = __fsub_rn(x, t);
+    t = __fsub_rn(__fadd_rn(x, 0.75f), 0.75f);              // grid 2^-24
+    q[1] = t * 16777216.0f;
+    x = __fsub_rn(x, t);
+    t = __fsub_rn(__fadd_rn(x, 0x1.8p-9f), 0x1.8p-9f);      // grid 2^-32
+    q[0] = t * 0x1p32f;
+}
+
+template <class T>
+__device__ __forceinline__ cx<T> ldg_cx(const cx<T> *p);
+template <>
+__device__ __forceinline__ cx<dd> ldg_cx<dd>(const cx<dd> *p)
+{
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    return {{v.x, v.y}, {v.z, v.w}};
+}
+template <>
+__device__ __forceinline__ cx<float> ldg_cx<float>(const cx<float> *p)
+{
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    return {v.x, v.y};
+}
+
+// Raw packed-spectrum values of one chunk held by a split thread: X rows
+// 4 i4 .. 4 i4 + 3 at column k0 + (t & 15); Y rows k0 + 4 k4 .. + 3 at column
+// j; both partner rows ra and rb of the pair.
+template <class T>
+struct Raw {
+    cx<T> xa[4], xb[4], ya[4], yb[4];
+};
+
+template <class T>
+__device__ __forceinline__ void load_x(Raw<T> &r, const cx<T> *ZX, int64_t ra, int64_t rb, int d, int k0, int t)
+{
+    const int64_t E = (int64_t)d * d;
+    const int k = k0 + (t & 15), i4 = t >> 4;
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii) {
+        const int i = 4 * i4 + ii;
+        const bool ok = i < d && k < d;
+        const int64_t e = (int64_t)i * d + k;
+        r.xa[ii] = ok ? ldg_cx(ZX + ra * E + e) : c_zero<T>();
+        r.xb[ii] = ok ? ldg_cx(ZX + rb * E + e) : c_zero<T>();
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void load_y(Raw<T> &r, const cx<T> *ZY, int64_t ra, int64_t rb, int d, int k0, int t)
+{
+    const int64_t E = (int64_t)d * d;
+    const int lane = t & 31, j = 8 * (t >> 5) + (lane & 7), k4 = lane >> 3;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const int k = k0 + 4 * k4 + kk;
+        const bool ok = k < d && j < d;
+        const int64_t e = (int64_t)k * d + j;
+        r.ya[kk] = ok ? ldg_cx(ZY + ra * E + e) : c_zero<T>();
+        r.yb[kk] = ok ? ldg_cx(ZY + rb * E + e) : c_zero<T>();
+    }
+}
+
+// digit tiles of X for the slot: per digit, 8 bytes (4 consecutive rows) into
+// each of the three blocks -X_i (rows 0..63), X_r (64..127), X_i (128..191)
+template <class T>
+__device__ __forceinline__ void split_x(const Raw<T> &r, unsigned char *slot, const int *sig, cx<T> w, int d, int t)
+{
+    constexpr int S = TcL<T>::S;
+    const int k = t & 15, i4 = t >> 4;
+    unsigned wr[S][2], wi[S][2];
+    float pr[S], pi[S];
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii) {
+        const int i = 4 * i4 + ii;
+        float qr[S], qi[S];
+        const cx<T> x = split2(r.xa[ii], r.xb[ii], w);
+        const float sc = i < d ? pow2f(-sig[i]) : 0.0f;
+        digits(x.re, sc, qr);
+        digits(x.im, sc, qi);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            if (ii & 1) {
+                wr[s][ii >> 1] = pack2(pr[s], qr[s]);
+                wi[s][ii >> 1] = pack2(pi[s], qi[s]);
+            } else {
+                pr[s] = qr[s];
+                pi[s] = qi[s];
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        unsigned char *tl = slot + s * A_TILE;
+        *reinterpret_cast<uint2 *>(tl + mn_off(4 * i4, k)) = make_uint2(wi[s][0] ^ 0x80008000u, wi[s][1] ^ 0x80008000u);
+        *reinterpret_cast<uint2 *>(tl + mn_off(64 + 4 * i4, k)) = make_uint2(wr[s][0], wr[s][1]);
+        *reinterpret_cast<uint2 *>(tl + mn_off(128 + 4 * i4, k)) = make_uint2(wi[s][0], wi[s][1]);
+    }
+}
+
+// digit tiles of Y_r and Y_i (K-major, row n = j): 8 bytes of 4 consecutive k per digit
+template <class T>
+__device__ __forceinline__ void split_y(const Raw<T> &r, unsigned char *slot, const int *tau, cx<T> w, int d, int t)
+{
+    constexpr int S = TcL<T>::S;
+    const int lane = t & 31, j = 8 * (t >> 5) + (lane & 7), k4 = lane >> 3;
+    unsigned wr[S][2], wi[S][2];
+    float pr[S], pi[S];
+    const float sc = j < d ? pow2f(-tau[j]) : 0.0f;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        float qr[S], qi[S];
+        const cx<T> y = split2(r.ya[kk], r.yb[kk], w);
+        digits(y.re, sc, qr);
+        digits(y.im, sc, qi);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            if (kk & 1) {
+                wr[s][kk >> 1] = pack2(pr[s], qr[s]);
+                wi[s][kk >> 1] = pack2(pi[s], qi[s]);
+            } else {
+                pr[s] = qr[s];
+                pi[s] = qi[s];
+            }
+        }
+    }
+    unsigned char *br = slot + S * A_TILE, *bi = br + S * B_TILE;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        *reinterpret_cast<uint2 *>(br + s * B_TILE + k_off(j, 4 * k4)) = make_uint2(wr[s][0], wr[s][1]);
+        *reinterpret_cast<uint2 *>(bi + s * B_TILE + k_off(j, 4 * k4)) = make_uint2(wi[s][0], wi[s][1]);
+    }
+}
+
+// value + v for a float v: one TwoSum of the high parts, lo parts added once
+__device__ __forceinline__ dd add_f(dd a, float v)
+{
+    const dd s = dd_two_sum(a.hi, v);
+    return dd_fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+// Fold the NG group accumulators of TMEM lanes 32 q + lane, columns
+// col .. col + 7: sum over g of acc_g 2^(8 (g - NG + 1)), every term an exact
+// FP32 value, top group first.  Double-float: the top three groups as a
+// compensated sum, the groups below (weights 2^-24 and less of the top one)
+// in FP32, joining once; FP32: plain FP32 adds.
+template <class T, int NG>
+__device__ __forceinline__ void fold8(unsigned tbase, T (&out)[8])
+{
+    float lo[8];
+#pragma unroll
+    for (int g = NG - 1; g >= 0; --g) {
+        unsigned r[8];
+        ld8(tbase + (unsigned)(g * 64), r);
+        const float w = __uint_as_float((unsigned)(127 - 8 * (NG - 1 - g)) << 23);  // 2^(8 (g - NG + 1))
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float v = __uint_as_float(r[c]) * w;
+            if constexpr (__is_same(T, dd)) {
+                if (g == NG - 1) out[c] = dd{v, 0.0f};
+                else if (g >= NG - 3) out[c] = add_f(out[c], v);
+                else if (g == NG - 4) lo[c] = v;
+                else lo[c] = __fadd_rn(lo[c], v);
+            } else {
+                if (g == NG - 1) out[c] = v;
+                else out[c] = __fadd_rn(out[c], v);
+            }
+        }
+    }
+    if constexpr (__is_same(T, dd) && NG > 3) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) out[c] = add_f(out[c], lo[c]);
+    }
+}
+
+__device__ __forceinline__ dd tc_scale(dd x, int e) { return {scale2(x.hi, e), scale2(x.lo, e)}; }
+__device__ __forceinline__ float tc_scale(float x, int e) { return scale2(x, e); }
+
+template <class T>
+__device__ __forceinline__ void st_cx(cx<T> *p, cx<T> v);
+template <>
+__device__ __forceinline__ void st_cx<dd>(cx<dd> *p, cx<dd> v)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v.re.hi, v.re.lo, v.im.hi, v.im.lo);
+}
+template <>
+__device__ __forceinline__ void st_cx<float>(cx<float> *p, cx<float> v)
+{
+    *reinterpret_cast<float2 *>(p) = make_float2(v.re, v.im);
+}
+
+template <class T>
+__global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *status)
+{
+    using L = TcL<T>;
+    constexpr int S = L::S, GMIN = L::GMIN, NG = L::NG, NSLOT = L::NSLOT, NTB = L::NTB;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    T *xch = reinterpret_cast<T *>(smem + L::OFF_XCH);  // [2][64][XLD]: C_r, C_i of 32 columns
+    int *sigb = reinterpret_cast<int *>(smem + L::OFF_SIG);  // [NB][64] row exponents, by pair counter mod NB
+    int *taub = sigb + 64 * L::NB;                           // [NB][64] column exponents
+    unsigned *bx = reinterpret_cast<unsigned *>(taub + 64 * L::NB), *by = bx + 64;
+    __shared__ __align__(8) unsigned long long bar_full[NSLOT], bar_empty[NSLOT], bar_tfull[NTB], bar_tempty[NTB],
+        bar_done;
+    __shared__ unsigned tslot;
+    __shared__ volatile int abort_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < NSLOT; ++s) {
+            mbar_init(smem_u32(&bar_full[s]), NSPLIT);
+            mbar_init(smem_u32(&bar_empty[s]), 1);
+        }
+        for (int b = 0; b < NTB; ++b) {
+            mbar_init(smem_u32(&bar_tfull[b]), 1);
+            mbar_init(smem_u32(&bar_tempty[b]), NEPI);
+        }
+        mbar_init(smem_u32(&bar_done), 1);
+        abort_flag = 0;
+        mbar_init_fence();
+    }
+    if (warp == WMMA) tmem_alloc(smem_u32(&tslot), TMEM_COLS);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = tslot;
+
+    const cx<T> *ZX = reinterpret_cast<const cx<T> *>(a.zx);
+    const cx<T> *ZY = reinterpret_cast<const cx<T> *>(a.zy);
+    cx<T> *ZC = reinterpret_cast<cx<T> *>(a.zc);
+    const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
+    const int d = a.r;
+    const int64_t E = (int64_t)d * d, M = a.M;
+    bool failed = false;
+    auto give_up = [&]() {
+        failed = true;
+        abort_flag = 1;
+        if (status) atomicExch(status, 6);
+    };
+
+    if (warp < WEPI0) {
+        // ------------------------------------------------------------ split
+        const int t = tid;
+        int it = 0;  // chunk counter: slot it % NSLOT, use it / NSLOT
+        int pl = 0;  // pair counter (mod NB selects the exponent buffers)
+        Raw<T> raw;
+        for (int64_t p = blockIdx.x; p < a.npairs; p += gridDim.x, ++pl) {
+            const int64_t f = p, gL = M - p, gZ = gL & (M - 1);
+            const int nfreq = (gL == f) ? 1 : 2;  // p = M/2 pairs with itself
+            const cx<T> wf = tw[f << (a.tw_log - a.logM - 1)];
+            const cx<T> wg = c_neg(c_conj(wf));
+            int *sig = sigb + 64 * (pl % L::NB), *tau = taub + 64 * (pl % L::NB);
+            // ---- bounds over both frequencies: |Xh(f)|, |Xh(g)| <= |Z(f)|_1 + |Z(g)|_1 entrywise
+            if (t < 128) bx[t] = 0u;
+            if (bar_or(BAR_SPLIT, NSPLIT, failed || abort_flag)) break;
+            {
+                const int k = t & 63;
+                float my = 0.0f;
+#pragma unroll 4
+                for (int n = 0; n < 16; ++n) {
+                    const int i = (t >> 6) + 4 * n;  // X row (one row per warp pair) and Y row
+                    float mx = 0.0f;
+                    if (i < d && k < d) {
+                        const int64_t e = (int64_t)i * d + k;
+                        const cx<T> xa = ldg_cx(ZX + f * E + e), xb = ldg_cx(ZX + gZ * E + e);
+                        const cx<T> ya = ldg_cx(ZY + f * E + e), yb = ldg_cx(ZY + gZ * E + e);
+                        mx = fabsf(hi_part(xa.re)) + fabsf(hi_part(xa.im)) + fabsf(hi_part(xb.re)) +
+                             fabsf(hi_part(xb.im));
+                        my = fmaxf(my, fabsf(hi_part(ya.re)) + fabsf(hi_part(ya.im)) + fabsf(hi_part(yb.re)) +
+                                           fabsf(hi_part(yb.im)));
+                    }
+                    const unsigned wmx = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));  // nonnegative: bits order
+                    if (lane == 0) atomicMax(&bx[i], wmx);
+                }
+                atomicMax(&by[k], __float_as_uint(my));
+            }
+            bar_sync(BAR_SPLIT, NSPLIT);
+            if (t < 64) {
+                // 2 Xh and 2 Yh are split (split2): bound 2 |.|
+                sig[t] = scale_exp(2.0f * __uint_as_float(bx[t]));
+                tau[t] = scale_exp(2.0f * __uint_as_float(by[t]));
+            }
+            bar_sync(BAR_SPLIT, NSPLIT);
+            // ---- chunks of both frequencies
+            const int nch = nfreq * NCH;
+            load_x(raw, ZX, f, gZ, d, 0, t);
+            load_y(raw, ZY, f, gZ, d, 0, t);
+            for (int c = 0; c < nch; ++c, ++it) {
+                const int phase = c / NCH;
+                const cx<T> w = phase == 0 ? wf : wg;
+                const int slot = it % NSLOT, use = it / NSLOT;
+                unsigned char *sp = smem + slot * L::SLOT;
+                if (!failed && use > 0 && (abort_flag || !mbar_wait(smem_u32(&bar_empty[slot]), (use - 1) & 1)))
+                    give_up();
+                const int cn = c + 1;  // next chunk of this pair
+                const int64_t na = (cn / NCH) == 0 ? f : gZ, nb = (cn / NCH) == 0 ? gZ : f;
+                if (!failed) split_x<T>(raw, sp, sig, w, d, t);
+                if (cn < nch) load_x(raw, ZX, na, nb, d, (cn % NCH) * KC, t);
+                if (!failed) split_y<T>(raw, sp, tau, w, d, t);
+                if (cn < nch) load_y(raw, ZY, na, nb, d, (cn % NCH) * KC, t);
+                if (!failed) {
+                    fence_async_smem();  // digit tiles visible to the tensor cores
+                    mbar_arrive(smem_u32(&bar_full[slot]));
+                }
+            }
+        }
+    } else if (warp < WMMA) {
+        // --------------------------------------------------------- epilogue
+        const int et = tid - WEPI0 * 32;
+        const int q = warp & 3;  // TMEM lanes 32 q .. 32 q + 31
+        int fi = 0, pl = 0;
+        for (int64_t p = blockIdx.x; p < a.npairs; p += gridDim.x, ++pl) {
+            const int64_t f = p, gL = M - p, gZ = gL & (M - 1);
+            const int nfreq = (gL == f) ? 1 : 2;
+            const bool two = (gZ != f);
+            const cx<T> wf = tw[f << (a.tw_log - a.logM - 1)];
+            const cx<T> wg = c_neg(c_conj(wf));
+            const int *sig = sigb + 64 * (pl % L::NB), *tau = taub + 64 * (pl % L::NB);
+            bool stop = false;
+            for (int phase = 0; phase < nfreq; ++phase, ++fi) {
+                const int b = fi % NTB, ub = fi / NTB;
+                bool ok = !failed && !abort_flag && mbar_wait(smem_u32(&bar_tfull[b]), ub & 1);
+                if (bar_or(BAR_EPI, NEPI, !ok)) {
+                    if (!failed) give_up();
+                    stop = true;
+                    break;
+                }
+                fence_after();
+                const unsigned tb = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(b * NG * 64);
+                T *xr = xch + ((q >> 1) * 64 + 32 * (q & 1) + lane) * XLD;  // part q >> 1: C_r or C_i rows
+                T cv[32];
+                // columns 0..31 to the transpose, columns 32..63 kept in registers
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        T o8[8];
+                        fold8<T, NG>(tb + (unsigned)(32 * hh + 8 * m), o8);
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            if (hh == 0) xr[8 * m + c] = o8[c];
+                            else cv[8 * m + c] = o8[c];
+                        }
+                    }
+                }
+                fence_before();
+                mbar_arrive(smem_u32(&bar_tempty[b]));  // accumulators read: the next MMAs may overwrite them
+                // two rounds of 32 columns, lanes along j for coalesced global accesses
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    if (r == 1) {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) xr[c] = cv[c];
+                    }
+                    bar_sync(BAR_EPI, NEPI);
+                    const int jl = et & 31, j = 32 * r + jl;
+#pragma unroll 2
+                    for (int m = 0; m < 16; ++m) {
+                        const int i = (et >> 5) + 4 * m;
+                        if (i < d && j < d) {
+                            const int ex = sig[i] + tau[j] - 18;  // 2^(sigma + tau) / 4 x the fold's 2^-16
+                            const cx<T> v = {tc_scale(xch[i * XLD + jl], ex), tc_scale(xch[(64 + i) * XLD + jl], ex)};
+                            cx<T> *zf = ZC + f * E + (int64_t)i * d + j;
+                            if (nfreq == 1) {
+                                st_cx(zf, merge_real(v, v, c_conj(wf)));  // p = M/2: C(g) = C(f)
+                            } else if (phase == 0) {
+                                st_cx(zf, v);  // C(f), merged once C(g) is known (same thread)
+                            } else {
+                                const cx<T> cf = *zf;
+                                st_cx(zf, merge_real(cf, v, c_conj(wf)));
+                                if (two) st_cx(ZC + gZ * E + (int64_t)i * d + j, merge_real(v, cf, c_conj(wg)));
+                            }
+                        }
+                    }
+                    bar_sync(BAR_EPI, NEPI);  // transpose read before it is rewritten
+                }
+            }
+            if (stop) break;
+        }
+    } else if (lane == 0) {  // the MMA warp's other lanes go straight to the final barrier (below)
+        // -------------------------------------------------------------- MMA
+        int it = 0, fi = 0;
+        bool issued = false;
+        for (int64_t p = blockIdx.x; p < a.npairs && !failed; p += gridDim.x) {
+            const int64_t gL = M - p;
+            const int nfreq = (gL == p) ? 1 : 2;
+            for (int phase = 0; phase < nfreq && !failed; ++phase, ++fi) {
+                const int b = fi % NTB, ub = fi / NTB;
+                if (ub > 0 && (abort_flag || !mbar_wait(smem_u32(&bar_tempty[b]), (ub - 1) & 1))) {
+                    give_up();
+                    break;
+                }
+                fence_after();
+                const unsigned dbase = tmem + (unsigned)(b * NG * 64);
+                for (int c = 0; c < NCH; ++c, ++it) {
+                    const int slot = it % NSLOT, use = it / NSLOT;
+                    if (abort_flag || !mbar_wait(smem_u32(&bar_full[slot]), use & 1)) {
+                        give_up();
+                        break;
+                    }
+                    fence_after();
+                    const unsigned sa = smem_u32(smem + slot * L::SLOT);
+                    const unsigned sbr = sa + S * A_TILE, sbi = sbr + S * B_TILE;
+#pragma unroll
+                    for (int g = GMIN; g <= 2 * (S - 1); ++g) {
+                        const unsigned dcol = dbase + (unsigned)(g - GMIN) * 64u;
+                        unsigned acc = c == 0 ? 0u : 1u;
+#pragma unroll
+                        for (int s = (g - (S - 1) > 0 ? g - (S - 1) : 0); s <= (g < S - 1 ? g : S - 1); ++s) {
+                            const int tt = g - s;
+                            const unsigned as = sa + s * A_TILE;
+                            mma<IDESC>(dcol, desc<SBO>(as + 8 * SBO), desc<SBO>(sbr + tt * B_TILE), acc);
+                            acc = 1u;
+                            mma<IDESC>(dcol, desc<SBO>(as), desc<SBO>(sbi + tt * B_TILE), 1u);
+                        }
+                    }
+                    issued = true;
+                    commit(smem_u32(&bar_empty[slot]));  // the slot is free once these MMAs completed
+                }
+                if (failed) break;
+                commit(smem_u32(&bar_tfull[b]));  // the frequency's accumulators are complete
+            }
+        }
+        if (issued) {
+            commit(smem_u32(&bar_done));
+            if (!mbar_wait(smem_u32(&bar_done), 0)) give_up();  // every MMA finished before the TMEM is freed
+        }
+    }
+    if (warp == WMMA) __syncwarp();  // lane 0 rejoins its warp before the CTA-wide barrier
+
+    fence_before();
+    __syncthreads();
+    if (warp == WMMA) {
+        fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+int sm_count()
+{
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (nsm <= 0) nsm = 1;
+    }
+    return nsm;
+}
+
+template <class T>
+cudaError_t tcp_run(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
+                    int *status, cudaStream_t st, int kclass)
+{
+    PairArgs a{};
+    a.zx = zx; a.zy = zy; a.zc = zc; a.tw = tw; a.tw_log = tw_log; a.M = M;
+    int l = 0;
+    while (((int64_t)1 << l) < M) ++l;
+    a.logM = l;
+    a.npairs = M >= 2 ? M / 2 + 1 : 1;
+    a.r = a.m = a.c = d;
+    const unsigned grid = (unsigned)std::min<int64_t>(a.npairs, sm_count());
+    const double bytes = (double)M * 3.0 * d * d * sizeof(cx<T>);
+    const double flops = 8.0 * d * d * d * (double)(M + 1);
+    mrc_prof_pre(kclass, st);
+    tcp_kernel<T><<<grid, NTHREADS, TcL<T>::SMEM, st>>>(a, status);
+    mrc_prof_post(kclass, st, bytes, flops);
+    return cudaGetLastError();
+}
+
+} // namespace
+
+bool mrc_tcp_supported(int r, int m, int c) { return r == m && m == c && r >= 32 && r <= 64; }
+
+cudaError_t mrc_tcp_init(void)
+{
+    cudaError_t e = cudaFuncSetAttribute(tcp_kernel<dd>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcL<dd>::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tcp_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcL<float>::SMEM);
+    return e;
+}
+
+cudaError_t mrc_pairmul_dd_tcp(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
+                               int *status, cudaStream_t st)
+{
+    return tcp_run<dd>(zx, zy, zc, M, d, tw, tw_log, status, st, 6);
+}
+
+cudaError_t mrc_pairmul_f32_tcp(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
+                                int *status, cudaStream_t st)
+{
+    return tcp_run<float>(zx, zy, zc, M, d, tw, tw_log, status, st, 5);
+}

@@ -9,8 +9,6 @@
 // the critical path, so that their event durations include time spent
 // waiting for SMs) are counted but not timed.  Not thread safe: profile one
 // host thread at a time.
-#include <stdlib.h>
-
 #include <atomic>
 #include <vector>
 
@@ -36,17 +34,6 @@ namespace {
 cudaStream_t g_untimed = nullptr;
 }
 void mrc_prof_set_untimed(cudaStream_t st) { g_untimed = st; }
-
-namespace {
-int *g_status_word = nullptr;
-}
-int *mrc_status_word(void) { return g_status_word; }
-void mrc_set_status_word(int *p) { g_status_word = p; }
-bool mrc_fft_tma_enabled(void)
-{
-    const char *v = getenv("MRC_FFT_TMA");
-    return v && v[0] == '1';
-}
 
 
 void mrc_prof_pre(int kclass, cudaStream_t st)

@@ -80,9 +80,10 @@ def load():
         lib.mrc_occupation.argtypes = [P, I, I64, P, P, P, I, P, P]
         lib.mrc_reward.argtypes = [P, I, I, I64, P, P, P, I, P]
         lib.mrc_renewal_visits.argtypes = [P, I, I64, P, P, P, I, P, P]
+        lib.mrc_selftest_timeout.argtypes = [P, I, P]
         for name in ("mrc_create", "mrc_destroy", "mrc_sync_status", "mrc_inverse", "mrc_inverse_batched",
                      "mrc_residual", "mrc_transition", "mrc_first_entrance", "mrc_occupation", "mrc_reward",
-                     "mrc_renewal_visits"):
+                     "mrc_renewal_visits", "mrc_selftest_timeout"):
             getattr(lib, name).restype = I
         _lib = lib
         return lib
@@ -286,6 +287,13 @@ def renewal_visits(psi, alpha, B, stream=None):
     _check(load().mrc_renewal_visits(context(psi.device.index), d, N, _ptr(psi), _ptr(alpha), Bv, len(B), _ptr(out),
                                      _stream(stream)), "mrc_renewal_visits")
     return out
+
+
+def selftest_timeout(spins=256, stream=None):
+    """Enqueue the bounded-wait self-test (mrc_selftest_timeout): a device
+    wait on a barrier nothing arrives on gives up after `spins` rounds and
+    leaves MRC_ERR_TIMEOUT in the context's status word."""
+    _check(load().mrc_selftest_timeout(context(), int(spins), _stream(stream)), "mrc_selftest_timeout")
 
 
 def sync_status(stream=None):

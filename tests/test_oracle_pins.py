@@ -254,6 +254,38 @@ def test_two_sided_inverse_and_residuals():
         np.testing.assert_allclose(oracle.residual_left_at(A, L, k), rl[k], atol=1e-16)
 
 
+def test_residual_entries_vs_numpy_polynomial_products():
+    """rho_L(k)_ij = delta - sum_u (A_iu * psi_uj)(k) and rho_R(k)_ij =
+    delta - sum_u (psi_iu * A_uj)(k), each 1-D convolution by np.convolve;
+    integer entries make both sides exact.  A transposed operand or a
+    dropped l = 0 term would fail here."""
+    rng = np.random.default_rng(77)
+    d, N = 3, 40
+    A = rng.integers(-5, 6, size=(N, d, d)).astype(np.float64)
+    P = rng.integers(-5, 6, size=(N, d, d)).astype(np.float64)
+    for k in (0, 1, 17, N - 1):
+        for i in range(d):
+            for j in range(d):
+                dl = 1.0 if (k == 0 and i == j) else 0.0
+                wl = dl - sum(np.convolve(A[:, i, u], P[:, u, j])[k] for u in range(d))
+                wr = dl - sum(np.convolve(P[:, i, u], A[:, u, j])[k] for u in range(d))
+                assert oracle.residual_left_entry(A, P, k, i, j) == wl
+                assert oracle.residual_right_entry(A, P, k, i, j) == wr
+
+
+def test_norm1_frob_vs_numpy():
+    """||X||_{1,N} with the Frobenius norm per coefficient: the sum over k of
+    numpy's matrix Frobenius norm (a missing square root, or squares summed
+    over k, would fail)."""
+    rng = np.random.default_rng(78)
+    X = rng.standard_normal((37, 4, 3))
+    ref = sum(np.linalg.norm(X[k], "fro") for k in range(X.shape[0]))
+    assert abs(oracle.norm1_frob(X) - ref) <= 1e-13 * ref
+    Y = np.zeros((5, 2, 2))
+    Y[2] = [[3.0, 0.0], [0.0, 4.0]]
+    assert oracle.norm1_frob(Y) == 5.0
+
+
 def test_prefix_exactness():
     """Proposition 2.3: the first N' coefficients depend only on A(0..N'-1)."""
     q, _ = synth.weibull_model(4, 200, seed=8)

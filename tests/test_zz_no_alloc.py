@@ -35,18 +35,41 @@ def _run_noalloc(lib, A):
     return st, psi
 
 
-def test_noalloc_matches_allocating_inverse_twice(libs):
+def test_noalloc_matches_oracle_and_allocating_inverse_twice(libs):
+    """Two calls in a row with different shapes, each against the FP64 oracle
+    and against mrc_inverse.  After one warm-up call per shape (the first call
+    on a device maps the library's fixed array and kernels), the calls change
+    neither the device's free memory nor torch's allocations: nothing is
+    allocated."""
+    import oracle
     lib, mrc = libs
     cases = [(16, 2048, 31), (5, 1000, 32)]
+    data = []
     for d, N, seed in cases:
         q, _ = synth.weibull_model(d, N, seed=seed)
-        A = torch.from_numpy(synth.identity_minus(q)).cuda()
-        ref = mrc.inverse(A, prec="fp64")
-        st, psi = _run_noalloc(lib, A)
-        assert st == 0
+        A_h = synth.identity_minus(q)
+        A = torch.from_numpy(A_h).cuda()
+        data.append((A_h, A, mrc.inverse(A, prec="fp64"), oracle.inverse_left(A_h)))
+    psis = [torch.full_like(A, float("nan")) for _, A, _, _ in data]
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def call(A, psi):
+        N, d, _ = A.shape
+        return lib.mrc_inverse_noalloc(d, N, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(psi.data_ptr()), stream)
+
+    for (_, A, _, _), psi in zip(data, psis):  # warm-up: initialisation on this device
+        assert call(A, psi) == 0
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    for (_, A, ref_dev, ref), psi in zip(data, psis):
+        psi.fill_(float("nan"))
+        assert call(A, psi) == 0
         torch.cuda.synchronize()
-        err = (psi - ref).abs().max().item()
-        assert err <= TOL64, (d, N, err)
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert torch.cuda.memory_allocated() == alloc0
+        got = psi.cpu().numpy()
+        assert np.abs(got - ref).max() <= TOL64
+        assert (psi - ref_dev).abs().max().item() <= TOL64
 
 
 def test_noalloc_rejects_oversized_request(libs):
