@@ -69,7 +69,8 @@ void mrc_prof_set_untimed(cudaStream_t st);
 namespace {
 
 struct PrecOps {
-    cudaError_t (*fft)(const FftSrc &, const FftDst &, int64_t, int, int, void *, const void *, int, cudaStream_t);
+    cudaError_t (*fft)(const FftSrc &, const FftDst &, int64_t, int, int, void *, const void *, int, cudaStream_t,
+                       int);
     cudaError_t (*pairmul)(const void *, const void *, void *, int64_t, int, int, int, const void *, int, cudaStream_t);
     cudaError_t (*pairmul_cfg)(const void *, const void *, void *, int64_t, int, int, int, int, const void *, int,
                                cudaStream_t);
@@ -263,6 +264,70 @@ int tuned_choice(mrc_ctx *cx, int prec, const void *zx, const void *zy, void *zc
     return pick;
 }
 
+// Autotuned FFT plan for (precision, direction, source and destination
+// kinds, entries, log2 M): the candidate radix splits (each pass at most
+// 2^10 points) with the default or four entries per CTA, each run once to
+// warm up and twice under CUDA events on the call's own buffers and stream,
+// the fastest kept in the context.  Transforms whose destination accumulates
+// (DST_REAL64_ADD) are not re-run and keep the built-in plan, as do calls
+// while a graph is being captured.
+uint64_t fft_key(int prec, const FftSrc &sx, const FftDst &dx, int64_t M, int E, int dir)
+{
+    int l = 0;
+    while (((int64_t)1 << l) < M) ++l;
+    return ((uint64_t)1 << 62) | ((uint64_t)prec << 56) | ((uint64_t)(dir > 0) << 55) | ((uint64_t)sx.mode << 52) |
+           ((uint64_t)dx.mode << 48) | ((uint64_t)E << 8) | (uint64_t)l;
+}
+
+int fft_plan_choice(mrc_ctx *cx, int prec, const FftSrc &sx, const FftDst &dx, int64_t M, int E, int dir,
+                    void *scratch, const void *tw, cudaStream_t st)
+{
+    if (!cx || !cx->autotune) return -1;
+    const uint64_t key = fft_key(prec, sx, dx, M, E, dir);
+    auto it = cx->tune.find(key);
+    if (it != cx->tune.end()) return it->second;
+    if (cx->capturing || dx.mode == DST_REAL64_ADD || (cx->aux && st == cx->aux)) return -1;
+    int l = 0;
+    while (((int64_t)1 << l) < M) ++l;
+    std::vector<int> cands;
+    const bool ec4_alt = (prec == PREC_F32 ? E >= 16 : E >= 8);  // four entries per CTA differ from the default
+    if (l <= 10) {
+        cands.push_back(0);
+        if (ec4_alt) cands.push_back(256);
+    } else {
+        for (int a = std::max(1, l - 10); a <= std::min(10, l - 1); ++a) {
+            cands.push_back(a);
+            if (ec4_alt) cands.push_back(a | 256);
+        }
+    }
+    float best = 1e30f;
+    int pick = -1;
+    for (int pl : cands) {
+        if (OPS[prec].fft(sx, dx, M, E, dir, scratch, tw, MRC_TW_LOG, st, pl) != cudaSuccess) continue;
+        cudaEventRecord(cx->ev0, st);
+        OPS[prec].fft(sx, dx, M, E, dir, scratch, tw, MRC_TW_LOG, st, pl);
+        OPS[prec].fft(sx, dx, M, E, dir, scratch, tw, MRC_TW_LOG, st, pl);
+        cudaEventRecord(cx->ev1, st);
+        if (cudaEventSynchronize(cx->ev1) != cudaSuccess) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, cx->ev0, cx->ev1);
+        if (ms < best) { best = ms; pick = pl; }
+    }
+    cudaGetLastError();
+    if (pick >= 0) {
+        cx->tune[key] = pick;
+        cx->tune_dirty = true;
+    }
+    return pick;
+}
+
+cudaError_t fft_any(mrc_ctx *cx, int prec, const FftSrc &sx, const FftDst &dx, int64_t M, int E, int dir,
+                    void *scratch, const void *tw, cudaStream_t st)
+{
+    const int plan = fft_plan_choice(cx, prec, sx, dx, M, E, dir, scratch, tw, st);
+    return OPS[prec].fft(sx, dx, M, E, dir, scratch, tw, MRC_TW_LOG, st, plan);
+}
+
 // The per-frequency product of one precision: the autotuned choice when the
 // call asked for tuning, else the tensor-core digit kernels for square
 // double-float products with 32 <= d <= 512 and square FP32 products with
@@ -309,18 +374,24 @@ mrc_status conv_product(mrc_ctx *c, Arena &ar, int prec, const double *X, int64_
     FftSrc sy{y_mode, Y, 0, std::min(NY, N), (int)EY, 0};
     FftDst dx{DST_CPLX, bX, (int)EX, 0, 0, 0, 1.0, 0};
     FftDst dy{DST_CPLX, bY, (int)EY, 0, 0, 0, 1.0, 0, y_hi};
-    if (!preX) CK(op.fft(sx, dx, Mr, (int)EX, -1, bT, tw, MRC_TW_LOG, st));
-    CK(op.fft(sy, dy, Mr, (int)EY, -1, bT, tw, MRC_TW_LOG, st));
+    if (!preX) CK(fft_any(c, prec, sx, dx, Mr, (int)EX, -1, bT, tw, st));
+    CK(fft_any(c, prec, sy, dy, Mr, (int)EY, -1, bT, tw, st));
     if (diag) CK(op.pairdiag(bX, bY, bC, Mr, r, cc, tw, MRC_TW_LOG, st));
     else CK(pairmul_any(c, prec, bX, bY, bC, Mr, r, m, cc, tw, st));
     FftSrc sc{SRC_CPLX, bC, 0, Mr, (int)EC, 0};
     FftDst dc{out_mode >= 0 ? out_mode : (add ? DST_REAL64_ADD : DST_REAL64), out, (int)EC, 0, N, 0,
               sign / (double)Mr, eye_d, nullptr, out_base};
-    CK(op.fft(sc, dc, Mr, (int)EC, +1, bT, tw, MRC_TW_LOG, st));
+    CK(fft_any(c, prec, sc, dc, Mr, (int)EC, +1, bT, tw, st));
     return MRC_OK;
 }
 
-// The level product through the context: autotuned or built-in choice.
+// The level transforms and products through the context: autotuned or built-in choices.
+cudaError_t level_fft(void *user, int prec, const FftSrc &sx, const FftDst &dx, int64_t M, int E, int dir,
+                      void *scratch, const void *tw, int, cudaStream_t st)
+{
+    return fft_any((mrc_ctx *)user, prec, sx, dx, M, E, dir, scratch, tw, st);
+}
+
 cudaError_t level_product(void *user, int prec, const void *zx, const void *zy, void *zc, int64_t M, int d,
                           const void *tw, int, cudaStream_t st)
 {
@@ -343,8 +414,8 @@ mrc_status newton_levels(mrc_ctx *c, Arena &ar, int prec, int d, int64_t N, cons
     b.b1 = ar.take((size_t)Mmax * E * op.cxb);
     b.b2 = ar.take((size_t)Mmax * E * op.cxb);
     b.bt = ar.take(mrc_fft_scratch_elems(Mmax, E) * op.cxb);
-    return (mrc_status)mrc_newton_levels(prec, d, N, A, psi, m0, b, c->tw[prec], MRC_TW_LOG, level_product, c, st,
-                                         rw, A32, psi32, levels);
+    return (mrc_status)mrc_newton_levels(prec, d, N, A, psi, m0, b, c->tw[prec], MRC_TW_LOG, level_fft,
+                                         level_product, c, st, rw, A32, psi32, levels);
 }
 
 bool valid_dN(int d, int64_t N) { return d >= 1 && d <= 512 && N >= 1 && N <= ((int64_t)1 << 20); }
@@ -386,7 +457,7 @@ mrc_status inverse_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A
         if (rw) CK(rw->wait(sa, N));
         FftSrc sx{SRC_REAL64, A, 0, N, (int)E, 0};
         FftDst dx{DST_CPLX, ahat, (int)E, 0, 0, 0, 1.0, 0};
-        CK(OPS[PREC_DD].fft(sx, dx, Mr, (int)E, -1, ascr, c->tw[PREC_DD], MRC_TW_LOG, sa));
+        CK(fft_any(c, PREC_DD, sx, dx, Mr, (int)E, -1, ascr, c->tw[PREC_DD], sa));
         if (split) CK(cudaEventRecord(c->ev_join, c->aux));
     }
     // mixed: psi_0 is kept in binary32 (every entry the FP32 levels write is
@@ -524,7 +595,7 @@ void tune_load(mrc_ctx *cx)
     unsigned long long k;
     int ch;
     while (fscanf(f, "%llu %d", &k, &ch) == 2)
-        if (ch >= 0 && ch <= 3) cx->tune[(uint64_t)k] = ch;
+        if (ch >= 0 && ch <= ((k >> 62) ? 511 : 3)) cx->tune[(uint64_t)k] = ch;  // FFT plans / product choices
     fclose(f);
 }
 
@@ -559,10 +630,9 @@ int64_t mrc_newton_maxM(int d, int64_t N)
 // Each level m -> min(2m, N) follows Eq. (newton) with the middle product
 // (L = 2m): E = A*B (cyclic), R = -E[m, 2m), B[m, 2m) = (B*R)[0, m).
 int mrc_newton_levels(int prec, int d, int64_t N, const double *A, double *psi, int64_t m0, const NewtonBufs &b,
-                      const void *tw, int tw_log, mrc_level_product_fn product, void *user, cudaStream_t st,
-                      const RowWait *rw, float *A32, float *psi32, int *levels)
+                      const void *tw, int tw_log, mrc_level_fft_fn fft, mrc_level_product_fn product, void *user,
+                      cudaStream_t st, const RowWait *rw, float *A32, float *psi32, int *levels)
 {
-    const PrecOps &op = OPS[prec];
     const int E = d * d;
     const bool f32 = A32 && psi32;
     int64_t conv = 0;  // rows of A32 converted so far
@@ -578,19 +648,19 @@ int mrc_newton_levels(int prec, int d, int64_t N, const double *A, double *psi, 
         FftSrc sB{f32 ? SRC_REAL32 : SRC_REAL64, f32 ? (const void *)psi32 : psi, 0, m, E, 0};
         FftDst to0{DST_CPLX, b.b0, E, 0, 0, 0, 1.0, 0};
         FftDst to1{DST_CPLX, b.b1, E, 0, 0, 0, 1.0, 0};
-        CK(op.fft(sA, to0, M, E, -1, b.bt, tw, tw_log, st));                  // A-hat
-        CK(op.fft(sB, to1, M, E, -1, b.bt, tw, tw_log, st));                  // B-hat
+        CK(fft(user, prec, sA, to0, M, E, -1, b.bt, tw, tw_log, st));        // A-hat
+        CK(fft(user, prec, sB, to1, M, E, -1, b.bt, tw, tw_log, st));        // B-hat
         CK(product(user, prec, b.b0, b.b1, b.b2, M, d, tw, tw_log, st));      // (A B)-hat
         FftSrc s2{SRC_CPLX, b.b2, 0, M, E, 0};
         FftDst t0s{DST_CPLX, b.b0, E, 0, 0, 0, 1.0 / (double)M, 0};
-        CK(op.fft(s2, t0s, M, E, +1, b.bt, tw, tw_log, st));                  // A*B, packed time
+        CK(fft(user, prec, s2, t0s, M, E, +1, b.bt, tw, tw_log, st));        // A*B, packed time
         FftSrc sR{SRC_CPLX, b.b0, M / 2, M / 2, E, 1};                         // R = -(A*B)[m, 2m)
         FftDst to2{DST_CPLX, b.b2, E, 0, 0, 0, 1.0, 0};
-        CK(op.fft(sR, to2, M, E, -1, b.bt, tw, tw_log, st));                  // R-hat
+        CK(fft(user, prec, sR, to2, M, E, -1, b.bt, tw, tw_log, st));        // R-hat
         CK(product(user, prec, b.b1, b.b2, b.b0, M, d, tw, tw_log, st));      // (B R)-hat
         FftSrc s0{SRC_CPLX, b.b0, 0, M, E, 0};
         FftDst toP{f32 ? DST_REAL32 : DST_REAL64, f32 ? (void *)psi32 : psi, E, 0, m2 - m, m, 1.0 / (double)M, 0};
-        CK(op.fft(s0, toP, M, E, +1, b.bt, tw, tw_log, st));                  // B[m, m2)
+        CK(fft(user, prec, s0, toP, M, E, +1, b.bt, tw, tw_log, st));        // B[m, m2)
     }
     if (levels) *levels = lv;
     return MRC_OK;

@@ -56,15 +56,32 @@ inline int fft_plan(int logM, int *logRs)
     return 2;
 }
 
+// The passes and entries per CTA of `plan` (see mrc_internal.h), or the
+// built-in ones when the plan does not fit logM.
+inline int fft_plan_apply(int logM, int plan, int *logRs, bool *ec4)
+{
+    *ec4 = plan >= 0 && ((plan >> 8) & 1);
+    const int a = plan >= 0 ? (plan & 31) : -1;
+    if (a == 0 && logM <= 10) { logRs[0] = logM; return 1; }
+    if (a >= 1 && a <= 10 && logM - a >= 1 && logM - a <= 10) {
+        logRs[0] = a;
+        logRs[1] = logM - a;
+        return 2;
+    }
+    *ec4 = false;
+    return fft_plan(logM, logRs);
+}
+
 template <class T>
 cudaError_t fft_run(const FftSrc &src, const FftDst &dst, int64_t M, int E, int dir, void *scratch,
-                    const void *tw, int tw_log, cudaStream_t st)
+                    const void *tw, int tw_log, cudaStream_t st, int plan)
 {
     const int logM = ilog2_i64(M);
     if (((int64_t)1 << logM) != M || logM > 20 || logM + 1 > tw_log) return cudaErrorInvalidValue;
     int logRs[2];
-    const int np = fft_plan(logM, logRs);
-    const int ec = pick_ec<T>(E);
+    bool ec4 = false;
+    const int np = fft_plan_apply(logM, plan, logRs, &ec4);
+    const int ec = ec4 ? 4 : pick_ec<T>(E);
     const int sld = E;  // scratch row length (complex elements)
     int logNs = 0;
     for (int ps = 0; ps < np; ++ps) {
@@ -234,9 +251,9 @@ cudaError_t init_run()
         return t;                                                                                           \
     }                                                                                                       \
     cudaError_t mrc_fft_##SUF(const FftSrc &src, const FftDst &dst, int64_t M, int E, int dir, void *scratch, \
-                              const void *tw, int tw_log, cudaStream_t st)                                  \
+                              const void *tw, int tw_log, cudaStream_t st, int plan)                        \
     {                                                                                                       \
-        return fft_run<T>(src, dst, M, E, dir, scratch, tw, tw_log, st);                                    \
+        return fft_run<T>(src, dst, M, E, dir, scratch, tw, tw_log, st, plan);                              \
     }                                                                                                       \
     cudaError_t mrc_pairmul_##SUF(const void *zx, const void *zy, void *zc, int64_t M, int r, int m, int c,   \
                                   const void *tw, int tw_log, cudaStream_t st)                              \

@@ -81,9 +81,15 @@ void mrc_prof_pre(int kclass, cudaStream_t st);
 void mrc_prof_post(int kclass, cudaStream_t st, double bytes, double flops);
 
 // Per-precision launchers (k_f64.cu, k_f32.cu, k_dd.cu).
+// An FFT plan: -1 the built-in one (one pass up to 2^10 points, else two
+// passes of 2^ceil(l/2) and 2^floor(l/2); the default entries per CTA), or
+// plan bits 0-4 = log2 of the first pass's radix (0: one pass), bit 8 = four
+// entries per CTA.  Plans that do not fit the transform fall back to the
+// built-in one.
 #define MRC_DECLARE_PREC(SUF)                                                                         \
     cudaError_t mrc_fft_##SUF(const FftSrc &src, const FftDst &dst, int64_t M, int E, int dir,        \
-                              void *scratch, const void *tw, int tw_log, cudaStream_t st);            \
+                              void *scratch, const void *tw, int tw_log, cudaStream_t st,             \
+                              int plan = -1);                                                         \
     cudaError_t mrc_pairmul_##SUF(const void *zx, const void *zy, void *zc, int64_t M, int r, int m,  \
                                   int c, const void *tw, int tw_log, cudaStream_t st);                \
     cudaError_t mrc_pairmul_cfg_##SUF(const void *zx, const void *zy, void *zc, int64_t M, int r,     \
@@ -140,6 +146,9 @@ struct RowWait {
         return n ? cudaStreamWaitEvent(s, ev[n - 1], 0) : cudaSuccess;
     }
 };
+// The transform a level uses (an mrc_fft_<prec> call, perhaps with a tuned plan)
+typedef cudaError_t (*mrc_level_fft_fn)(void *user, int prec, const FftSrc &src, const FftDst &dst, int64_t M, int E,
+                                        int dir, void *scratch, const void *tw, int tw_log, cudaStream_t st);
 // The per-frequency product a level uses: zc = zx * zy at the M/2 + 1
 // frequency pairs of (PREC_F64 or PREC_F32) spectra of length M, d x d.
 typedef cudaError_t (*mrc_level_product_fn)(void *user, int prec, const void *zx, const void *zy, void *zc,
@@ -155,8 +164,8 @@ struct NewtonBufs {
 // binary32.  rw (nullable) delays each level until its rows of A arrived.
 // Returns 0 or 4 (a CUDA error, printed); *levels (nullable) = levels run.
 int mrc_newton_levels(int prec, int d, int64_t N, const double *A, double *psi, int64_t m0, const NewtonBufs &b,
-                      const void *tw, int tw_log, mrc_level_product_fn product, void *user, cudaStream_t st,
-                      const RowWait *rw, float *A32, float *psi32, int *levels);
+                      const void *tw, int tw_log, mrc_level_fft_fn fft, mrc_level_product_fn product, void *user,
+                      cudaStream_t st, const RowWait *rw, float *A32, float *psi32, int *levels);
 
 // misc.cu
 cudaError_t mrc_gauss_jordan(const double *A0, double *out, double *work, int d, int *status, cudaStream_t st);

@@ -50,6 +50,14 @@ constexpr size_t kWorkOff = kTwOff + kTwBytes;
 
 int64_t max_level(int d, int64_t N) { return mrc_newton_maxM(d, N); }
 
+// the level transforms and products: the built-in FFT plans and the default
+// FP64 product kernel (no autotuning here)
+cudaError_t fft_f64(void *, int, const FftSrc &sx, const FftDst &dx, int64_t M, int E, int dir, void *scratch,
+                    const void *tw, int tw_log, cudaStream_t st)
+{
+    return mrc_fft_f64(sx, dx, M, E, dir, scratch, tw, tw_log, st, -1);
+}
+
 // the level product: the default FP64 product kernel (no autotuning here)
 cudaError_t product_f64(void *, int, const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw,
                         int tw_log, cudaStream_t st)
@@ -133,8 +141,8 @@ extern "C" mrc_status mrc_inverse_noalloc(int d, int64_t N, const double *A, dou
     const int64_t m0 = mrc_base_size(d, N);
     CKN(mrc_base_case(A, psi, d, m0, st));
     const NewtonBufs nb{b0, b1, b2, bt};
-    if (mrc_newton_levels(PREC_F64, d, N, A, psi, m0, nb, tw, kTwLog, product_f64, nullptr, st, nullptr, nullptr,
-                          nullptr, nullptr) != 0)
+    if (mrc_newton_levels(PREC_F64, d, N, A, psi, m0, nb, tw, kTwLog, fft_f64, product_f64, nullptr, st, nullptr,
+                          nullptr, nullptr, nullptr) != 0)
         return MRC_ERR_CUDA;
     CKN(cudaStreamSynchronize(st));
     int h = 0;

@@ -10,32 +10,38 @@
 //     four digits, pairs s + t >= 3 (10 pairs in 4 groups), about 2^-29.
 //
 // The rows of X are scaled by 2^-sigma_i and the columns of Y by 2^-tau_j
-// (powers of two from bounds over both frequencies of the pair), every value
-// is split into S digits (digits.cuh: exact BF16 integers, |q| <= 128), and
-// all digit pairs of one weight group g accumulate in one FP32 accumulator in
-// TMEM -- exactly, since a group holds at most 6 pairs of two 64-term dot
-// products of digits <= 128 (below 2^24).  One MMA of M = 128, N = 64 forms
-// [C_r; C_i] from the 192-row MN-major A tile [-X_i; X_r; X_i] of a digit:
-// D += [X_r; X_i] Y_r (rows 64..191) and D += [-X_i; X_r] Y_i (rows 0..127).
+// (powers of two from bounds over both frequencies of the pair) and every
+// value v is split into S digits t_s, each a multiple of 2^(8s - 8S) of at
+// most 8 significant bits (an exact BF16 value; digits.cuh's rounding steps,
+// kept at their own scale).  Every digit pair of weight group g = s + t has
+// the quantum 2^(8g - 16S), so all pairs of one group accumulate exactly in
+// one FP32 accumulator in TMEM: a group holds at most 6 pairs of two 64-term
+// dot products of digits <= 128 quanta each (below 2^24 quanta).  One MMA of
+// M = 128, N = 64 forms [C_r; C_i] from the 192-row MN-major A tile
+// [-X_i; X_r; X_i] of a digit: D += [X_r; X_i] Y_r (rows 64..191) and
+// D += [-X_i; X_r] Y_i (rows 0..127).  The group sums add top group first.
 //
-// The kernel is persistent (one CTA per SM, pairs p = blockIdx.x, + grid, ...)
-// and warp-specialised, with every hand-off on an mbarrier:
+// The kernels are persistent (one CTA per SM, pairs p = blockIdx.x, + grid,
+// ...) and warp-specialised, with every hand-off on an mbarrier:
 //   warps 0-7  (split): per frequency pair the row / column bounds, then per
-//              frequency and K chunk of 16 the real-FFT split of the packed
-//              spectra (the fused split of kernels.cuh) and the digit tiles,
-//              into a ring of NSLOT chunk slots (full / empty barriers);
+//              K chunk of 16 the real-FFT split of the packed spectra (the
+//              fused split of kernels.cuh) and the digit tiles, into a ring
+//              of NSLOT chunk slots (full / empty barriers);
 //   warp 12    (MMA): one thread issues every kept digit pair's MMAs of a
 //              chunk and releases the slot with tcgen05.commit; after the
-//              last chunk of a frequency it signals the epilogue;
-//   warps 8-11 (epilogue): tcgen05.ld of the group accumulators, the fold
-//              top group first (compensated double-float for the top three
-//              groups of the residual product, FP32 below and for FP32),
-//              then, through a shared-memory transpose, the scaling by
-//              2^(sigma + tau), the real-FFT merge of the pair and coalesced
-//              stores of the packed output spectrum.
-// FP32 keeps two accumulator sets in TMEM (4 x 64 columns each), so the MMAs
-// of one frequency overlap the epilogue of the previous one; double-float
-// (6 x 64 columns) has one.
+//              last chunk it signals the epilogue;
+//   warps 8-11 (epilogue): tcgen05.ld of the group accumulators and the fold
+//              (a compensated double-float sum of the top three groups for
+//              the residual product, FP32 below and for FP32), then, through
+//              a shared-memory transpose, the scaling by 2^(sigma + tau), the
+//              real-FFT merge of the pair and coalesced stores.
+// FP32 takes both frequencies of a pair at once: the split of f and M - f
+// shares its loads and its twiddle product (2 Xh(M - f) = conj(s - t) where
+// 2 Xh(f) = s + t), both accumulator sets fill the 512 TMEM columns
+// (4 x 64 each), and the epilogue merges C(f) and C(M - f) directly.
+// Double-float (6 x 64 columns per frequency) takes the two frequencies one
+// after the other and keeps the unmerged C(f) in the output until C(M - f)
+// is known.
 //
 // Every wait is bounded: a wait that gives up sets MRC_ERR_TIMEOUT (6) in the
 // status word and a shared abort flag; all roles then leave their loops, the
@@ -48,9 +54,11 @@ namespace {
 using namespace mrc_digits;
 using namespace mrc_tc;
 
+// S digits, smallest group kept, ring slots, frequencies per pass (2: both
+// of a pair at once)
 template <class T> struct TcP;
-template <> struct TcP<dd> { static constexpr int S = 6, GMIN = 5, NSLOT = 3, NTB = 1; };
-template <> struct TcP<float> { static constexpr int S = 4, GMIN = 3, NSLOT = 4, NTB = 2; };
+template <> struct TcP<dd> { static constexpr int S = 6, GMIN = 5, NSLOT = 3, NF = 1; };
+template <> struct TcP<float> { static constexpr int S = 4, GMIN = 3, NSLOT = 2, NF = 2; };
 
 constexpr int KC = 16;                // K per chunk: one MMA K step
 constexpr int NCH = 64 / KC;          // chunks per frequency
@@ -70,53 +78,84 @@ constexpr unsigned IDESC = idesc_bf16<128, 64>();
 template <class T>
 struct TcL {
     static constexpr int S = TcP<T>::S, GMIN = TcP<T>::GMIN, NG = 2 * (S - 1) - GMIN + 1;
-    static constexpr int NSLOT = TcP<T>::NSLOT, NTB = TcP<T>::NTB;
-    static constexpr int SLOT = S * (A_TILE + 2 * B_TILE);
-    static constexpr int XCH = 2 * 64 * XLD * (int)sizeof(T);
+    static constexpr int NSLOT = TcP<T>::NSLOT, NF = TcP<T>::NF;
+    static constexpr int SUB = S * (A_TILE + 2 * B_TILE);  // digit tiles of one frequency and chunk
+    static constexpr int SLOT = NF * SUB;
+    static constexpr int XCH = 2 * NF * 64 * XLD * (int)sizeof(T);  // [NF][C_r, C_i][64][XLD]
     static constexpr int OFF_XCH = NSLOT * SLOT;
-    // per-pair row / column exponents sig[NB][64], tau[NB][64], then the bounds bx[64], by[64].  The split
-    // warps run at most NSLOT chunks ahead of the MMAs and those at most NTB frequencies ahead of the
-    // epilogue, so the epilogue is fewer than NB = 8 pairs behind the split warps.
+    // Per-pair scale factors scx[i] = 2^-sigma_i, scy[j] = 2^-tau_j (the
+    // split) and fx[i] = 2^(sigma_i - 1), fy[j] = 2^(tau_j - 1) (the output:
+    // fx fy = 2^(sigma + tau) / 4 undoes the scalings and the split's factor
+    // 2 on both operands) in NB buffers by pair counter, then the bounds
+    // bx[64], by[64].  The split warps run at most NSLOT chunks ahead of the
+    // MMAs and those at most one pass ahead of the epilogue, so the epilogue
+    // is fewer than NB pairs behind the split.
     static constexpr int NB = 8;
-    static constexpr int OFF_SIG = OFF_XCH + XCH;
-    static constexpr int SMEM = OFF_SIG + (2 * NB + 2) * 64 * 4;
-    static_assert(NTB * NG * 64 <= (int)TMEM_COLS, "accumulators fit in TMEM");
+    static constexpr int OFF_SC = OFF_XCH + XCH;
+    static constexpr int SMEM = OFF_SC + (4 * NB + 2) * 64 * 4;
+    static constexpr int TCOLS = NG * 64;  // TMEM columns of one frequency's groups
+    static_assert(NF * TCOLS <= (int)TMEM_COLS, "accumulators fit in TMEM");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
 __device__ __forceinline__ int mn_off(int m, int k) { return (m >> 3) * SBO + (k >> 3) * 128 + (k & 7) * 16 + (m & 7) * 2; }
 __device__ __forceinline__ int k_off(int n, int k) { return (n >> 3) * SBO + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2; }
 
-// 2 Xh(f) from the packed spectrum: Z(f) = a, conj-partner Z(M - f) = b,
-// w = W_L^f:  s + w (-i) dlt  with s = a + conj b, dlt = a - conj b (the
-// real-FFT split of kernels.cuh without its factor 1/2, which the output
-// scaling takes instead)
+// 2^e clamped to the normal float exponents
+__device__ __forceinline__ float pow2c(int e) { return pow2f(max(-126, min(127, e))); }
+
+// s and t of the real-FFT split (kernels.cuh: split_real without its factor
+// 1/2) for packed values a = Z(f), b = Z(M - f), w = W_L^f: 2 Xh(f) = s + t
+// and 2 Xh(M - f) = conj(s - t), with s = a + conj b, t = w (-i) (a - conj b).
 template <class T>
-__device__ __forceinline__ cx<T> split2(cx<T> za, cx<T> zb, cx<T> w)
+__device__ __forceinline__ void split_st(cx<T> za, cx<T> zb, cx<T> w, cx<T> &s, cx<T> &t)
 {
-    const cx<T> s = {Ar<T>::add(za.re, zb.re), Ar<T>::sub(za.im, zb.im)};
+    s = {Ar<T>::add(za.re, zb.re), Ar<T>::sub(za.im, zb.im)};
     const cx<T> dlt = {Ar<T>::sub(za.re, zb.re), Ar<T>::add(za.im, zb.im)};
-    const cx<T> o = {dlt.im, Ar<T>::neg(dlt.re)};
-    return c_add(s, c_mul(w, o));
+    t = c_mul(w, cx<T>{dlt.im, Ar<T>::neg(dlt.re)});
 }
 
-__device__ __forceinline__ void digits(dd v, float sc, float (&q)[6]) { digits6(v.hi * sc, v.lo * sc, q); }
-// four balanced base-256 digits of an FP32 value, weights 2^-8 .. 2^-32
-// (the same rounding steps as digits6: t = (x + C) - C rounds x to a grid)
+// Balanced digits at their own scale.  t = (x + C) - C with C = 1.5 * 2^k
+// rounds x to the nearest multiple of 2^(k-23) and x - t is exact; the
+// digits of a value |v| <= 1/2 stay within 128 quanta (digits.cuh).
+// Double-float hi + lo: six digits on the grids 2^-8 .. 2^-48, lo joining
+// through an exact TwoSum after two digits, its error after four.
+__device__ __forceinline__ void digits(dd v, float sc, float (&q)[6])
+{
+    float x = v.hi * sc, t;
+    t = __fsub_rn(__fadd_rn(x, 49152.0f), 49152.0f);  // grid 2^-8
+    q[5] = t;
+    x = __fsub_rn(x, t);
+    t = __fsub_rn(__fadd_rn(x, 192.0f), 192.0f);      // grid 2^-16
+    q[4] = t;
+    x = __fsub_rn(x, t);
+    const dd ye = dd_two_sum(x, v.lo * sc);           // exact: x + lo = y + e
+    x = ye.hi;
+    t = __fsub_rn(__fadd_rn(x, 0.75f), 0.75f);        // grid 2^-24
+    q[3] = t;
+    x = __fsub_rn(x, t);
+    t = __fsub_rn(__fadd_rn(x, 0x1.8p-9f), 0x1.8p-9f);  // grid 2^-32
+    q[2] = t;
+    x = __fadd_rn(__fsub_rn(x, t), ye.lo);
+    t = __fsub_rn(__fadd_rn(x, 0x1.8p-17f), 0x1.8p-17f);  // grid 2^-40
+    q[1] = t;
+    x = __fsub_rn(x, t);
+    q[0] = __fsub_rn(__fadd_rn(x, 0x1.8p-25f), 0x1.8p-25f);  // grid 2^-48
+}
+// FP32: four digits on the grids 2^-8 .. 2^-32
 __device__ __forceinline__ void digits(float v, float sc, float (&q)[4])
 {
     float x = v * sc, t;
-    t = __fsub_rn(__fadd_rn(x, 49152.0f), 49152.0f);        // grid 2^-8
-    q[3] = t * 256.0f;
+    t = __fsub_rn(__fadd_rn(x, 49152.0f), 49152.0f);
+    q[3] = t;
     x = __fsub_rn(x, t);
-    t = __fsub_rn(__fadd_rn(x, 192.0f), 192.0f);            // grid 2^-16
-    q[2] = t * 65536.0f;
+    t = __fsub_rn(__fadd_rn(x, 192.0f), 192.0f);
+    q[2] = t;
     x = __fsub_rn(x, t);
-    t = __fsub_rn(__fadd_rn(x, 0.75f), 0.75f);              // grid 2^-24
-    q[1] = t * 16777216.0f;
+    t = __fsub_rn(__fadd_rn(x, 0.75f), 0.75f);
+    q[1] = t;
     x = __fsub_rn(x, t);
-    t = __fsub_rn(__fadd_rn(x, 0x1.8p-9f), 0x1.8p-9f);      // grid 2^-32
-    q[0] = t * 0x1p32f;
+    q[0] = __fsub_rn(__fadd_rn(x, 0x1.8p-9f), 0x1.8p-9f);
 }
 
 template <class T>
@@ -135,8 +174,8 @@ __device__ __forceinline__ cx<float> ldg_cx<float>(const cx<float> *p)
 }
 
 // Raw packed-spectrum values of one chunk held by a split thread: X rows
-// 4 i4 .. 4 i4 + 3 at column k0 + (t & 15); Y rows k0 + 4 k4 .. + 3 at column
-// j; both partner rows ra and rb of the pair.
+// 4 i4 .. 4 i4 + 3 at column k0 + (t & 15); Y rows k0 + 4 k4 .. + 3 at
+// column j = 8 (t / 32) + (t & 7), k4 = (t & 31) / 8; both rows ra and rb.
 template <class T>
 struct Raw {
     cx<T> xa[4], xb[4], ya[4], yb[4];
@@ -172,37 +211,42 @@ __device__ __forceinline__ void load_y(Raw<T> &r, const cx<T> *ZY, int64_t ra, i
     }
 }
 
-// digit tiles of X for the slot: per digit, 8 bytes (4 consecutive rows) into
-// each of the three blocks -X_i (rows 0..63), X_r (64..127), X_i (128..191)
-template <class T>
-__device__ __forceinline__ void split_x(const Raw<T> &r, unsigned char *slot, const int *sig, cx<T> w, int d, int t)
+// Packed BF16 digits of 4 values (two uint per digit and component) of one
+// frequency: v[n] = 2 Xh or 2 Yh, scaled by sc[n]
+template <class T, int S>
+__device__ __forceinline__ void pack4(const cx<T> (&v)[4], const float (&sc)[4], unsigned (&wr)[S][2],
+                                      unsigned (&wi)[S][2])
 {
-    constexpr int S = TcL<T>::S;
-    const int k = t & 15, i4 = t >> 4;
-    unsigned wr[S][2], wi[S][2];
     float pr[S], pi[S];
 #pragma unroll
-    for (int ii = 0; ii < 4; ++ii) {
-        const int i = 4 * i4 + ii;
+    for (int n = 0; n < 4; ++n) {
         float qr[S], qi[S];
-        const cx<T> x = split2(r.xa[ii], r.xb[ii], w);
-        const float sc = i < d ? pow2f(-sig[i]) : 0.0f;
-        digits(x.re, sc, qr);
-        digits(x.im, sc, qi);
+        digits(v[n].re, sc[n], qr);
+        digits(v[n].im, sc[n], qi);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            if (ii & 1) {
-                wr[s][ii >> 1] = pack2(pr[s], qr[s]);
-                wi[s][ii >> 1] = pack2(pi[s], qi[s]);
+            if (n & 1) {
+                wr[s][n >> 1] = pack2(pr[s], qr[s]);
+                wi[s][n >> 1] = pack2(pi[s], qi[s]);
             } else {
                 pr[s] = qr[s];
                 pi[s] = qi[s];
             }
         }
     }
+}
+
+// digit tiles of X for one frequency's sub-slot: per digit, 8 bytes (4
+// consecutive rows) into each of the blocks -X_i (rows 0..63), X_r
+// (64..127), X_i (128..191)
+template <int S>
+__device__ __forceinline__ void store_x(unsigned char *sub, const unsigned (&wr)[S][2], const unsigned (&wi)[S][2],
+                                        int t)
+{
+    const int k = t & 15, i4 = t >> 4;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        unsigned char *tl = slot + s * A_TILE;
+        unsigned char *tl = sub + s * A_TILE;
         *reinterpret_cast<uint2 *>(tl + mn_off(4 * i4, k)) = make_uint2(wi[s][0] ^ 0x80008000u, wi[s][1] ^ 0x80008000u);
         *reinterpret_cast<uint2 *>(tl + mn_off(64 + 4 * i4, k)) = make_uint2(wr[s][0], wr[s][1]);
         *reinterpret_cast<uint2 *>(tl + mn_off(128 + 4 * i4, k)) = make_uint2(wi[s][0], wi[s][1]);
@@ -210,36 +254,75 @@ __device__ __forceinline__ void split_x(const Raw<T> &r, unsigned char *slot, co
 }
 
 // digit tiles of Y_r and Y_i (K-major, row n = j): 8 bytes of 4 consecutive k per digit
-template <class T>
-__device__ __forceinline__ void split_y(const Raw<T> &r, unsigned char *slot, const int *tau, cx<T> w, int d, int t)
+template <int S>
+__device__ __forceinline__ void store_y(unsigned char *sub, const unsigned (&wr)[S][2], const unsigned (&wi)[S][2],
+                                        int t)
 {
-    constexpr int S = TcL<T>::S;
     const int lane = t & 31, j = 8 * (t >> 5) + (lane & 7), k4 = lane >> 3;
-    unsigned wr[S][2], wi[S][2];
-    float pr[S], pi[S];
-    const float sc = j < d ? pow2f(-tau[j]) : 0.0f;
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-        float qr[S], qi[S];
-        const cx<T> y = split2(r.ya[kk], r.yb[kk], w);
-        digits(y.re, sc, qr);
-        digits(y.im, sc, qi);
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            if (kk & 1) {
-                wr[s][kk >> 1] = pack2(pr[s], qr[s]);
-                wi[s][kk >> 1] = pack2(pi[s], qi[s]);
-            } else {
-                pr[s] = qr[s];
-                pi[s] = qi[s];
-            }
-        }
-    }
-    unsigned char *br = slot + S * A_TILE, *bi = br + S * B_TILE;
+    unsigned char *br = sub + S * A_TILE, *bi = br + S * B_TILE;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         *reinterpret_cast<uint2 *>(br + s * B_TILE + k_off(j, 4 * k4)) = make_uint2(wr[s][0], wr[s][1]);
         *reinterpret_cast<uint2 *>(bi + s * B_TILE + k_off(j, 4 * k4)) = make_uint2(wi[s][0], wi[s][1]);
+    }
+}
+
+// The split of one chunk into the slot.  NF == 1: the frequency with
+// twiddle w of the raw rows (ra, rb); NF == 2: f (sub-slot 0) and M - f (1).
+template <class T>
+__device__ __forceinline__ void split_chunk_x(const Raw<T> &r, unsigned char *slot, const float *scx, cx<T> w, int t)
+{
+    using L = TcL<T>;
+    constexpr int S = L::S;
+    const int i4 = t >> 4;
+    float sc[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) sc[n] = scx[4 * i4 + n];
+    cx<T> vf[4], vg[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        cx<T> s, tt;
+        split_st(r.xa[n], r.xb[n], w, s, tt);
+        vf[n] = c_add(s, tt);
+        if constexpr (L::NF == 2) vg[n] = {Ar<T>::sub(s.re, tt.re), Ar<T>::sub(tt.im, s.im)};
+    }
+    {
+        unsigned wr[S][2], wi[S][2];
+        pack4<T, S>(vf, sc, wr, wi);
+        store_x<S>(slot, wr, wi, t);
+    }
+    if constexpr (L::NF == 2) {
+        unsigned wr[S][2], wi[S][2];
+        pack4<T, S>(vg, sc, wr, wi);
+        store_x<S>(slot + L::SUB, wr, wi, t);
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void split_chunk_y(const Raw<T> &r, unsigned char *slot, const float *scy, cx<T> w, int t)
+{
+    using L = TcL<T>;
+    constexpr int S = L::S;
+    const int lane = t & 31, j = 8 * (t >> 5) + (lane & 7);
+    const float c = scy[j];
+    const float sc[4] = {c, c, c, c};
+    cx<T> vf[4], vg[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        cx<T> s, tt;
+        split_st(r.ya[n], r.yb[n], w, s, tt);
+        vf[n] = c_add(s, tt);
+        if constexpr (L::NF == 2) vg[n] = {Ar<T>::sub(s.re, tt.re), Ar<T>::sub(tt.im, s.im)};
+    }
+    {
+        unsigned wr[S][2], wi[S][2];
+        pack4<T, S>(vf, sc, wr, wi);
+        store_y<S>(slot, wr, wi, t);
+    }
+    if constexpr (L::NF == 2) {
+        unsigned wr[S][2], wi[S][2];
+        pack4<T, S>(vg, sc, wr, wi);
+        store_y<S>(slot + L::SUB, wr, wi, t);
     }
 }
 
@@ -251,10 +334,10 @@ __device__ __forceinline__ dd add_f(dd a, float v)
 }
 
 // Fold the NG group accumulators of TMEM lanes 32 q + lane, columns
-// col .. col + 7: sum over g of acc_g 2^(8 (g - NG + 1)), every term an exact
-// FP32 value, top group first.  Double-float: the top three groups as a
-// compensated sum, the groups below (weights 2^-24 and less of the top one)
-// in FP32, joining once; FP32: plain FP32 adds.
+// col .. col + 7 (every group sum an exact FP32 value at its own scale), top
+// group first.  Double-float: the top three groups as a compensated sum, the
+// groups below (2^-24 and less of the top one) in FP32, joining once; FP32:
+// plain FP32 adds.
 template <class T, int NG>
 __device__ __forceinline__ void fold8(unsigned tbase, T (&out)[8])
 {
@@ -263,10 +346,9 @@ __device__ __forceinline__ void fold8(unsigned tbase, T (&out)[8])
     for (int g = NG - 1; g >= 0; --g) {
         unsigned r[8];
         ld8(tbase + (unsigned)(g * 64), r);
-        const float w = __uint_as_float((unsigned)(127 - 8 * (NG - 1 - g)) << 23);  // 2^(8 (g - NG + 1))
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const float v = __uint_as_float(r[c]) * w;
+            const float v = __uint_as_float(r[c]);
             if constexpr (__is_same(T, dd)) {
                 if (g == NG - 1) out[c] = dd{v, 0.0f};
                 else if (g >= NG - 3) out[c] = add_f(out[c], v);
@@ -284,8 +366,8 @@ __device__ __forceinline__ void fold8(unsigned tbase, T (&out)[8])
     }
 }
 
-__device__ __forceinline__ dd tc_scale(dd x, int e) { return {scale2(x.hi, e), scale2(x.lo, e)}; }
-__device__ __forceinline__ float tc_scale(float x, int e) { return scale2(x, e); }
+__device__ __forceinline__ dd mul_f(dd x, float f) { return {x.hi * f, x.lo * f}; }
+__device__ __forceinline__ float mul_f(float x, float f) { return x * f; }
 
 template <class T>
 __device__ __forceinline__ void st_cx(cx<T> *p, cx<T> v);
@@ -304,14 +386,12 @@ template <class T>
 __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *status)
 {
     using L = TcL<T>;
-    constexpr int S = L::S, GMIN = L::GMIN, NG = L::NG, NSLOT = L::NSLOT, NTB = L::NTB;
+    constexpr int S = L::S, GMIN = L::GMIN, NG = L::NG, NSLOT = L::NSLOT, NF = L::NF;
     extern __shared__ __align__(1024) unsigned char smem[];
-    T *xch = reinterpret_cast<T *>(smem + L::OFF_XCH);  // [2][64][XLD]: C_r, C_i of 32 columns
-    int *sigb = reinterpret_cast<int *>(smem + L::OFF_SIG);  // [NB][64] row exponents, by pair counter mod NB
-    int *taub = sigb + 64 * L::NB;                           // [NB][64] column exponents
-    unsigned *bx = reinterpret_cast<unsigned *>(taub + 64 * L::NB), *by = bx + 64;
-    __shared__ __align__(8) unsigned long long bar_full[NSLOT], bar_empty[NSLOT], bar_tfull[NTB], bar_tempty[NTB],
-        bar_done;
+    T *xch = reinterpret_cast<T *>(smem + L::OFF_XCH);          // [NF][C_r, C_i][64][XLD]
+    float *scb = reinterpret_cast<float *>(smem + L::OFF_SC);  // [NB][scx, scy, fx, fy][64]
+    unsigned *bx = reinterpret_cast<unsigned *>(scb + 4 * 64 * L::NB), *by = bx + 64;
+    __shared__ __align__(8) unsigned long long bar_full[NSLOT], bar_empty[NSLOT], bar_tfull, bar_tempty, bar_done;
     __shared__ unsigned tslot;
     __shared__ volatile int abort_flag;
 
@@ -321,10 +401,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
             mbar_init(smem_u32(&bar_full[s]), NSPLIT);
             mbar_init(smem_u32(&bar_empty[s]), 1);
         }
-        for (int b = 0; b < NTB; ++b) {
-            mbar_init(smem_u32(&bar_tfull[b]), 1);
-            mbar_init(smem_u32(&bar_tempty[b]), NEPI);
-        }
+        mbar_init(smem_u32(&bar_tfull), 1);
+        mbar_init(smem_u32(&bar_tempty), NEPI);
         mbar_init(smem_u32(&bar_done), 1);
         abort_flag = 0;
         mbar_init_fence();
@@ -347,20 +425,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
         abort_flag = 1;
         if (status) atomicExch(status, 6);
     };
+    // passes of pair p: its frequencies one at a time (NF == 1; one for the
+    // self-paired p = M/2), or both at once (NF == 2)
+    auto npass = [&](int64_t p) { return NF == 2 ? 1 : (((M - p) == p) ? 1 : 2); };
 
     if (warp < WEPI0) {
         // ------------------------------------------------------------ split
         const int t = tid;
         int it = 0;  // chunk counter: slot it % NSLOT, use it / NSLOT
-        int pl = 0;  // pair counter (mod NB selects the exponent buffers)
+        int pl = 0;  // pair counter (mod NB selects the scale buffers)
         Raw<T> raw;
         for (int64_t p = blockIdx.x; p < a.npairs; p += gridDim.x, ++pl) {
-            const int64_t f = p, gL = M - p, gZ = gL & (M - 1);
-            const int nfreq = (gL == f) ? 1 : 2;  // p = M/2 pairs with itself
+            const int64_t f = p, gZ = (M - p) & (M - 1);
             const cx<T> wf = tw[f << (a.tw_log - a.logM - 1)];
             const cx<T> wg = c_neg(c_conj(wf));
-            int *sig = sigb + 64 * (pl % L::NB), *tau = taub + 64 * (pl % L::NB);
-            // ---- bounds over both frequencies: |Xh(f)|, |Xh(g)| <= |Z(f)|_1 + |Z(g)|_1 entrywise
+            float *sc = scb + 4 * 64 * (pl % L::NB);
+            // ---- bounds over both frequencies: |Xh(f)|, |Xh(M - f)| <= |Z(f)|_1 + |Z(M - f)|_1 entrywise
             if (t < 128) bx[t] = 0u;
             if (bar_or(BAR_SPLIT, NSPLIT, failed || abort_flag)) break;
             {
@@ -386,27 +466,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
             }
             bar_sync(BAR_SPLIT, NSPLIT);
             if (t < 64) {
-                // 2 Xh and 2 Yh are split (split2): bound 2 |.|
-                sig[t] = scale_exp(2.0f * __uint_as_float(bx[t]));
-                tau[t] = scale_exp(2.0f * __uint_as_float(by[t]));
+                // 2 Xh and 2 Yh are split: bound 2 |.|, scaled values <= 1/2
+                const int sx = t < d ? scale_exp(2.0f * __uint_as_float(bx[t])) : 0;
+                const int sy = t < d ? scale_exp(2.0f * __uint_as_float(by[t])) : 0;
+                sc[t] = t < d ? pow2c(-sx) : 0.0f;
+                sc[64 + t] = t < d ? pow2c(-sy) : 0.0f;
+                sc[128 + t] = pow2c(sx - 1);
+                sc[192 + t] = pow2c(sy - 1);
             }
             bar_sync(BAR_SPLIT, NSPLIT);
-            // ---- chunks of both frequencies
-            const int nch = nfreq * NCH;
+            // ---- chunks of the pair's passes
+            const int nch = npass(p) * NCH;
             load_x(raw, ZX, f, gZ, d, 0, t);
             load_y(raw, ZY, f, gZ, d, 0, t);
             for (int c = 0; c < nch; ++c, ++it) {
-                const int phase = c / NCH;
-                const cx<T> w = phase == 0 ? wf : wg;
+                const cx<T> w = (c / NCH) == 0 ? wf : wg;
                 const int slot = it % NSLOT, use = it / NSLOT;
                 unsigned char *sp = smem + slot * L::SLOT;
                 if (!failed && use > 0 && (abort_flag || !mbar_wait(smem_u32(&bar_empty[slot]), (use - 1) & 1)))
                     give_up();
-                const int cn = c + 1;  // next chunk of this pair
+                const int cn = c + 1;  // next chunk of this pair: pass cn / NCH
                 const int64_t na = (cn / NCH) == 0 ? f : gZ, nb = (cn / NCH) == 0 ? gZ : f;
-                if (!failed) split_x<T>(raw, sp, sig, w, d, t);
+                if (!failed) split_chunk_x<T>(raw, sp, sc, w, t);
                 if (cn < nch) load_x(raw, ZX, na, nb, d, (cn % NCH) * KC, t);
-                if (!failed) split_y<T>(raw, sp, tau, w, d, t);
+                if (!failed) split_chunk_y<T>(raw, sp, sc + 64, w, t);
                 if (cn < nch) load_y(raw, ZY, na, nb, d, (cn % NCH) * KC, t);
                 if (!failed) {
                     fence_async_smem();  // digit tiles visible to the tensor cores
@@ -418,63 +501,76 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
         // --------------------------------------------------------- epilogue
         const int et = tid - WEPI0 * 32;
         const int q = warp & 3;  // TMEM lanes 32 q .. 32 q + 31
-        int fi = 0, pl = 0;
+        int fi = 0, pl = 0;      // passes drained, pairs
         for (int64_t p = blockIdx.x; p < a.npairs; p += gridDim.x, ++pl) {
-            const int64_t f = p, gL = M - p, gZ = gL & (M - 1);
-            const int nfreq = (gL == f) ? 1 : 2;
+            const int64_t f = p, gZ = (M - p) & (M - 1);
+            const int np = npass(p);
+            const bool self = (M - p) == p;  // p = M/2 pairs with itself
             const bool two = (gZ != f);
             const cx<T> wf = tw[f << (a.tw_log - a.logM - 1)];
             const cx<T> wg = c_neg(c_conj(wf));
-            const int *sig = sigb + 64 * (pl % L::NB), *tau = taub + 64 * (pl % L::NB);
+            const float *fx = scb + 4 * 64 * (pl % L::NB) + 128, *fy = fx + 64;
             bool stop = false;
-            for (int phase = 0; phase < nfreq; ++phase, ++fi) {
-                const int b = fi % NTB, ub = fi / NTB;
-                bool ok = !failed && !abort_flag && mbar_wait(smem_u32(&bar_tfull[b]), ub & 1);
+            for (int phase = 0; phase < np; ++phase, ++fi) {
+                bool ok = !failed && !abort_flag && mbar_wait(smem_u32(&bar_tfull), fi & 1);
                 if (bar_or(BAR_EPI, NEPI, !ok)) {
                     if (!failed) give_up();
                     stop = true;
                     break;
                 }
                 fence_after();
-                const unsigned tb = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(b * NG * 64);
-                T *xr = xch + ((q >> 1) * 64 + 32 * (q & 1) + lane) * XLD;  // part q >> 1: C_r or C_i rows
-                T cv[32];
-                // columns 0..31 to the transpose, columns 32..63 kept in registers
+                const unsigned tb = tmem + ((unsigned)(32 * q) << 16);
+                T cv[NF][32];
+                // every frequency of the pass: columns 0..31 to the transpose, 32..63 kept in registers
 #pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
+                for (int fq = 0; fq < NF; ++fq) {
+                    T *xr = xch + ((fq * 2 + (q >> 1)) * 64 + 32 * (q & 1) + lane) * XLD;  // C_r or C_i rows
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        T o8[8];
-                        fold8<T, NG>(tb + (unsigned)(32 * hh + 8 * m), o8);
+                    for (int hh = 0; hh < 2; ++hh) {
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            if (hh == 0) xr[8 * m + c] = o8[c];
-                            else cv[8 * m + c] = o8[c];
+                        for (int m = 0; m < 4; ++m) {
+                            T o8[8];
+                            fold8<T, NG>(tb + (unsigned)(fq * L::TCOLS + 32 * hh + 8 * m), o8);
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) {
+                                if (hh == 0) xr[8 * m + c] = o8[c];
+                                else cv[fq][8 * m + c] = o8[c];
+                            }
                         }
                     }
                 }
                 fence_before();
-                mbar_arrive(smem_u32(&bar_tempty[b]));  // accumulators read: the next MMAs may overwrite them
+                mbar_arrive(smem_u32(&bar_tempty));  // accumulators read: the next MMAs may overwrite them
                 // two rounds of 32 columns, lanes along j for coalesced global accesses
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
                     if (r == 1) {
 #pragma unroll
-                        for (int c = 0; c < 32; ++c) xr[c] = cv[c];
+                        for (int fq = 0; fq < NF; ++fq) {
+                            T *xr = xch + ((fq * 2 + (q >> 1)) * 64 + 32 * (q & 1) + lane) * XLD;
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) xr[c] = cv[fq][c];
+                        }
                     }
                     bar_sync(BAR_EPI, NEPI);
                     const int jl = et & 31, j = 32 * r + jl;
+                    const float sj = fy[j];
 #pragma unroll 2
                     for (int m = 0; m < 16; ++m) {
                         const int i = (et >> 5) + 4 * m;
                         if (i < d && j < d) {
-                            const int ex = sig[i] + tau[j] - 18;  // 2^(sigma + tau) / 4 x the fold's 2^-16
-                            const cx<T> v = {tc_scale(xch[i * XLD + jl], ex), tc_scale(xch[(64 + i) * XLD + jl], ex)};
+                            const float s_ = fx[i] * sj;  // 2^(sigma_i + tau_j - 2), exact
+                            const cx<T> v = {mul_f(xch[i * XLD + jl], s_), mul_f(xch[(64 + i) * XLD + jl], s_)};
                             cx<T> *zf = ZC + f * E + (int64_t)i * d + j;
-                            if (nfreq == 1) {
-                                st_cx(zf, merge_real(v, v, c_conj(wf)));  // p = M/2: C(g) = C(f)
+                            if constexpr (NF == 2) {
+                                const cx<T> vg = {mul_f(xch[(128 + i) * XLD + jl], s_),
+                                                  mul_f(xch[(192 + i) * XLD + jl], s_)};
+                                st_cx(zf, merge_real(v, vg, c_conj(wf)));
+                                if (two) st_cx(ZC + gZ * E + (int64_t)i * d + j, merge_real(vg, v, c_conj(wg)));
+                            } else if (self) {
+                                st_cx(zf, merge_real(v, v, c_conj(wf)));  // C(M - f) = C(f)
                             } else if (phase == 0) {
-                                st_cx(zf, v);  // C(f), merged once C(g) is known (same thread)
+                                st_cx(zf, v);  // C(f), merged once C(M - f) is known (same thread)
                             } else {
                                 const cx<T> cf = *zf;
                                 st_cx(zf, merge_real(cf, v, c_conj(wf)));
@@ -492,16 +588,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
         int it = 0, fi = 0;
         bool issued = false;
         for (int64_t p = blockIdx.x; p < a.npairs && !failed; p += gridDim.x) {
-            const int64_t gL = M - p;
-            const int nfreq = (gL == p) ? 1 : 2;
-            for (int phase = 0; phase < nfreq && !failed; ++phase, ++fi) {
-                const int b = fi % NTB, ub = fi / NTB;
-                if (ub > 0 && (abort_flag || !mbar_wait(smem_u32(&bar_tempty[b]), (ub - 1) & 1))) {
+            const int np = npass(p);
+            for (int phase = 0; phase < np && !failed; ++phase, ++fi) {
+                if (fi > 0 && (abort_flag || !mbar_wait(smem_u32(&bar_tempty), (fi - 1) & 1))) {
                     give_up();
                     break;
                 }
                 fence_after();
-                const unsigned dbase = tmem + (unsigned)(b * NG * 64);
                 for (int c = 0; c < NCH; ++c, ++it) {
                     const int slot = it % NSLOT, use = it / NSLOT;
                     if (abort_flag || !mbar_wait(smem_u32(&bar_full[slot]), use & 1)) {
@@ -509,26 +602,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
                         break;
                     }
                     fence_after();
-                    const unsigned sa = smem_u32(smem + slot * L::SLOT);
-                    const unsigned sbr = sa + S * A_TILE, sbi = sbr + S * B_TILE;
 #pragma unroll
-                    for (int g = GMIN; g <= 2 * (S - 1); ++g) {
-                        const unsigned dcol = dbase + (unsigned)(g - GMIN) * 64u;
-                        unsigned acc = c == 0 ? 0u : 1u;
+                    for (int fq = 0; fq < NF; ++fq) {
+                        const unsigned sa = smem_u32(smem + slot * L::SLOT + fq * L::SUB);
+                        const unsigned sbr = sa + S * A_TILE, sbi = sbr + S * B_TILE;
+                        const unsigned dbase = tmem + (unsigned)(fq * L::TCOLS);
 #pragma unroll
-                        for (int s = (g - (S - 1) > 0 ? g - (S - 1) : 0); s <= (g < S - 1 ? g : S - 1); ++s) {
-                            const int tt = g - s;
-                            const unsigned as = sa + s * A_TILE;
-                            mma<IDESC>(dcol, desc<SBO>(as + 8 * SBO), desc<SBO>(sbr + tt * B_TILE), acc);
-                            acc = 1u;
-                            mma<IDESC>(dcol, desc<SBO>(as), desc<SBO>(sbi + tt * B_TILE), 1u);
+                        for (int g = GMIN; g <= 2 * (S - 1); ++g) {
+                            const unsigned dcol = dbase + (unsigned)(g - GMIN) * 64u;
+                            unsigned acc = c == 0 ? 0u : 1u;
+#pragma unroll
+                            for (int s = (g - (S - 1) > 0 ? g - (S - 1) : 0); s <= (g < S - 1 ? g : S - 1); ++s) {
+                                const int tt = g - s;
+                                const unsigned as = sa + s * A_TILE;
+                                mma<IDESC>(dcol, desc<SBO>(as + 8 * SBO), desc<SBO>(sbr + tt * B_TILE), acc);
+                                acc = 1u;
+                                mma<IDESC>(dcol, desc<SBO>(as), desc<SBO>(sbi + tt * B_TILE), 1u);
+                            }
                         }
                     }
                     issued = true;
                     commit(smem_u32(&bar_empty[slot]));  // the slot is free once these MMAs completed
                 }
                 if (failed) break;
-                commit(smem_u32(&bar_tfull[b]));  // the frequency's accumulators are complete
+                commit(smem_u32(&bar_tfull));  // the pass's accumulators are complete
             }
         }
         if (issued) {

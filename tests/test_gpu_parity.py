@@ -442,9 +442,11 @@ def test_renewal_visits_matches_oracle(mrc):
 
 
 def test_autotuned_inverse_and_batch(mrc, tmp_path):
-    """autotune=1 times the product-kernel candidates per shape on the call's
-    stream; results stay within the parity gates and the choices are written
-    to MRC_AUTOTUNE_CACHE when the context is destroyed."""
+    """autotune=1 times the product-kernel candidates and the FFT plans (radix
+    splits, entries per CTA) per shape on the call's stream; results stay
+    within the parity gates and the choices are written to MRC_AUTOTUNE_CACHE
+    when the context is destroyed (product choices 0..3, FFT plans below 512
+    under keys with bit 62 set)."""
     import os
     cache = tmp_path / "tune.txt"
     os.environ["MRC_AUTOTUNE_CACHE"] = str(cache)
@@ -462,6 +464,8 @@ def test_autotuned_inverse_and_batch(mrc, tmp_path):
             assert e_rel(o.cpu().numpy(), oracle.inverse_left(m["A"])) <= TOL_REL
         mrc.release()
         lines = cache.read_text().split()
-        assert len(lines) >= 2 and all(int(c) in (0, 1, 2, 3) for c in lines[1::2])
+        keys, picks = [int(k) for k in lines[0::2]], [int(c) for c in lines[1::2]]
+        assert any(k >> 62 for k in keys) and any(not k >> 62 for k in keys)
+        assert all(0 <= c <= (511 if k >> 62 else 3) for k, c in zip(keys, picks))
     finally:
         del os.environ["MRC_AUTOTUNE_CACHE"]
