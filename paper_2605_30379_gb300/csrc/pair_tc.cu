@@ -57,8 +57,14 @@ using namespace mrc_tc;
 // S digits, smallest group kept, ring slots, frequencies per pass (2: both
 // of a pair at once)
 template <class T> struct TcP;
-template <> struct TcP<dd> { static constexpr int S = 6, GMIN = 5, NSLOT = 3, NF = 1; };
-template <> struct TcP<float> { static constexpr int S = 4, GMIN = 3, NSLOT = 2, NF = 2; };
+// PF: pairs ahead whose spectra are prefetched into L2 (each pair's four
+// rows X(f), X(M-f), Y(f), Y(M-f) are 4 E sizeof(cx<T>) bytes); with PF = 1
+// the next pair's bounds would be gathered during the second half of the
+// current pair's chunks, once the prefetch has landed.  Measured at d = 64,
+// N = 2^18: FP32 two pairs ahead 39.2 -> 38.8 ms; double-float one pair
+// ahead 41.4 -> 46.4 ms (256 KB per pair and SM crowd L2), so none.
+template <> struct TcP<dd> { static constexpr int S = 6, GMIN = 5, NSLOT = 3, NF = 1, PF = 0; };
+template <> struct TcP<float> { static constexpr int S = 4, GMIN = 3, NSLOT = 2, NF = 2, PF = 2; };
 
 constexpr int KC = 16;                // K per chunk: one MMA K step
 constexpr int NCH = 64 / KC;          // chunks per frequency
@@ -78,7 +84,7 @@ constexpr unsigned IDESC = idesc_bf16<128, 64>();
 template <class T>
 struct TcL {
     static constexpr int S = TcP<T>::S, GMIN = TcP<T>::GMIN, NG = 2 * (S - 1) - GMIN + 1;
-    static constexpr int NSLOT = TcP<T>::NSLOT, NF = TcP<T>::NF;
+    static constexpr int NSLOT = TcP<T>::NSLOT, NF = TcP<T>::NF, PF = TcP<T>::PF;
     static constexpr int SUB = S * (A_TILE + 2 * B_TILE);  // digit tiles of one frequency and chunk
     static constexpr int SLOT = NF * SUB;
     static constexpr int XCH = 2 * NF * 64 * XLD * (int)sizeof(T);  // [NF][C_r, C_i][64][XLD]
@@ -86,13 +92,14 @@ struct TcL {
     // Per-pair scale factors scx[i] = 2^-sigma_i, scy[j] = 2^-tau_j (the
     // split) and fx[i] = 2^(sigma_i - 1), fy[j] = 2^(tau_j - 1) (the output:
     // fx fy = 2^(sigma + tau) / 4 undoes the scalings and the split's factor
-    // 2 on both operands) in NB buffers by pair counter, then the bounds
-    // bx[64], by[64].  The split warps run at most NSLOT chunks ahead of the
-    // MMAs and those at most one pass ahead of the epilogue, so the epilogue
-    // is fewer than NB pairs behind the split.
+    // 2 on both operands) in NB buffers by pair counter, then two bound
+    // buffers bx[64], by[64] (a pair's, and the next pair's being gathered).
+    // The split warps run at most NSLOT chunks ahead of the MMAs and those
+    // at most one pass ahead of the epilogue, so the epilogue is fewer than
+    // NB pairs behind the split.
     static constexpr int NB = 8;
     static constexpr int OFF_SC = OFF_XCH + XCH;
-    static constexpr int SMEM = OFF_SC + (4 * NB + 2) * 64 * 4;
+    static constexpr int SMEM = OFF_SC + (4 * NB + 4) * 64 * 4;
     static constexpr int TCOLS = NG * 64;  // TMEM columns of one frequency's groups
     static_assert(NF * TCOLS <= (int)TMEM_COLS, "accumulators fit in TMEM");
     static_assert(SMEM <= 227 * 1024, "shared memory");
@@ -173,6 +180,97 @@ __device__ __forceinline__ cx<float> ldg_cx<float>(const cx<float> *p)
     return {v.x, v.y};
 }
 
+// The same read-only loads as volatile inline PTX: issued where they stand
+// (the compiler keeps volatile asm in order), so that the next chunk's
+// values are in flight during the current chunk's digit work instead of
+// being requested just before their use
+template <class T>
+__device__ __forceinline__ cx<T> ldv_cx(const cx<T> *p);
+template <>
+__device__ __forceinline__ cx<dd> ldv_cx<dd>(const cx<dd> *p)
+{
+    float4 v;
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];\n" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return {{v.x, v.y}, {v.z, v.w}};
+}
+template <>
+__device__ __forceinline__ cx<float> ldv_cx<float>(const cx<float> *p)
+{
+    float2 v;
+    asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return {v.x, v.y};
+}
+
+// High parts of one packed value (re, im): the bounds use them only
+template <class T>
+__device__ __forceinline__ float2 ldg_hi(const cx<T> *p);
+template <>
+__device__ __forceinline__ float2 ldg_hi<dd>(const cx<dd> *p)
+{
+    const float *q = reinterpret_cast<const float *>(p);
+    return make_float2(__ldg(q), __ldg(q + 2));
+}
+template <>
+__device__ __forceinline__ float2 ldg_hi<float>(const cx<float> *p)
+{
+    return __ldg(reinterpret_cast<const float2 *>(p));
+}
+
+// Bounds of a pair: row bounds bx[i] = max_k (|Z_X(f)_ik|_1 + |Z_X(M-f)_ik|_1)
+// and column bounds by[j] = max_k (|Z_Y(f)_kj|_1 + |Z_Y(M-f)_kj|_1), which
+// bound |Xh| and |Yh| at both frequencies entrywise.  Split thread t covers
+// column t & 63 of rows (t >> 6) + 4 n, n = 0 .. 15, in slices of two n:
+// bnd_issue loads a slice, bnd_reduce folds it into bx (a warp reduction, one
+// shared atomic per row) and into the thread's running column maximum my.
+struct BndIn {
+    float2 xa[2], xb[2], ya[2], yb[2];
+};
+
+template <class T>
+__device__ __forceinline__ void bnd_issue(BndIn &b, const cx<T> *ZX, const cx<T> *ZY, int64_t f, int64_t g, int d,
+                                          int t, int n0)
+{
+    const int64_t E = (int64_t)d * d;
+    const int k = t & 63;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int i = (t >> 6) + 4 * (n0 + u);
+        const float2 z = make_float2(0.0f, 0.0f);
+        b.xa[u] = b.xb[u] = b.ya[u] = b.yb[u] = z;
+        if (i < d && k < d) {
+            const int64_t e = (int64_t)i * d + k;
+            b.xa[u] = ldg_hi(ZX + f * E + e);
+            b.xb[u] = ldg_hi(ZX + g * E + e);
+            b.ya[u] = ldg_hi(ZY + f * E + e);
+            b.yb[u] = ldg_hi(ZY + g * E + e);
+        }
+    }
+}
+
+__device__ __forceinline__ void bnd_reduce(const BndIn &b, unsigned *bx, float &my, int t, int n0)
+{
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int i = (t >> 6) + 4 * (n0 + u);  // one row per pair of warps
+        const float mx = fabsf(b.xa[u].x) + fabsf(b.xa[u].y) + fabsf(b.xb[u].x) + fabsf(b.xb[u].y);
+        my = fmaxf(my, fabsf(b.ya[u].x) + fabsf(b.ya[u].y) + fabsf(b.yb[u].x) + fabsf(b.yb[u].y));
+        const unsigned wmx = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));  // nonnegative: bits order
+        if ((t & 31) == 0) atomicMax(&bx[i], wmx);
+    }
+}
+
+// The pair's scale factors from its bounds (2 Xh and 2 Yh are split: bound
+// 2 |.|, scaled values <= 1/2)
+__device__ __forceinline__ void bnd_scales(const unsigned *bx, const unsigned *by, float *sc, int d, int t)
+{
+    const int sx = t < d ? scale_exp(2.0f * __uint_as_float(bx[t])) : 0;
+    const int sy = t < d ? scale_exp(2.0f * __uint_as_float(by[t])) : 0;
+    sc[t] = t < d ? pow2c(-sx) : 0.0f;
+    sc[64 + t] = t < d ? pow2c(-sy) : 0.0f;
+    sc[128 + t] = pow2c(sx - 1);
+    sc[192 + t] = pow2c(sy - 1);
+}
+
 // Raw packed-spectrum values of one chunk held by a split thread: X rows
 // 4 i4 .. 4 i4 + 3 at column k0 + (t & 15); Y rows k0 + 4 k4 .. + 3 at
 // column j = 8 (t / 32) + (t & 7), k4 = (t & 31) / 8; both rows ra and rb.
@@ -191,8 +289,12 @@ __device__ __forceinline__ void load_x(Raw<T> &r, const cx<T> *ZX, int64_t ra, i
         const int i = 4 * i4 + ii;
         const bool ok = i < d && k < d;
         const int64_t e = (int64_t)i * d + k;
-        r.xa[ii] = ok ? ldg_cx(ZX + ra * E + e) : c_zero<T>();
-        r.xb[ii] = ok ? ldg_cx(ZX + rb * E + e) : c_zero<T>();
+        r.xa[ii] = c_zero<T>();
+        r.xb[ii] = c_zero<T>();
+        if (ok) {
+            r.xa[ii] = ldv_cx(ZX + ra * E + e);
+            r.xb[ii] = ldv_cx(ZX + rb * E + e);
+        }
     }
 }
 
@@ -206,8 +308,12 @@ __device__ __forceinline__ void load_y(Raw<T> &r, const cx<T> *ZY, int64_t ra, i
         const int k = k0 + 4 * k4 + kk;
         const bool ok = k < d && j < d;
         const int64_t e = (int64_t)k * d + j;
-        r.ya[kk] = ok ? ldg_cx(ZY + ra * E + e) : c_zero<T>();
-        r.yb[kk] = ok ? ldg_cx(ZY + rb * E + e) : c_zero<T>();
+        r.ya[kk] = c_zero<T>();
+        r.yb[kk] = c_zero<T>();
+        if (ok) {
+            r.ya[kk] = ldv_cx(ZY + ra * E + e);
+            r.yb[kk] = ldv_cx(ZY + rb * E + e);
+        }
     }
 }
 
@@ -390,7 +496,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
     extern __shared__ __align__(1024) unsigned char smem[];
     T *xch = reinterpret_cast<T *>(smem + L::OFF_XCH);          // [NF][C_r, C_i][64][XLD]
     float *scb = reinterpret_cast<float *>(smem + L::OFF_SC);  // [NB][scx, scy, fx, fy][64]
-    unsigned *bx = reinterpret_cast<unsigned *>(scb + 4 * 64 * L::NB), *by = bx + 64;
+    unsigned *bxy = reinterpret_cast<unsigned *>(scb + 4 * 64 * L::NB);  // [2][bx, by][64]
     __shared__ __align__(8) unsigned long long bar_full[NSLOT], bar_empty[NSLOT], bar_tfull, bar_tempty, bar_done;
     __shared__ unsigned tslot;
     __shared__ volatile int abort_flag;
@@ -431,71 +537,94 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
 
     if (warp < WEPI0) {
         // ------------------------------------------------------------ split
+        // The bounds of pair p + grid are gathered during pair p's chunks, in
+        // slices (their loads, first touches of those spectra, overlap the
+        // digit work); the first pair's before its chunks.
         const int t = tid;
         int it = 0;  // chunk counter: slot it % NSLOT, use it / NSLOT
         int pl = 0;  // pair counter (mod NB selects the scale buffers)
         Raw<T> raw;
+        BndIn bi;
+        // the four spectrum rows of pair q into L2, one bulk prefetch per row
+        // over its 16-byte aligned interior (a bulk copy must start on a
+        // 16-byte boundary and span a multiple of 16 bytes; FP32 rows of odd
+        // E start and end on 8-byte ones), so it never leaves the row
+        auto prefetch_pair = [&](int64_t q) {
+            if (t < 4 && q < a.npairs) {
+                const int64_t r = (t & 1) ? ((M - q) & (M - 1)) : q;
+                const uintptr_t b0 = (uintptr_t)((t < 2 ? ZX : ZY) + r * E);
+                const uintptr_t lo = (b0 + 15) & ~(uintptr_t)15, hi = (b0 + E * sizeof(cx<T>)) & ~(uintptr_t)15;
+                if (hi > lo) prefetch_l2((const void *)lo, (unsigned)(hi - lo));
+            }
+        };
+        for (int k = 1; k < L::PF; ++k) prefetch_pair((int64_t)blockIdx.x + (int64_t)k * gridDim.x);
+        bxy[t] = 0u;  // both bound buffers (256 threads, 256 words)
+        bar_sync(BAR_SPLIT, NSPLIT);
+        if (blockIdx.x < a.npairs) {
+            const int64_t f = blockIdx.x, gZ = (M - f) & (M - 1);
+            float my = 0.0f;
+            for (int n0 = 0; n0 < 16; n0 += 2) {
+                bnd_issue(bi, ZX, ZY, f, gZ, d, t, n0);
+                bnd_reduce(bi, bxy, my, t, n0);
+            }
+            atomicMax(&bxy[64 + (t & 63)], __float_as_uint(my));
+        }
+        bar_sync(BAR_SPLIT, NSPLIT);
+        if (t < 64) bnd_scales(bxy, bxy + 64, scb, d, t);
+        bar_sync(BAR_SPLIT, NSPLIT);
         for (int64_t p = blockIdx.x; p < a.npairs; p += gridDim.x, ++pl) {
             const int64_t f = p, gZ = (M - p) & (M - 1);
             const cx<T> wf = tw[f << (a.tw_log - a.logM - 1)];
             const cx<T> wg = c_neg(c_conj(wf));
-            float *sc = scb + 4 * 64 * (pl % L::NB);
-            // ---- bounds over both frequencies: |Xh(f)|, |Xh(M - f)| <= |Z(f)|_1 + |Z(M - f)|_1 entrywise
-            if (t < 128) bx[t] = 0u;
-            if (bar_or(BAR_SPLIT, NSPLIT, failed || abort_flag)) break;
-            {
-                const int k = t & 63;
-                float my = 0.0f;
-#pragma unroll 4
-                for (int n = 0; n < 16; ++n) {
-                    const int i = (t >> 6) + 4 * n;  // X row (one row per warp pair) and Y row
-                    float mx = 0.0f;
-                    if (i < d && k < d) {
-                        const int64_t e = (int64_t)i * d + k;
-                        const cx<T> xa = ldg_cx(ZX + f * E + e), xb = ldg_cx(ZX + gZ * E + e);
-                        const cx<T> ya = ldg_cx(ZY + f * E + e), yb = ldg_cx(ZY + gZ * E + e);
-                        mx = fabsf(hi_part(xa.re)) + fabsf(hi_part(xa.im)) + fabsf(hi_part(xb.re)) +
-                             fabsf(hi_part(xb.im));
-                        my = fmaxf(my, fabsf(hi_part(ya.re)) + fabsf(hi_part(ya.im)) + fabsf(hi_part(yb.re)) +
-                                           fabsf(hi_part(yb.im)));
-                    }
-                    const unsigned wmx = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));  // nonnegative: bits order
-                    if (lane == 0) atomicMax(&bx[i], wmx);
-                }
-                atomicMax(&by[k], __float_as_uint(my));
-            }
-            bar_sync(BAR_SPLIT, NSPLIT);
-            if (t < 64) {
-                // 2 Xh and 2 Yh are split: bound 2 |.|, scaled values <= 1/2
-                const int sx = t < d ? scale_exp(2.0f * __uint_as_float(bx[t])) : 0;
-                const int sy = t < d ? scale_exp(2.0f * __uint_as_float(by[t])) : 0;
-                sc[t] = t < d ? pow2c(-sx) : 0.0f;
-                sc[64 + t] = t < d ? pow2c(-sy) : 0.0f;
-                sc[128 + t] = pow2c(sx - 1);
-                sc[192 + t] = pow2c(sy - 1);
-            }
-            bar_sync(BAR_SPLIT, NSPLIT);
-            // ---- chunks of the pair's passes
+            const float *sc = scb + 4 * 64 * (pl % L::NB);
+            const int64_t pn = p + gridDim.x, fn = pn, gn = (M - pn) & (M - 1);
+            const bool next = pn < a.npairs;
+            unsigned *bn = bxy + 128 * ((pl + 1) & 1);  // the next pair's bounds
+            float myn = 0.0f;
             const int nch = npass(p) * NCH;
+            const int cb = L::PF == 1 ? nch / 2 : 0;  // first chunk that gathers the next pair's bounds
+            if (L::PF > 0) prefetch_pair(p + (int64_t)L::PF * gridDim.x);
+            const int ns = 16 / (nch - cb);           // bound rows n per gathering chunk: 2, 4 or 8
             load_x(raw, ZX, f, gZ, d, 0, t);
             load_y(raw, ZY, f, gZ, d, 0, t);
             for (int c = 0; c < nch; ++c, ++it) {
                 const cx<T> w = (c / NCH) == 0 ? wf : wg;
                 const int slot = it % NSLOT, use = it / NSLOT;
                 unsigned char *sp = smem + slot * L::SLOT;
+                // bound slices of the next pair (in L2 by now): rows n0 .. n0 + ns - 1,
+                // two at a time, loads issued before the digit work they overlap
+                const bool gather = next && c >= cb;
+                const int n0 = (c - cb) * ns;
                 if (!failed && use > 0 && (abort_flag || !mbar_wait(smem_u32(&bar_empty[slot]), (use - 1) & 1)))
                     give_up();
                 const int cn = c + 1;  // next chunk of this pair: pass cn / NCH
                 const int64_t na = (cn / NCH) == 0 ? f : gZ, nb = (cn / NCH) == 0 ? gZ : f;
+                if (gather) bnd_issue(bi, ZX, ZY, fn, gn, d, t, n0);
                 if (!failed) split_chunk_x<T>(raw, sp, sc, w, t);
                 if (cn < nch) load_x(raw, ZX, na, nb, d, (cn % NCH) * KC, t);
+                asm volatile("" ::: "memory");  // the loads above stay ahead of the Y digit stores
+                if (gather) {
+                    bnd_reduce(bi, bn, myn, t, n0);
+                    for (int u = 2; u < ns - 2; u += 2) {
+                        bnd_issue(bi, ZX, ZY, fn, gn, d, t, n0 + u);
+                        bnd_reduce(bi, bn, myn, t, n0 + u);
+                    }
+                    if (ns > 2) bnd_issue(bi, ZX, ZY, fn, gn, d, t, n0 + ns - 2);
+                }
                 if (!failed) split_chunk_y<T>(raw, sp, sc + 64, w, t);
                 if (cn < nch) load_y(raw, ZY, na, nb, d, (cn % NCH) * KC, t);
+                asm volatile("" ::: "memory");
+                if (gather && ns > 2) bnd_reduce(bi, bn, myn, t, n0 + ns - 2);
                 if (!failed) {
                     fence_async_smem();  // digit tiles visible to the tensor cores
                     mbar_arrive(smem_u32(&bar_full[slot]));
                 }
             }
+            if (next) atomicMax(&bn[64 + (t & 63)], __float_as_uint(myn));
+            if (bar_or(BAR_SPLIT, NSPLIT, failed || abort_flag)) break;  // the next pair's bounds complete
+            if (next && t < 64) bnd_scales(bn, bn + 64, scb + 4 * 64 * ((pl + 1) % L::NB), d, t);
+            if (t < 128) bxy[128 * (pl & 1) + t] = 0u;  // this pair's buffer: free for pair p + 2 grid
+            bar_sync(BAR_SPLIT, NSPLIT);
         }
     } else if (warp < WMMA) {
         // --------------------------------------------------------- epilogue
@@ -520,61 +649,58 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
                 }
                 fence_after();
                 const unsigned tb = tmem + ((unsigned)(32 * q) << 16);
-                T cv[NF][32];
-                // every frequency of the pass: columns 0..31 to the transpose, 32..63 kept in registers
+                // two rounds of 32 columns: fold them into the transpose (lanes
+                // along i), release the accumulators after the second fold, then
+                // lanes along j for coalesced global accesses
+#pragma unroll 1
+                for (int r = 0; r < 2; ++r) {
 #pragma unroll
-                for (int fq = 0; fq < NF; ++fq) {
-                    T *xr = xch + ((fq * 2 + (q >> 1)) * 64 + 32 * (q & 1) + lane) * XLD;  // C_r or C_i rows
-#pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {
+                    for (int fq = 0; fq < NF; ++fq) {
+                        T *xr = xch + ((fq * 2 + (q >> 1)) * 64 + 32 * (q & 1) + lane) * XLD;  // C_r or C_i rows
 #pragma unroll
                         for (int m = 0; m < 4; ++m) {
                             T o8[8];
-                            fold8<T, NG>(tb + (unsigned)(fq * L::TCOLS + 32 * hh + 8 * m), o8);
+                            fold8<T, NG>(tb + (unsigned)(fq * L::TCOLS + 32 * r + 8 * m), o8);
 #pragma unroll
-                            for (int c = 0; c < 8; ++c) {
-                                if (hh == 0) xr[8 * m + c] = o8[c];
-                                else cv[fq][8 * m + c] = o8[c];
-                            }
+                            for (int c = 0; c < 8; ++c) xr[8 * m + c] = o8[c];
                         }
                     }
-                }
-                fence_before();
-                mbar_arrive(smem_u32(&bar_tempty));  // accumulators read: the next MMAs may overwrite them
-                // two rounds of 32 columns, lanes along j for coalesced global accesses
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
                     if (r == 1) {
-#pragma unroll
-                        for (int fq = 0; fq < NF; ++fq) {
-                            T *xr = xch + ((fq * 2 + (q >> 1)) * 64 + 32 * (q & 1) + lane) * XLD;
-#pragma unroll
-                            for (int c = 0; c < 32; ++c) xr[c] = cv[fq][c];
-                        }
+                        fence_before();
+                        mbar_arrive(smem_u32(&bar_tempty));  // accumulators read: the next MMAs may overwrite them
                     }
                     bar_sync(BAR_EPI, NEPI);
                     const int jl = et & 31, j = 32 * r + jl;
                     const float sj = fy[j];
-#pragma unroll 2
-                    for (int m = 0; m < 16; ++m) {
-                        const int i = (et >> 5) + 4 * m;
-                        if (i < d && j < d) {
+                    // four outputs at a time, their loads first
+#pragma unroll 1
+                    for (int m0 = 0; m0 < 16; m0 += 4) {
+                        cx<T> v[4], vg[4], cf[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int i = (et >> 5) + 4 * (m0 + u);
                             const float s_ = fx[i] * sj;  // 2^(sigma_i + tau_j - 2), exact
-                            const cx<T> v = {mul_f(xch[i * XLD + jl], s_), mul_f(xch[(64 + i) * XLD + jl], s_)};
+                            v[u] = {mul_f(xch[i * XLD + jl], s_), mul_f(xch[(64 + i) * XLD + jl], s_)};
+                            if constexpr (NF == 2)
+                                vg[u] = {mul_f(xch[(128 + i) * XLD + jl], s_), mul_f(xch[(192 + i) * XLD + jl], s_)};
+                            else if (phase == 1 && i < d && j < d)
+                                cf[u] = ZC[f * E + (int64_t)i * d + j];  // C(f), stored unmerged by this thread
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int i = (et >> 5) + 4 * (m0 + u);
+                            if (i >= d || j >= d) continue;
                             cx<T> *zf = ZC + f * E + (int64_t)i * d + j;
                             if constexpr (NF == 2) {
-                                const cx<T> vg = {mul_f(xch[(128 + i) * XLD + jl], s_),
-                                                  mul_f(xch[(192 + i) * XLD + jl], s_)};
-                                st_cx(zf, merge_real(v, vg, c_conj(wf)));
-                                if (two) st_cx(ZC + gZ * E + (int64_t)i * d + j, merge_real(vg, v, c_conj(wg)));
+                                st_cx(zf, merge_real(v[u], vg[u], c_conj(wf)));
+                                if (two) st_cx(ZC + gZ * E + (int64_t)i * d + j, merge_real(vg[u], v[u], c_conj(wg)));
                             } else if (self) {
-                                st_cx(zf, merge_real(v, v, c_conj(wf)));  // C(M - f) = C(f)
+                                st_cx(zf, merge_real(v[u], v[u], c_conj(wf)));  // C(M - f) = C(f)
                             } else if (phase == 0) {
-                                st_cx(zf, v);  // C(f), merged once C(M - f) is known (same thread)
+                                st_cx(zf, v[u]);  // C(f), merged once C(M - f) is known
                             } else {
-                                const cx<T> cf = *zf;
-                                st_cx(zf, merge_real(cf, v, c_conj(wf)));
-                                if (two) st_cx(ZC + gZ * E + (int64_t)i * d + j, merge_real(v, cf, c_conj(wg)));
+                                st_cx(zf, merge_real(cf[u], v[u], c_conj(wf)));
+                                if (two) st_cx(ZC + gZ * E + (int64_t)i * d + j, merge_real(v[u], cf[u], c_conj(wg)));
                             }
                         }
                     }

@@ -82,6 +82,13 @@ __device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity, int sp
     return false;
 }
 
+// Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) of global
+// memory into L2, without a destination in shared memory
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Named barrier over `count` threads (a multiple of 32); the OR of `pred`
 // over them is returned to every one.
 __device__ __forceinline__ bool bar_or(int id, int count, bool pred)
