@@ -144,22 +144,23 @@ def sources_digest(kernel):
     return h.hexdigest()
 
 
-def measured_traffic(workload, kernel):
-    """DRAM bytes per launch of one kernel class (dram__bytes_read.sum +
-    dram__bytes_write.sum) from the committed ncu capture of it, scaled from
-    the captured workload to this one by the units one launch processes --
-    only while that class's sources are the ones the capture was taken on;
-    else (None, None)."""
-    path = os.path.join(HERE, "profiles", f"traffic_{workload}.json")
+def measured_traffic(kernel, bytes_per_launch):
+    """DRAM traffic per launch of one kernel class: the ratio of DRAM bytes
+    (dram__bytes_read.sum + dram__bytes_write.sum) to the algorithmic bytes
+    that profiles/traffic_<kernel>.json records from an ncu capture of that
+    class on a smaller case of the same d (the traffic of these kernels grows
+    with the units they process), times this run's algorithmic bytes per
+    launch -- only while the class's sources are the ones the capture was
+    taken on; else (None, None)."""
+    path = os.path.join(HERE, "profiles", f"traffic_{kernel}.json")
     try:
         with open(path) as fh:
             doc = json.load(fh)
     except (OSError, ValueError):
         return None, None
-    ent = doc.get("classes", {}).get(kernel)
-    if not ent or ent.get("sources_sha256") != sources_digest(kernel):
+    if doc.get("sources_sha256") != sources_digest(kernel):
         return None, None
-    return ent["dram_bytes_per_launch"], os.path.relpath(path, HERE)
+    return doc["dram_over_algorithmic"] * bytes_per_launch, os.path.relpath(path, HERE)
 
 
 class ClockSampler:
@@ -343,7 +344,7 @@ def run_mre(args, rank, world, local):
                         d=d)
     if roof:
         roof["peak_kind"] = peak_kind
-        roof["traffic"], roof["traffic_source"] = measured_traffic(args.workload, roof["kernel"])
+        roof["traffic"], roof["traffic_source"] = measured_traffic(roof["kernel"], pb.value / max(pn.value, 1))
     # accuracy: availability against the exact solution (exp(G h) powers)
     import scipy.linalg as sl
     step_m = sl.expm(b["G"] * extra["h"])
@@ -454,6 +455,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-autotune", action="store_true",
                     help="built-in product-kernel choices instead of tuning them during warm-up")
+    ap.add_argument("--traffic-step", action="store_true",
+                    help="after warm-up, one step per kernel class inside a cudaProfilerStart/Stop window, "
+                         "printing each class's algorithmic bytes and launches (for an ncu DRAM capture with "
+                         "--profile-from-start off); no timed region")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
@@ -524,6 +529,22 @@ def main():
     for _ in range(max(args.warmup, 3) - 1):
         step()
     torch.cuda.synchronize()
+
+    if args.traffic_step:
+        # one profiler window per kernel class, in KCLASS order
+        out = {}
+        for kc in KCLASS:
+            lib.mrc_profile_begin(kc)
+            torch.cuda.profiler.start()
+            step()
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
+            ms, n, b, f = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+            lib.mrc_profile_end(ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b), ctypes.byref(f))
+            out[KCLASS[kc]] = {"window": len(out), "algorithmic_bytes": b.value, "launches": n.value}
+        if rank == 0:
+            print(json.dumps({"workload": args.workload, "traffic_windows": out}), flush=True)
+        return
 
     # per-class device time of one step (untimed), to pick the dominant kernel
     breakdown = {}
@@ -612,7 +633,7 @@ def main():
                         clocks["sm_mhz"] if clocks else None, d=None if batch else d)
     if roof:
         roof["peak_kind"] = peak_kind
-        roof["traffic"], roof["traffic_source"] = measured_traffic(args.workload, roof["kernel"])
+        roof["traffic"], roof["traffic_source"] = measured_traffic(roof["kernel"], pb.value / max(pn.value, 1))
     # the same roofline for every kernel class of the untimed breakdown step
     by_class = {}
     for kc, (cms, cn, cb, cf) in class_work.items():

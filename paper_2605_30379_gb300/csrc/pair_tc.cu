@@ -122,65 +122,7 @@ __device__ __forceinline__ void split_st(cx<T> za, cx<T> zb, cx<T> w, cx<T> &s, 
     t = c_mul(w, cx<T>{dlt.im, Ar<T>::neg(dlt.re)});
 }
 
-// Balanced digits at their own scale.  t = (x + C) - C with C = 1.5 * 2^k
-// rounds x to the nearest multiple of 2^(k-23) and x - t is exact; the
-// digits of a value |v| <= 1/2 stay within 128 quanta (digits.cuh).
-// Double-float hi + lo: six digits on the grids 2^-8 .. 2^-48, lo joining
-// through an exact TwoSum after two digits, its error after four.
-__device__ __forceinline__ void digits(dd v, float sc, float (&q)[6])
-{
-    float x = v.hi * sc, t;
-    t = __fsub_rn(__fadd_rn(x, 49152.0f), 49152.0f);  // grid 2^-8
-    q[5] = t;
-    x = __fsub_rn(x, t);
-    t = __fsub_rn(__fadd_rn(x, 192.0f), 192.0f);      // grid 2^-16
-    q[4] = t;
-    x = __fsub_rn(x, t);
-    const dd ye = dd_two_sum(x, v.lo * sc);           // exact: x + lo = y + e
-    x = ye.hi;
-    t = __fsub_rn(__fadd_rn(x, 0.75f), 0.75f);        // grid 2^-24
-    q[3] = t;
-    x = __fsub_rn(x, t);
-    t = __fsub_rn(__fadd_rn(x, 0x1.8p-9f), 0x1.8p-9f);  // grid 2^-32
-    q[2] = t;
-    x = __fadd_rn(__fsub_rn(x, t), ye.lo);
-    t = __fsub_rn(__fadd_rn(x, 0x1.8p-17f), 0x1.8p-17f);  // grid 2^-40
-    q[1] = t;
-    x = __fsub_rn(x, t);
-    q[0] = __fsub_rn(__fadd_rn(x, 0x1.8p-25f), 0x1.8p-25f);  // grid 2^-48
-}
-// FP32: four digits on the grids 2^-8 .. 2^-32
-__device__ __forceinline__ void digits(float v, float sc, float (&q)[4])
-{
-    float x = v * sc, t;
-    t = __fsub_rn(__fadd_rn(x, 49152.0f), 49152.0f);
-    q[3] = t;
-    x = __fsub_rn(x, t);
-    t = __fsub_rn(__fadd_rn(x, 192.0f), 192.0f);
-    q[2] = t;
-    x = __fsub_rn(x, t);
-    t = __fsub_rn(__fadd_rn(x, 0.75f), 0.75f);
-    q[1] = t;
-    x = __fsub_rn(x, t);
-    q[0] = __fsub_rn(__fadd_rn(x, 0x1.8p-9f), 0x1.8p-9f);
-}
-
-template <class T>
-__device__ __forceinline__ cx<T> ldg_cx(const cx<T> *p);
-template <>
-__device__ __forceinline__ cx<dd> ldg_cx<dd>(const cx<dd> *p)
-{
-    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
-    return {{v.x, v.y}, {v.z, v.w}};
-}
-template <>
-__device__ __forceinline__ cx<float> ldg_cx<float>(const cx<float> *p)
-{
-    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
-    return {v.x, v.y};
-}
-
-// The same read-only loads as volatile inline PTX: issued where they stand
+// Read-only loads as volatile inline PTX: issued where they stand
 // (the compiler keeps volatile asm in order), so that the next chunk's
 // values are in flight during the current chunk's digit work instead of
 // being requested just before their use
@@ -317,6 +259,33 @@ __device__ __forceinline__ void load_y(Raw<T> &r, const cx<T> *ZY, int64_t ra, i
     }
 }
 
+// Double-float digits value by value (the order the double-float split
+// runs fastest in: d = 64, N = 2^18, pairmul_dd 40.6 ms against 51.7 ms in
+// digit-major order): hi + lo into six digits on the grids 2^-8 .. 2^-48 by
+// the rounding steps described below, lo joining through an exact TwoSum
+// after the second digit and that sum's error after the fourth.
+__device__ __forceinline__ void digits(dd v, float sc, float (&q)[6])
+{
+    float x = v.hi * sc, t;
+    t = __fsub_rn(__fadd_rn(x, 49152.0f), 49152.0f);  // grid 2^-8
+    q[5] = t;
+    x = __fsub_rn(x, t);
+    t = __fsub_rn(__fadd_rn(x, 192.0f), 192.0f);      // grid 2^-16
+    q[4] = t;
+    x = __fsub_rn(x, t);
+    const dd ye = dd_two_sum(x, v.lo * sc);           // exact: x + lo = y + e
+    x = ye.hi;
+    t = __fsub_rn(__fadd_rn(x, 0.75f), 0.75f);        // grid 2^-24
+    q[3] = t;
+    x = __fsub_rn(x, t);
+    t = __fsub_rn(__fadd_rn(x, 0x1.8p-9f), 0x1.8p-9f);  // grid 2^-32
+    q[2] = t;
+    x = __fadd_rn(__fsub_rn(x, t), ye.lo);
+    t = __fsub_rn(__fadd_rn(x, 0x1.8p-17f), 0x1.8p-17f);  // grid 2^-40
+    q[1] = t;
+    x = __fsub_rn(x, t);
+    q[0] = __fsub_rn(__fadd_rn(x, 0x1.8p-25f), 0x1.8p-25f);  // grid 2^-48
+}
 // Packed BF16 digits of 4 values (two uint per digit and component) of one
 // frequency: v[n] = 2 Xh or 2 Yh, scaled by sc[n]
 template <class T, int S>
@@ -373,34 +342,124 @@ __device__ __forceinline__ void store_y(unsigned char *sub, const unsigned (&wr)
     }
 }
 
+// Balanced digits at their own scale: t = (x + C) - C with C = 1.5 * 2^k
+// rounds x to the nearest multiple of 2^(k-23) and x - t is exact, so digit
+// s of a value |v| <= 1/2 is a multiple of 2^(8s - 8S) within 128 of its
+// quanta (digits.cuh).  FP32 takes four digits on the grids 2^-8 .. 2^-32 in
+// digit-major order: the running remainders of all values a split thread
+// holds advance one digit at a time together, and each digit is packed and
+// stored as soon as it exists (pairmul_f32 38.3 -> 37.7 ms at d = 64,
+// N = 2^18 against value by value).
+template <class T> struct DState;
+template <> struct DState<float> { float x; };
+__device__ __forceinline__ DState<float> dstart(float v, float sc) { return {v * sc}; }
+
+constexpr float pow2_ce(int e) { return e >= 0 ? (e == 0 ? 1.0f : 2.0f * pow2_ce(e - 1)) : 0.5f * pow2_ce(e + 1); }
+
+// digit s (grid 2^(8s - 8S)) of the state; the remainder moves on
+template <int S, int s>
+__device__ __forceinline__ float dstep(DState<float> &st)
+{
+    constexpr float C = 1.5f * pow2_ce(8 * (s - S) + 23);
+    const float t = __fsub_rn(__fadd_rn(st.x, C), C);
+    if constexpr (s > 0) st.x = __fsub_rn(st.x, t);
+    return t;
+}
+// X digit tiles of the chunk: per frequency fq of the pass and digit, 8
+// bytes (4 consecutive rows) into each of the blocks -X_i (rows 0..63), X_r
+// (64..127), X_i (128..191) of sub-slot fq
+template <class T, int NFQ, int s>
+__device__ __forceinline__ void xdigit(DState<T> (&st)[NFQ][4][2], unsigned char *slot, int off_n, int off_r, int off_p)
+{
+    using L = TcL<T>;
+#pragma unroll
+    for (int fq = 0; fq < NFQ; ++fq) {
+        float q[4][2];
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            q[n][0] = dstep<L::S, s>(st[fq][n][0]);
+            q[n][1] = dstep<L::S, s>(st[fq][n][1]);
+        }
+        const unsigned r0 = pack2(q[0][0], q[1][0]), r1 = pack2(q[2][0], q[3][0]);
+        const unsigned i0 = pack2(q[0][1], q[1][1]), i1 = pack2(q[2][1], q[3][1]);
+        unsigned char *tl = slot + fq * L::SUB + s * A_TILE;
+        *reinterpret_cast<uint2 *>(tl + off_n) = make_uint2(i0 ^ 0x80008000u, i1 ^ 0x80008000u);
+        *reinterpret_cast<uint2 *>(tl + off_r) = make_uint2(r0, r1);
+        *reinterpret_cast<uint2 *>(tl + off_p) = make_uint2(i0, i1);
+    }
+}
+
+// Y_r and Y_i digit tiles (K-major, row n = j): 8 bytes of 4 consecutive k per digit
+template <class T, int NFQ, int s>
+__device__ __forceinline__ void ydigit(DState<T> (&st)[NFQ][4][2], unsigned char *slot, int off)
+{
+    using L = TcL<T>;
+#pragma unroll
+    for (int fq = 0; fq < NFQ; ++fq) {
+        float q[4][2];
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            q[n][0] = dstep<L::S, s>(st[fq][n][0]);
+            q[n][1] = dstep<L::S, s>(st[fq][n][1]);
+        }
+        unsigned char *br = slot + fq * L::SUB + L::S * A_TILE + s * B_TILE;
+        *reinterpret_cast<uint2 *>(br + off) = make_uint2(pack2(q[0][0], q[1][0]), pack2(q[2][0], q[3][0]));
+        *reinterpret_cast<uint2 *>(br + L::S * B_TILE + off) = make_uint2(pack2(q[0][1], q[1][1]), pack2(q[2][1], q[3][1]));
+    }
+}
+
+template <class T, int NFQ, int... s>
+__device__ __forceinline__ void xdigits(DState<T> (&st)[NFQ][4][2], unsigned char *slot, int on, int orr, int op,
+                                        std::integer_sequence<int, s...>)
+{
+    (xdigit<T, NFQ, TcL<T>::S - 1 - s>(st, slot, on, orr, op), ...);
+}
+template <class T, int NFQ, int... s>
+__device__ __forceinline__ void ydigits(DState<T> (&st)[NFQ][4][2], unsigned char *slot, int off,
+                                        std::integer_sequence<int, s...>)
+{
+    (ydigit<T, NFQ, TcL<T>::S - 1 - s>(st, slot, off), ...);
+}
+
 // The split of one chunk into the slot.  NF == 1: the frequency with
 // twiddle w of the raw rows (ra, rb); NF == 2: f (sub-slot 0) and M - f (1).
 template <class T>
 __device__ __forceinline__ void split_chunk_x(const Raw<T> &r, unsigned char *slot, const float *scx, cx<T> w, int t)
 {
     using L = TcL<T>;
-    constexpr int S = L::S;
-    const int i4 = t >> 4;
-    float sc[4];
+    constexpr int NF = L::NF;
+    const int k = t & 15, i4 = t >> 4;
+    if constexpr (__is_same(T, dd)) {  // value by value
+        float sc[4];
 #pragma unroll
-    for (int n = 0; n < 4; ++n) sc[n] = scx[4 * i4 + n];
-    cx<T> vf[4], vg[4];
+        for (int n = 0; n < 4; ++n) sc[n] = scx[4 * i4 + n];
+        cx<T> vf[4];
 #pragma unroll
-    for (int n = 0; n < 4; ++n) {
-        cx<T> s, tt;
-        split_st(r.xa[n], r.xb[n], w, s, tt);
-        vf[n] = c_add(s, tt);
-        if constexpr (L::NF == 2) vg[n] = {Ar<T>::sub(s.re, tt.re), Ar<T>::sub(tt.im, s.im)};
-    }
-    {
-        unsigned wr[S][2], wi[S][2];
-        pack4<T, S>(vf, sc, wr, wi);
-        store_x<S>(slot, wr, wi, t);
-    }
-    if constexpr (L::NF == 2) {
-        unsigned wr[S][2], wi[S][2];
-        pack4<T, S>(vg, sc, wr, wi);
-        store_x<S>(slot + L::SUB, wr, wi, t);
+        for (int n = 0; n < 4; ++n) {
+            cx<T> s, tt;
+            split_st(r.xa[n], r.xb[n], w, s, tt);
+            vf[n] = c_add(s, tt);
+        }
+        unsigned wr[L::S][2], wi[L::S][2];
+        pack4<T, L::S>(vf, sc, wr, wi);
+        store_x<L::S>(slot, wr, wi, t);
+    } else {  // digit-major
+        DState<T> st[NF][4][2];
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            const float sc = scx[4 * i4 + n];
+            cx<T> s, tt;
+            split_st(r.xa[n], r.xb[n], w, s, tt);
+            const cx<T> vf = c_add(s, tt);
+            st[0][n][0] = dstart(vf.re, sc);
+            st[0][n][1] = dstart(vf.im, sc);
+            if constexpr (NF == 2) {
+                st[NF - 1][n][0] = dstart(Ar<T>::sub(s.re, tt.re), sc);
+                st[NF - 1][n][1] = dstart(Ar<T>::sub(tt.im, s.im), sc);
+            }
+        }
+        xdigits<T, NF>(st, slot, mn_off(4 * i4, k), mn_off(64 + 4 * i4, k), mn_off(128 + 4 * i4, k),
+                       std::make_integer_sequence<int, L::S>{});
     }
 }
 
@@ -408,27 +467,36 @@ template <class T>
 __device__ __forceinline__ void split_chunk_y(const Raw<T> &r, unsigned char *slot, const float *scy, cx<T> w, int t)
 {
     using L = TcL<T>;
-    constexpr int S = L::S;
-    const int lane = t & 31, j = 8 * (t >> 5) + (lane & 7);
-    const float c = scy[j];
-    const float sc[4] = {c, c, c, c};
-    cx<T> vf[4], vg[4];
+    constexpr int NF = L::NF;
+    const int lane = t & 31, j = 8 * (t >> 5) + (lane & 7), k4 = lane >> 3;
+    const float sc = scy[j];
+    if constexpr (__is_same(T, dd)) {  // value by value
+        const float scv[4] = {sc, sc, sc, sc};
+        cx<T> vf[4];
 #pragma unroll
-    for (int n = 0; n < 4; ++n) {
-        cx<T> s, tt;
-        split_st(r.ya[n], r.yb[n], w, s, tt);
-        vf[n] = c_add(s, tt);
-        if constexpr (L::NF == 2) vg[n] = {Ar<T>::sub(s.re, tt.re), Ar<T>::sub(tt.im, s.im)};
-    }
-    {
-        unsigned wr[S][2], wi[S][2];
-        pack4<T, S>(vf, sc, wr, wi);
-        store_y<S>(slot, wr, wi, t);
-    }
-    if constexpr (L::NF == 2) {
-        unsigned wr[S][2], wi[S][2];
-        pack4<T, S>(vg, sc, wr, wi);
-        store_y<S>(slot + L::SUB, wr, wi, t);
+        for (int n = 0; n < 4; ++n) {
+            cx<T> s, tt;
+            split_st(r.ya[n], r.yb[n], w, s, tt);
+            vf[n] = c_add(s, tt);
+        }
+        unsigned wr[L::S][2], wi[L::S][2];
+        pack4<T, L::S>(vf, scv, wr, wi);
+        store_y<L::S>(slot, wr, wi, t);
+    } else {  // digit-major
+        DState<T> st[NF][4][2];
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            cx<T> s, tt;
+            split_st(r.ya[n], r.yb[n], w, s, tt);
+            const cx<T> vf = c_add(s, tt);
+            st[0][n][0] = dstart(vf.re, sc);
+            st[0][n][1] = dstart(vf.im, sc);
+            if constexpr (NF == 2) {
+                st[NF - 1][n][0] = dstart(Ar<T>::sub(s.re, tt.re), sc);
+                st[NF - 1][n][1] = dstart(Ar<T>::sub(tt.im, s.im), sc);
+            }
+        }
+        ydigits<T, NF>(st, slot, k_off(j, 4 * k4), std::make_integer_sequence<int, L::S>{});
     }
 }
 
