@@ -57,6 +57,9 @@ WORKLOADS = {
     # continuous-time Markov renewal equation (mrc_mre_solve, mean-value rule):
     # the paper's four-state exponential benchmark, N = 2^15, h = 0.005, transition function
     "mre_exponential_N32768": (4, 1 << 15, "mre", {"h": 0.005}),
+    # FFT-Gauss-Jordan (mrc_inverse_gj) against FFT-Newton (mrc_inverse, FP64) on the kernels of the
+    # paper's scaling experiments (Section 5): s = 2, 4, 6, 8 shifted Poisson, N = 2^7 .. 2^16
+    "gj_scaling": (0, 0, "gj", {"s": (2, 4, 6, 8), "logN": tuple(range(7, 17))}),
 }
 DEFAULT_WORKLOAD = "lognormal_d64_N262144"
 # the metric both arms report (mrc and the oracle reference arm)
@@ -232,6 +235,27 @@ def max_over_ranks_on(x, world, device):
     return float(t.item())
 
 
+def model_cost(d, N):
+    """Cost model of one inverse, ~ N d^2 (log2 N + d): the FFT and
+    per-frequency product terms of Proposition 2.4."""
+    return float(N) * d * d * (max(1, int(N - 1).bit_length()) + d)
+
+
+def lpt_partition(costs, world):
+    """Greedy longest-processing-time assignment of independent models to
+    ranks: models in decreasing cost (ties by index) go to the least-loaded
+    rank (ties to the lowest rank).  Deterministic, so every rank computes the
+    same partition without a collective.  Returns per-rank sorted index lists."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        parts[r].append(i)
+        load[r] += costs[i]
+    return [sorted(p) for p in parts]
+
+
 def job_throughput(units_per_rank, ms_step, world):
     """Whole-job rate: the units every rank processed per second of the
     slowest rank's step time (replicas: each rank processes units_per_rank)."""
@@ -370,7 +394,8 @@ def run_mre(args, rank, world, local):
                "sample": f"oracle mre_solve on the prefix m < {n} of the same benchmark ({dt:.1f} s)"}
     line = {"metric": "K_h coefficients/s (N*d^2), continuous-time transition function, mean-value rule",
             "value": coeffs / (ms_step * 1e-3), "unit": "coefficients/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak" if total_coeffs is None else "strong",
             "vs_baseline": None, "dtype": "f32+dd" if args.prec == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "d": d, "N": N, "h": extra["h"], "prec": args.prec,
                        "l2": "inputs below L2 size (latency-bound case)", "parallelism": "single"},
@@ -441,6 +466,64 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def run_gj_compare(args, rank, world):
+    """Per (s, N): device time of one FP64 inverse by series Gauss-Jordan and
+    by Newton doubling, each launched as a captured CUDA graph (the launch
+    cost of the host calls removed) and eagerly; the Gauss-Jordan result
+    against the Newton one.  One JSON line; rank 0 only."""
+    import torch
+    from paper_2605_30379_gb300 import mrc, synth
+    if rank != 0:
+        return
+    extra = WORKLOADS[args.workload][3]
+    rows = []
+    reps = max(args.steps, 3)
+    # size the context workspace for the largest case first: a captured graph
+    # holds workspace addresses, so the workspace must not move afterwards
+    Abig = torch.from_numpy(synth.identity_minus(
+        synth.poisson_paper_e2(max(extra["s"]), 1 << max(extra["logN"])))).cuda()
+    mrc.inverse_gj(Abig)
+    mrc.inverse(Abig, prec="fp64")
+    torch.cuda.synchronize()
+    del Abig
+    for s_ in extra["s"]:
+        for lg in extra["logN"]:
+            N = 1 << lg
+            A = torch.from_numpy(synth.identity_minus(synth.poisson_paper_e2(s_, N))).cuda()
+            out = {"gj": torch.empty_like(A), "newton": torch.empty_like(A)}
+            calls = {"gj": lambda: mrc.inverse_gj(A, out=out["gj"]),
+                     "newton": lambda: mrc.inverse(A, prec="fp64", out=out["newton"])}
+            row = {"s": s_, "N": N}
+            for name, fn in calls.items():
+                for _ in range(max(args.warmup, 3)):
+                    fn()
+                torch.cuda.synchronize()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g):
+                    fn()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                g.replay()
+                torch.cuda.synchronize()
+                e0.record()
+                for _ in range(reps):
+                    g.replay()
+                e1.record()
+                torch.cuda.synchronize()
+                row[name + "_graph_ms"] = e0.elapsed_time(e1) / reps
+                e0.record()
+                for _ in range(reps):
+                    fn()
+                e1.record()
+                torch.cuda.synchronize()
+                row[name + "_eager_ms"] = e0.elapsed_time(e1) / reps
+            row["gj_over_newton_graph"] = row["gj_graph_ms"] / row["newton_graph_ms"]
+            row["max_abs_gj_minus_newton"] = float((out["gj"] - out["newton"]).abs().max())
+            rows.append(row)
+    print(json.dumps({"workload": args.workload, "metric": "ms per FP64 inverse (CUDA events)",
+                      "data": "synthetic (shifted Poisson kernel of the paper's state-dimension experiment)",
+                      "reps": reps, "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -471,6 +554,9 @@ def main():
     if WORKLOADS[args.workload][2] == "mre":
         run_mre(args, rank, world, local)
         return
+    if WORKLOADS[args.workload][2] == "gj":
+        run_gj_compare(args, rank, world)
+        return
 
     import torch
     import torch.distributed as dist
@@ -490,6 +576,13 @@ def main():
     d, N, kind, _ = WORKLOADS[args.workload]
     hosts = make_input(args.workload)
     batch = kind == "batch"
+    total_coeffs = None
+    n_models = len(hosts) if batch else 1
+    if batch and world > 1:
+        # independent models: each rank inverts its greedy-LPT share of the batch
+        total_coeffs = sum(a.shape[0] * a.shape[1] * a.shape[2] for a in hosts)
+        share = lpt_partition([model_cost(a.shape[1], a.shape[0]) for a in hosts], world)[rank]
+        hosts = [hosts[i] for i in share]
     if not batch:
         hosts = [hosts]
     coeffs = sum(a.shape[0] * a.shape[1] * a.shape[2] for a in hosts)
@@ -578,7 +671,11 @@ def main():
     barrier()
     clocks = sampler.stop()
     ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps)
-    value = job_throughput(coeffs, ms_step, world)
+    # replicas: every rank's units; a partitioned batch: the whole batch once
+    def rate(ms):
+        return job_throughput(coeffs, ms, world) if total_coeffs is None else total_coeffs / (ms * 1e-3)
+
+    value = rate(ms_step)
 
     # ---- the plain FP64 path on the same inputs
     fp64 = None
@@ -592,7 +689,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ms64 = max_over_ranks(e0.elapsed_time(e1) / args.fp64_steps)
-        fp64 = {"value": job_throughput(coeffs, ms64, world), "ms_per_step": ms64, "steps": args.fp64_steps}
+        fp64 = {"value": rate(ms64), "ms_per_step": ms64, "steps": args.fp64_steps}
         # the FP64 path's own residuals (double-float evaluation), beside the mixed path's below
         r64 = {"res_max_abs": 0.0, "res_left_l1": 0.0, "res_right_l1": 0.0}
         for a, p_ in zip(As, psis):
@@ -659,10 +756,11 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+dd" if args.prec == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "autotune": tune, "d": d if not batch else "3..48",
-                       "N": N if not batch else "round(2^U[10,16])", "models": len(As), "prec": args.prec, "sweeps": sweeps,
+                       "N": N if not batch else "round(2^U[10,16])", "models": n_models, "prec": args.prec, "sweeps": sweeps,
                        "l2": (f"inputs ({coeffs * 8 / 1e9:.1f} GB) larger than L2; no flush" if coeffs * 8 > 2e8
                               else "inputs smaller than L2: latency-bound, no flush"),
-                       "parallelism": "replicas" if world > 1 else "single"},
+                       "parallelism": ("single" if world == 1 else "replicas" if total_coeffs is None
+                                       else f"greedy LPT partition of the models over {world} ranks")},
             "accuracy": {"max_abs_rho_L": rep["res_max_abs"], "rho_L_l1": rep["res_left_l1"],
                          "rho_R_l1": rep["res_right_l1"], "vs_oracle": outputs},
             "fp64_path": fp64,
@@ -673,7 +771,7 @@ def main():
             "roofline_by_class": by_class or None,
             "clocks": clocks,
             "e2e": None if ms_e2e is None else {
-                "value": job_throughput(coeffs, ms_e2e, world), "unit": "coefficients/s",
+                "value": rate(ms_e2e), "unit": "coefficients/s",
                 "h2d_bytes_per_step": coeffs * 8, "d2h_bytes_per_step": coeffs * 8, "ms_per_step": ms_e2e},
             "cpu_baseline": cpu,
         }

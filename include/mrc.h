@@ -117,6 +117,31 @@ mrc_status mrc_inverse(mrc_ctx *ctx, int d, int64_t N, const double *A, double *
                        const mrc_options *opt, void *stream, mrc_report *report);
 
 /*
+ * mrc_inverse_gj -- the same inverse psi = A^{(-1)} mod x^N by Gauss-Jordan
+ * elimination on the augmented matrix [P_A(x) | I] over C[[x]]/<x^N>
+ * (Appendix D "Gauss-Jordan inversion"; cost O(d^3 N log N), Proposition 2.4),
+ * in FP64.  At column i the row r >= i whose series at (r, i) has the largest
+ * constant coefficient in absolute value becomes row i (partial pivoting on
+ * A(0), which ordinary Gauss-Jordan on A(0) shows to exist); the pivot series
+ * is inverted by scalar Newton doubling (Eq. (newton) with d = 1), the row is
+ * normalised and eliminated from the other rows, every truncated series
+ * product by zero-padded FFT of length 2 pow2ceil(N) (Eq. (fft-convolution)).
+ *   d       : 1 .. MRC_GJ_DMAX (the method's cost grows as d^3).
+ *   N, A, psi, stream : as mrc_inverse.
+ *   opt     : host, may be NULL; prec must be MRC_FP64; autotune as mrc_inverse.
+ *   report  : host, may be NULL; if set the call synchronises and fills ms and
+ *             levels (= d, the pivot steps).
+ * Workspace: 2 N d^2 doubles for the augmented matrix, spectra of length
+ * pow2ceil(N) for 2 d^2 + 3 d + 1 series, and the scalar inverse's buffers.
+ * Errors: MRC_ERR_INVALID_ARG, MRC_ERR_NO_MEMORY, MRC_ERR_CUDA; a singular
+ * A(0) fills psi with NaN and sets the status word (returned with a report,
+ * else by mrc_sync_status).
+ */
+#define MRC_GJ_DMAX 64
+mrc_status mrc_inverse_gj(mrc_ctx *ctx, int d, int64_t N, const double *A, double *psi,
+                          const mrc_options *opt, void *stream, mrc_report *report);
+
+/*
  * mrc_mre_solve -- the continuous-time Markov renewal equation
  * K = L + Q (Stieltjes-convolved) K on the grid t = m h (Section 4),
  * discretised by the endpoint mean-value rule (scheme 0, Eq. (mre-discrete)),

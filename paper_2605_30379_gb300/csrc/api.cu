@@ -506,6 +506,72 @@ mrc_status inverse_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A
     return MRC_OK;
 }
 
+// Gauss-Jordan elimination over C[[x]]/<x^N> (Appendix D, "Gauss-Jordan
+// inversion"; cost Proposition 2.4): W = [P_A(x) | I] in FP64, [N][d][2d].
+// Column i: the row with the largest |constant coefficient| among rows >= i
+// becomes row i; its pivot series u = W[i][i] is inverted by scalar Newton
+// (the d = 1 Newton doubling of Eq. (newton)); the row is normalised,
+// W[i][.] <- u^(-1) * W[i][.] mod x^N, and eliminated from every other row,
+// W[r][.] <- W[r][.] - W[r][i] * W[i][.] mod x^N.  Every truncated product is
+// a zero-padded FFT product of length 2 pow2ceil(N) (Eq. (fft-convolution)),
+// over the whole augmented row (2d entries).  After d columns the right block
+// is P_A(x)^(-1) mod x^N.
+size_t ws_gj_series(int d, int64_t N)
+{
+    const int64_t Mr = pow2ceil(N);
+    const size_t n2 = 2 * (size_t)d, EW = (size_t)d * n2;
+    return align_up(256) + align_up(sizeof(double) * N * EW) + 2 * align_up(sizeof(double) * N) +
+           align_up(sizeof(double) * N * d) + align_up((size_t)Mr * 16) + align_up((size_t)Mr * n2 * 16) +
+           align_up((size_t)Mr * d * 16) + align_up((size_t)Mr * EW * 16) +
+           align_up(mrc_fft_scratch_elems(Mr, (int)EW) * 16) + ws_inverse(1, N, MRC_FP64);
+}
+
+mrc_status gj_series_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A, double *psi, cudaStream_t st)
+{
+    const int n2 = 2 * d, EW = d * n2;
+    const int64_t Mr = pow2ceil(N);
+    const void *tw = c->tw[PREC_F64];
+    int *flags = (int *)ar.take(256);  // [0] pivot row, [1] singular flag
+    double *W = (double *)ar.take(sizeof(double) * N * EW);
+    double *u = (double *)ar.take(sizeof(double) * N), *v = (double *)ar.take(sizeof(double) * N);
+    double *cv = (double *)ar.take(sizeof(double) * N * d);
+    void *hv = ar.take((size_t)Mr * 16), *hr = ar.take((size_t)Mr * n2 * 16);
+    void *hc = ar.take((size_t)Mr * d * 16), *hp = ar.take((size_t)Mr * EW * 16);
+    void *bt = ar.take(mrc_fft_scratch_elems(Mr, EW) * 16);
+    CK(mrc_gjs_init(A, W, d, N, flags + 1, st));
+    for (int col = 0; col < d; ++col) {
+        double *row = W + (size_t)col * n2;  // row col at every k: 2d entries, row stride EW
+        CK(mrc_gjs_pivot(A, W, d, N, col, flags, u, cv, flags + 1, c->cur_status, st));
+        // v = u^(-1) mod x^N (scalar Newton; its own workspace above this call's)
+        const size_t mark = ar.off;
+        mrc_status s = inverse_impl(c, ar, 1, N, u, v, MRC_FP64, 0, nullptr, st);
+        if (s != MRC_OK) return s;
+        ar.off = mark;
+        // normalise: row <- v * row mod x^N
+        FftSrc sv{SRC_REAL64, v, 0, N, 1, 0};
+        FftSrc sr{SRC_REAL64, row, 0, N, EW, 0};
+        FftDst dv{DST_CPLX, hv, 1, 0, 0, 0, 1.0, 0};
+        FftDst dr{DST_CPLX, hr, n2, 0, 0, 0, 1.0, 0};
+        CK(fft_any(c, PREC_F64, sv, dv, Mr, 1, -1, bt, tw, st));
+        CK(fft_any(c, PREC_F64, sr, dr, Mr, n2, -1, bt, tw, st));
+        CK(pairmul_any(c, PREC_F64, hv, hr, hp, Mr, 1, 1, n2, tw, st));
+        FftSrc sp{SRC_CPLX, hp, 0, Mr, n2, 0};
+        FftDst drow{DST_REAL64, row, EW, 0, N, 0, 1.0 / (double)Mr, 0};
+        CK(fft_any(c, PREC_F64, sp, drow, Mr, n2, +1, bt, tw, st));
+        // eliminate: W[r][.] -= cv[r] * row mod x^N for r != col (cv[col] = 0)
+        FftSrc sc{SRC_REAL64, cv, 0, N, d, 0};
+        FftDst dc{DST_CPLX, hc, d, 0, 0, 0, 1.0, 0};
+        CK(fft_any(c, PREC_F64, sc, dc, Mr, d, -1, bt, tw, st));
+        CK(fft_any(c, PREC_F64, sr, dr, Mr, n2, -1, bt, tw, st));
+        CK(pairmul_any(c, PREC_F64, hc, hr, hp, Mr, d, 1, n2, tw, st));
+        FftSrc se{SRC_CPLX, hp, 0, Mr, EW, 0};
+        FftDst dw{DST_REAL64_ADD, W, EW, 0, N, 0, -1.0 / (double)Mr, 0};
+        CK(fft_any(c, PREC_F64, se, dw, Mr, EW, +1, bt, tw, st));
+    }
+    CK(mrc_gjs_extract(W, psi, d, N, flags + 1, st));
+    return MRC_OK;
+}
+
 mrc_status read_status(mrc_ctx *c, cudaStream_t st)
 {
     int h = 0;
@@ -811,6 +877,35 @@ mrc_status mrc_inverse(mrc_ctx *c, int d, int64_t N, const double *A, double *ps
             if (s != MRC_OK) return s;
             if (!(report->res_max_abs <= opt->target_residual)) return MRC_ERR_NOT_CONVERGED;
         }
+    }
+    return MRC_OK;
+}
+
+mrc_status mrc_inverse_gj(mrc_ctx *c, int d, int64_t N, const double *A, double *psi, const mrc_options *opt,
+                          void *stream, mrc_report *report)
+{
+    if (!c || !A || !psi || d < 1 || d > MRC_GJ_DMAX || N < 1 || N > ((int64_t)1 << 20)) return MRC_ERR_INVALID_ARG;
+    if (opt && opt->prec != MRC_FP64) return MRC_ERR_INVALID_ARG;
+    TuneScope tscope(c, opt);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaSetDevice(c->device);
+    mrc_status s;
+    if ((s = ensure_tw(c, PREC_F64, st)) != MRC_OK) return s;
+    if ((s = ensure_ws(c, ws_gj_series(d, N))) != MRC_OK) return s;
+    Arena ar{(char *)c->ws};
+    if (report) CK(cudaEventRecord(c->ev0, st));
+    c->cur_status = c->d_status;
+    if ((s = gj_series_impl(c, ar, d, N, A, psi, st)) != MRC_OK) return s;
+    if (report) {
+        CK(cudaEventRecord(c->ev1, st));
+        memset(report, 0, sizeof(*report));
+        report->res_left_l1 = report->res_right_l1 = report->res_max_abs = -1.0;
+        report->levels = d;
+        s = read_status(c, st);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        report->ms = ms;
+        if (s != MRC_OK) return s;
     }
     return MRC_OK;
 }

@@ -302,6 +302,94 @@ __global__ void mre_rhs_kernel(const double *__restrict__ Q, const double *__res
     }
 }
 
+// ---------------------------------------------------------------------------
+// Gauss-Jordan elimination over the truncated series ring C[[x]]/<x^N>
+// (Appendix D, "Gauss-Jordan inversion"), on the augmented matrix
+// W = [P_A(x) | I] stored as W(k) = [A(k) | delta_k0 I], [N][d][2d].
+
+// W(k)[i][j] = A(k)[i][j] (j < d), delta_k0 delta_i(j-d) (j >= d)
+// (and clears the call's singular flag)
+__global__ void gjs_init_kernel(const double *__restrict__ A, double *__restrict__ W, int d, int64_t N, int *flag)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) *flag = 0;
+    const int n2 = 2 * d;
+    const int64_t E = (int64_t)d * n2, n = N * E;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t / E, e = t - k * E;
+        const int i = (int)(e / n2), j = (int)(e - (int64_t)i * n2);
+        W[t] = j < d ? A[k * d * d + (int64_t)i * d + j] : (k == 0 && j - d == i ? 1.0 : 0.0);
+    }
+}
+
+// Pivot of column `col`: the row r >= col with the largest |W(0)[r][col]|
+// (the constant coefficients follow ordinary Gauss-Jordan on A(0)).  A pivot
+// with |p| <= d 2^-52 max|A(0)| marks A(0) singular (status word and the
+// call's flag); the column is then left in place.  One CTA.
+__global__ void __launch_bounds__(256) gjs_pivot_kernel(const double *__restrict__ A0, const double *__restrict__ W,
+                                                        int d, int col, int *__restrict__ piv, int *flag, int *status)
+{
+    __shared__ double sv[32];
+    __shared__ int si[32];
+    double amax = 0.0;
+    for (int t = threadIdx.x; t < d * d; t += blockDim.x) amax = fmax(amax, fabs(A0[t]));
+    int dummy = 0;
+    block_argmax(amax, dummy, sv, si);
+    double best = -1.0;
+    int p = 0x7fffffff;
+    for (int r = col + threadIdx.x; r < d; r += blockDim.x) {
+        const double v = fabs(W[(int64_t)r * 2 * d + col]);
+        if (v > best || (v == best && r < p)) { best = v; p = r; }
+    }
+    block_argmax(best, p, sv, si);
+    if (threadIdx.x == 0) {
+        const bool sing = !(best > (double)d * 0x1p-52 * amax);
+        if (sing) {
+            atomicExch(status, MRC_ST_SINGULAR);
+            *flag = 1;
+        }
+        *piv = sing ? col : p;
+    }
+}
+
+// Row exchange col <-> piv at every k, and the two series the pivot step
+// needs, both read before the exchange (each thread owns one k, so no other
+// thread touches its values): u(k) = W(k)[piv][col] (the pivot series) and
+// cv(k)[r] = W(k)[r][col] after the exchange for r != col, 0 for r = col
+// (the elimination factors; the pivot row is not eliminated from itself).
+__global__ void gjs_swap_kernel(double *__restrict__ W, int d, int64_t N, int col, const int *__restrict__ piv,
+                                double *__restrict__ u, double *__restrict__ cv)
+{
+    const int n2 = 2 * d, p = *piv;
+    const int64_t E = (int64_t)d * n2;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+        double *w = W + k * E;
+        u[k] = w[(int64_t)p * n2 + col];
+        for (int r = 0; r < d; ++r) {
+            const int src = r == p ? col : r;
+            cv[k * d + r] = r == col ? 0.0 : w[(int64_t)src * n2 + col];
+        }
+        if (p != col)
+            for (int j = 0; j < n2; ++j) {
+                const double a = w[(int64_t)col * n2 + j];
+                w[(int64_t)col * n2 + j] = w[(int64_t)p * n2 + j];
+                w[(int64_t)p * n2 + j] = a;
+            }
+    }
+}
+
+// psi(k) = right block of W(k); NaN everywhere if A(0) was found singular
+__global__ void gjs_extract_kernel(const double *__restrict__ W, double *__restrict__ psi, int d, int64_t N,
+                                   const int *flag)
+{
+    const int64_t E = (int64_t)d * d, n = N * E;
+    const bool bad = *flag != 0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t / E, e = t - k * E;
+        const int i = (int)(e / d), j = (int)(e - (int64_t)i * d);
+        psi[t] = bad ? __longlong_as_double(0x7ff8000000000000ll) : W[k * 2 * E + (int64_t)i * 2 * d + d + j];
+    }
+}
+
 inline unsigned grid_for(int64_t n, int bs = 256)
 {
     int64_t b = (n + bs - 1) / bs;
@@ -446,5 +534,35 @@ cudaError_t mrc_one_minus(const double *x, double *y, int64_t n, cudaStream_t st
     mrc_prof_pre(7, st);
     one_minus_kernel<<<grid_for(n), 256, 0, st>>>(x, y, n);
     mrc_prof_post(7, st, 0, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t mrc_gjs_init(const double *A, double *W, int d, int64_t N, int *flag, cudaStream_t st)
+{
+    const int64_t n = N * 2 * (int64_t)d * d;
+    mrc_prof_pre(7, st);
+    gjs_init_kernel<<<grid_for(n), 256, 0, st>>>(A, W, d, N, flag);
+    mrc_prof_post(7, st, (double)n * 12.0, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t mrc_gjs_pivot(const double *A0, double *W, int d, int64_t N, int col, int *piv, double *u, double *cv,
+                          int *flag, int *status, cudaStream_t st)
+{
+    mrc_prof_pre(7, st);
+    gjs_pivot_kernel<<<1, 256, 0, st>>>(A0, W, d, col, piv, flag, status);
+    mrc_prof_post(7, st, 0, 0);
+    mrc_prof_pre(7, st);
+    gjs_swap_kernel<<<grid_for(N, 128), 128, 0, st>>>(W, d, N, col, piv, u, cv);
+    mrc_prof_post(7, st, (double)N * (4.0 * d + 1 + d) * 8.0, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t mrc_gjs_extract(const double *W, double *psi, int d, int64_t N, const int *flag, cudaStream_t st)
+{
+    const int64_t n = N * (int64_t)d * d;
+    mrc_prof_pre(7, st);
+    gjs_extract_kernel<<<grid_for(n), 256, 0, st>>>(W, psi, d, N, flag);
+    mrc_prof_post(7, st, (double)n * 16.0, 0);
     return cudaGetLastError();
 }

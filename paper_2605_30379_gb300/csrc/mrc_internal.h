@@ -73,6 +73,24 @@ struct FftDst {
     const void *base = nullptr;  // DST_REAL64_BASE32: binary32 rows (FftArgs::dst_base)
 };
 
+// Segments per segmented launch: the argument blocks of a launch live in its
+// parameter space (at most 32764 bytes: MRC_SEG_MAX x (sizeof(FftArgs) + 4))
+#define MRC_SEG_MAX 144
+template <class A>
+struct SegParams;
+
+// The passes of one transform (at most two): argument blocks, radices, the
+// algorithmic charge of each, and the launch shape (nchunk entry chunks of ec
+// entries x nrow rows per pass)
+struct FftPasses {
+    int np;
+    int logR[2];
+    FftArgs a[2];
+    double bytes[2], flops[2];
+    unsigned nchunk, nrow[2];
+    int ec;
+};
+
 // elements of FFT scratch a transform of M points over E entries needs
 static inline size_t mrc_fft_scratch_elems(int64_t M, int E) { return (size_t)M * (size_t)E; }
 
@@ -98,7 +116,13 @@ void mrc_prof_post(int kclass, cudaStream_t st, double bytes, double flops);
     cudaError_t mrc_pairdiag_##SUF(const void *zx, const void *zy, void *zc, int64_t M, int r, int c, \
                                    const void *tw, int tw_log, cudaStream_t st);                      \
     cudaError_t mrc_twiddles_##SUF(void *tw, int tw_log, cudaStream_t st);                            \
-    cudaError_t mrc_init_##SUF(void);
+    cudaError_t mrc_init_##SUF(void);                                                                 \
+    cudaError_t mrc_fft_build_##SUF(const FftSrc &src, const FftDst &dst, int64_t M, int E, int dir,    \
+                                    void *scratch, const void *tw, int tw_log, FftPasses &ps);        \
+    cudaError_t mrc_fft_seg_##SUF(int logR, const SegParams<FftArgs> &P, unsigned nctas, double bytes,  \
+                                  double flops, cudaStream_t st);                                     \
+    cudaError_t mrc_pairmul_seg_##SUF(int cfg, const SegParams<PairArgs> &P, unsigned nctas,            \
+                                      double bytes, double flops, cudaStream_t st);
 
 MRC_DECLARE_PREC(f64)
 MRC_DECLARE_PREC(f32)
@@ -182,5 +206,13 @@ cudaError_t mrc_occupation_k(const double *P, int d, int64_t N, const double *al
                              cudaStream_t st);
 cudaError_t mrc_one_minus(const double *x, double *y, int64_t n, cudaStream_t st);
 cudaError_t mrc_f64_to_f32(const double *x, float *y, int64_t n, cudaStream_t st);
+// series Gauss-Jordan on W = [P_A | I] ([N][d][2d]): build W (clearing the
+// call's singular flag), choose the pivot of column col and exchange rows
+// (with the pivot series u [N] and the elimination factors cv [N][d]), take
+// psi from the right block (NaN if the flag is set)
+cudaError_t mrc_gjs_init(const double *A, double *W, int d, int64_t N, int *flag, cudaStream_t st);
+cudaError_t mrc_gjs_pivot(const double *A0, double *W, int d, int64_t N, int col, int *piv, double *u, double *cv,
+                          int *flag, int *status, cudaStream_t st);
+cudaError_t mrc_gjs_extract(const double *W, double *psi, int d, int64_t N, const int *flag, cudaStream_t st);
 cudaError_t mrc_mre_operator(const double *Q, double *A, int d, int64_t N, int scheme, cudaStream_t st);
 cudaError_t mrc_mre_rhs(const double *Q, const double *L, double *R, int d, int c, int64_t N, cudaStream_t st);

@@ -7,7 +7,10 @@
 //     base-256 digits per value, digit pairs of weight s + t >= 5 (21 pairs
 //     in 6 weight groups), about 2^-41 relative to the row and column bounds;
 //   FP32 (the Newton-level products of Eq. (newton) and the correction):
-//     four digits, pairs s + t >= 3 (10 pairs in 4 groups), about 2^-29.
+//     four digits, pairs s + t >= 3 (10 pairs in 4 groups), about 2^-26
+//     relative to the row and column bounds.  Three digits (6 pairs, about
+//     2^-21) made the product 1.27x faster at d = 64, N = 2^18 but left
+//     e_rel at 1.7e-9 after the sweep (gate 1e-10).
 //
 // The rows of X are scaled by 2^-sigma_i and the columns of Y by 2^-tau_j
 // (powers of two from bounds over both frequencies of the pair) and every
@@ -593,6 +596,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
     const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
     const int d = a.r;
     const int64_t E = (int64_t)d * d, M = a.M;
+    // K chunks of KC per frequency: FP32 takes the ones that hold k < d (the
+    // others' digit tiles are zero: d = 48 runs 3 of 4); double-float keeps
+    // all four (with its chunk count left to run time the product went from
+    // 41.4 to 46.9 ms at d = 64, N = 2^18)
+    const int nck = __is_same(T, dd) ? NCH : (d + KC - 1) / KC;
     bool failed = false;
     auto give_up = [&]() {
         failed = true;
@@ -631,7 +639,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
         if (blockIdx.x < a.npairs) {
             const int64_t f = blockIdx.x, gZ = (M - f) & (M - 1);
             float my = 0.0f;
-            for (int n0 = 0; n0 < 16; n0 += 2) {
+            for (int n0 = 0; n0 < 4 * nck; n0 += 2) {
                 bnd_issue(bi, ZX, ZY, f, gZ, d, t, n0);
                 bnd_reduce(bi, bxy, my, t, n0);
             }
@@ -649,14 +657,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
             const bool next = pn < a.npairs;
             unsigned *bn = bxy + 128 * ((pl + 1) & 1);  // the next pair's bounds
             float myn = 0.0f;
-            const int nch = npass(p) * NCH;
+            const int nch = npass(p) * nck;
             const int cb = L::PF == 1 ? nch / 2 : 0;  // first chunk that gathers the next pair's bounds
             if (L::PF > 0) prefetch_pair(p + (int64_t)L::PF * gridDim.x);
-            const int ns = 16 / (nch - cb);           // bound rows n per gathering chunk: 2, 4 or 8
+            // bound rows n per gathering chunk (2, 4 or 8): the 4 nck row steps that cover
+            // k < d over the nch - cb gathering chunks (nck per pass, half of them with PF = 1)
+            const int ns = (L::PF == 1 ? 8 : 4) >> (npass(p) - 1);
             load_x(raw, ZX, f, gZ, d, 0, t);
             load_y(raw, ZY, f, gZ, d, 0, t);
             for (int c = 0; c < nch; ++c, ++it) {
-                const cx<T> w = (c / NCH) == 0 ? wf : wg;
+                const cx<T> w = c < nck ? wf : wg;
                 const int slot = it % NSLOT, use = it / NSLOT;
                 unsigned char *sp = smem + slot * L::SLOT;
                 // bound slices of the next pair (in L2 by now): rows n0 .. n0 + ns - 1,
@@ -665,11 +675,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
                 const int n0 = (c - cb) * ns;
                 if (!failed && use > 0 && (abort_flag || !mbar_wait(smem_u32(&bar_empty[slot]), (use - 1) & 1)))
                     give_up();
-                const int cn = c + 1;  // next chunk of this pair: pass cn / NCH
-                const int64_t na = (cn / NCH) == 0 ? f : gZ, nb = (cn / NCH) == 0 ? gZ : f;
+                const int cn = c + 1;  // next chunk of this pair: the first pass while cn < nck
+                const bool first = cn < nck;
+                const int64_t na = first ? f : gZ, nb = first ? gZ : f;
+                const int kn = (first ? cn : cn - nck) * KC;
                 if (gather) bnd_issue(bi, ZX, ZY, fn, gn, d, t, n0);
                 if (!failed) split_chunk_x<T>(raw, sp, sc, w, t);
-                if (cn < nch) load_x(raw, ZX, na, nb, d, (cn % NCH) * KC, t);
+                if (cn < nch) load_x(raw, ZX, na, nb, d, kn, t);
                 asm volatile("" ::: "memory");  // the loads above stay ahead of the Y digit stores
                 if (gather) {
                     bnd_reduce(bi, bn, myn, t, n0);
@@ -680,7 +692,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
                     if (ns > 2) bnd_issue(bi, ZX, ZY, fn, gn, d, t, n0 + ns - 2);
                 }
                 if (!failed) split_chunk_y<T>(raw, sp, sc + 64, w, t);
-                if (cn < nch) load_y(raw, ZY, na, nb, d, (cn % NCH) * KC, t);
+                if (cn < nch) load_y(raw, ZY, na, nb, d, kn, t);
                 asm volatile("" ::: "memory");
                 if (gather && ns > 2) bnd_reduce(bi, bn, myn, t, n0 + ns - 2);
                 if (!failed) {
@@ -789,7 +801,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
                     break;
                 }
                 fence_after();
-                for (int c = 0; c < NCH; ++c, ++it) {
+                for (int c = 0; c < nck; ++c, ++it) {
                     const int slot = it % NSLOT, use = it / NSLOT;
                     if (abort_flag || !mbar_wait(smem_u32(&bar_full[slot]), use & 1)) {
                         give_up();

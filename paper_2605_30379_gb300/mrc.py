@@ -71,6 +71,7 @@ def load():
         lib.mrc_inverse_workspace_bytes.argtypes = [I, I64, I]
         lib.mrc_inverse_workspace_bytes.restype = SZ
         lib.mrc_inverse.argtypes = [P, I, I64, P, P, ctypes.POINTER(_Options), P, ctypes.POINTER(_Report)]
+        lib.mrc_inverse_gj.argtypes = [P, I, I64, P, P, ctypes.POINTER(_Options), P, ctypes.POINTER(_Report)]
         lib.mrc_mre_solve.argtypes = [P, I, I, I64, P, P, I, P, ctypes.POINTER(_Options), P]
         lib.mrc_inverse_host.argtypes = [P, I, I64, P, P, ctypes.POINTER(_Options), P, ctypes.POINTER(_Report)]
         lib.mrc_inverse_batched.argtypes = [P, I, P, P, P, P, ctypes.POINTER(_Options), P, ctypes.POINTER(_Report)]
@@ -150,6 +151,22 @@ def inverse(A, prec="fp64", sweeps=1, target_residual=0.0, report=False, out=Non
                             ctypes.byref(_opts(prec, sweeps, target_residual, autotune)), _stream(stream),
                             ctypes.byref(rep) if report else None)
     _check(st, "mrc_inverse")
+    return (psi, rep.as_dict()) if report else psi
+
+
+def inverse_gj(A, report=False, out=None, stream=None, autotune=False):
+    """psi = A^{(-1)} mod x^N by series Gauss-Jordan elimination
+    (mrc_inverse_gj, FP64).  A: CUDA float64 [N, d, d], d <= 64."""
+    A = _seq(A, "A")
+    N, d, d2 = A.shape
+    if d != d2:
+        raise ValueError("A must be square per coefficient")
+    psi = torch.empty_like(A) if out is None else out
+    rep = _Report()
+    st = load().mrc_inverse_gj(context(A.device.index), d, N, _ptr(A), _ptr(psi),
+                               ctypes.byref(_opts("fp64", 0, 0.0, autotune)), _stream(stream),
+                               ctypes.byref(rep) if report else None)
+    _check(st, "mrc_inverse_gj")
     return (psi, rep.as_dict()) if report else psi
 
 

@@ -261,6 +261,18 @@ def poisson_paper_e2(s, N):
     return q
 
 
+def _batch_shape(ss, d_range, logN_range):
+    rng = np.random.default_rng(ss)
+    d = int(rng.integers(d_range[0], d_range[1] + 1))
+    N = int(round(2.0 ** rng.uniform(*logN_range)))
+    return rng, d, N
+
+
+def batch_shapes(n=256, seed=0, d_range=(3, 48), logN_range=(10.0, 16.0)):
+    """The (d, N) of batch_models(n, seed) without building the models."""
+    return [_batch_shape(ss, d_range, logN_range)[1:] for ss in np.random.SeedSequence(seed).spawn(n)]
+
+
 def batch_models(n=256, seed=0, d_range=(3, 48), logN_range=(10.0, 16.0), h=0.05,
                  max_total_coeffs=None):
     """Mixed batch: d ~ U{d_lo..d_hi}, N = round(2^U[a,b]), even-indexed draws
@@ -271,9 +283,7 @@ def batch_models(n=256, seed=0, d_range=(3, 48), logN_range=(10.0, 16.0), h=0.05
     out = []
     total = 0
     for b, ss in enumerate(children):
-        rng = np.random.default_rng(ss)
-        d = int(rng.integers(d_range[0], d_range[1] + 1))
-        N = int(round(2.0 ** rng.uniform(*logN_range)))
+        rng, d, N = _batch_shape(ss, d_range, logN_range)
         if max_total_coeffs is not None and total + N * d * d > max_total_coeffs:
             break
         if b % 2 == 0:

@@ -108,6 +108,91 @@ def test_singular_A0_reports_error(mrc):
     assert np.abs(psi - oracle.inverse_left(A2)).max() <= TOL64
 
 
+# ------------------------------------------------- series Gauss-Jordan (App. D)
+@pytest.mark.parametrize("d,N,seed", [
+    (1, 1, 0), (1, 70, 1), (2, 1, 2), (2, 33, 3),   # degenerate and ragged horizons
+    (3, 1000, 4), (4, 257, 5), (6, 2048, 6), (8, 513, 7), (13, 300, 8),
+])
+def test_inverse_gj_matches_oracle(mrc, d, N, seed):
+    if d == 1:
+        rng = np.random.default_rng(seed)
+        q = np.zeros((N, 1, 1))
+        q[1:, 0, 0] = rng.uniform(0, 1, N - 1) / max(1, N)
+    else:
+        q, _ = synth.weibull_model(d, N, seed=seed)
+    A = synth.identity_minus(q)
+    psi, rep = mrc.inverse_gj(dev(A), report=True)
+    assert rep["levels"] == d
+    assert np.abs(psi.cpu().numpy() - oracle.inverse_left(A)).max() <= TOL64
+
+
+def test_inverse_gj_row_exchanges(mrc):
+    """A(0) with a zero diagonal (a scaled permutation plus a small dense
+    part): every column's pivot comes from another row, so the row exchanges
+    of the augmented matrix are exercised; signed dense later coefficients."""
+    rng = np.random.default_rng(21)
+    d, N = 5, 600
+    A = rng.standard_normal((N, d, d)) * (0.6 ** np.arange(N))[:, None, None] * 0.2
+    perm = [2, 0, 4, 1, 3]
+    A[0] = 0.05 * rng.standard_normal((d, d))
+    np.fill_diagonal(A[0], 0.0)
+    for i, j in enumerate(perm):
+        A[0, i, j] = 2.0 + i
+    ref = oracle.inverse_left(A)
+    psi = mrc.inverse_gj(dev(A)).cpu().numpy()
+    assert np.abs(psi - ref).max() <= TOL64 * max(1.0, np.abs(ref).max())
+
+
+def test_inverse_gj_paper_scaling_kernels(mrc):
+    """The kernels of the paper's scaling experiments (Section 5): s = 3 with
+    shifted discrete Gamma sojourns at N = 2048, and the shifted Poisson
+    state-dimension kernel at N = 256 for s = 2, 4, 6, 8; against the oracle,
+    with left and right residuals in the range the paper reports for its
+    accelerated inverses (Table 3: at most 5.2e-13)."""
+    cases = [synth.gamma_paper_e1(2048)] + [synth.poisson_paper_e2(s, 256) for s in (2, 4, 6, 8)]
+    for q in cases:
+        A = synth.identity_minus(q)
+        Ad = dev(A)
+        psi = mrc.inverse_gj(Ad)
+        assert np.abs(psi.cpu().numpy() - oracle.inverse_left(A)).max() <= TOL64
+        _, _, r = mrc.residual(Ad, psi, sides=3, prec="fp64", want_rho=False)
+        assert r["res_left_l1"] <= 1e-12 and r["res_right_l1"] <= 1e-12, r
+
+
+def test_inverse_gj_singular_A0(mrc):
+    A = np.zeros((64, 3, 3))
+    A[0] = [[1, 2, 3], [2, 4, 6], [0, 0, 1.0]]
+    with pytest.raises(mrc.MrcError) as ei:
+        mrc.inverse_gj(dev(A), report=True)
+    assert ei.value.status == 2
+    psi = mrc.inverse_gj(dev(A))  # without a report: NaN output, status word read afterwards
+    with pytest.raises(mrc.MrcError):
+        mrc.sync_status()
+    assert torch.isnan(psi).all()
+    q, _ = synth.weibull_model(3, 64, seed=1)
+    A2 = synth.identity_minus(q)
+    psi2 = mrc.inverse_gj(dev(A2), report=True)[0].cpu().numpy()
+    assert np.abs(psi2 - oracle.inverse_left(A2)).max() <= TOL64
+
+
+def test_inverse_gj_long_horizon_matches_newton(mrc):
+    """d = 4, N = 2^16 (two-pass transforms): Gauss-Jordan against FFT-Newton
+    on the same input, the 4096-prefix against the oracle (Proposition 2.3),
+    and sampled residual entries at k = N - 1 against the oracle's sums."""
+    d, N = 4, 1 << 16
+    q, _ = synth.weibull_model(d, N, seed=31)
+    A = synth.identity_minus(q)
+    Ad = dev(A)
+    gj = mrc.inverse_gj(Ad)
+    nw = mrc.inverse(Ad, prec="fp64")
+    assert float((gj - nw).abs().max()) <= TOL64
+    n = 4096
+    assert np.abs(gj[:n].cpu().numpy() - oracle.inverse_left(A[:n])).max() <= TOL64
+    g = gj.cpu().numpy()
+    for i, j in ((0, 0), (3, 1), (2, 2)):
+        assert abs(oracle.residual_left_entry(A, g, N - 1, i, j)) <= 1e-12
+
+
 def test_bounded_wait_times_out_and_context_stays_usable(mrc):
     """Failure detection without a fault: the tensor-core kernels' bounded
     mbarrier wait, run on a barrier nothing arrives on, gives up after its
@@ -129,7 +214,8 @@ def test_bounded_wait_times_out_and_context_stays_usable(mrc):
 
 
 # ------------------------------------------------------------ inverse mixed
-@pytest.mark.parametrize("d,N,seed", [(4, 1024, 0), (3, 777, 1), (16, 2048, 2), (33, 300, 3)])
+@pytest.mark.parametrize("d,N,seed", [(4, 1024, 0), (3, 777, 1), (16, 2048, 2), (33, 300, 3),
+                                      (20, 1500, 4), (48, 2000, 5), (64, 1300, 6)])
 def test_inverse_mixed_matches_oracle(mrc, d, N, seed):
     q, _ = synth.weibull_model(d, N, seed=seed)
     A = synth.identity_minus(q)
@@ -280,13 +366,15 @@ def test_batched_reports_singular_model(mrc):
         assert np.abs(o.cpu().numpy() - oracle.inverse_left(good)).max() <= TOL64
 
 
-@pytest.mark.parametrize("d,N", [(40, 300), (64, 200), (48, 513), (33, 129), (96, 100), (130, 33)])
+@pytest.mark.parametrize("d,N", [(40, 300), (64, 200), (48, 513), (33, 129), (96, 100), (130, 33),
+                                 (32, 300), (47, 200)])
 def test_tensor_core_dd_residual_matches_oracle(mrc, d, N):
     """The double-float residual product for 32 <= d <= 512 runs as exact
     digit products on the tcgen05 tensor cores; both residuals must match
     the oracle's to 1e-12 (d = 33: padded tiles with a ragged edge; N = 129:
     a partial last pair range and the self-paired middle frequency; d = 96
-    and 130: several 64 x 64 output tiles and K chunks, ragged)."""
+    and 130: several 64 x 64 output tiles and K chunks, ragged; d = 32, 33,
+    47, 48: two or three K chunks of 16 per frequency)."""
     rng = np.random.default_rng(d)
     q, _ = synth.weibull_model(d, N, seed=d)
     A = synth.identity_minus(q)
