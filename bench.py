@@ -359,7 +359,10 @@ def run_mre(args, rank, world, local):
     torch.cuda.synchronize()
     launches = lib.mrc_launch_count() - l0
     pms, pn, pb, pf = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
-    lib.mrc_profile_end(ctypes.byref(pms), ctypes.byref(pn), ctypes.byref(pb), ctypes.byref(pf))
+    if not batch:
+        lib.mrc_profile_end(ctypes.byref(pms), ctypes.byref(pn), ctypes.byref(pb), ctypes.byref(pf))
+    elif dominant in class_work:
+        pms.value, pn.value, pb.value, pf.value = class_work[dominant]
     clocks = sampler.stop()
     ms_step = e0.elapsed_time(e1) / args.steps
     coeffs = N * d * d
@@ -642,7 +645,7 @@ def main():
     # per-class device time of one step (untimed), to pick the dominant kernel
     breakdown = {}
     class_work = {}
-    for kc in ([] if (args.no_breakdown or batch) else KCLASS):
+    for kc in ([] if args.no_breakdown else KCLASS):
         ms, n, b, f = prof(kc, step)
         if n:
             breakdown[KCLASS[kc]] = {"ms": ms, "launches": n}
@@ -655,7 +658,10 @@ def main():
     sampler.start()
     barrier()
     torch.cuda.synchronize()
-    lib.mrc_profile_begin(dominant)
+    # a batch is timed as its graph replays; its per-launch class timing comes
+    # from the eager breakdown step above (a timed class makes the batch run eagerly)
+    if not batch:
+        lib.mrc_profile_begin(dominant)
     l0 = lib.mrc_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -664,10 +670,14 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     launches = lib.mrc_launch_count() - l0
-    if batch:  # graph replays: the kernels were counted once, at capture
-        launches = launches_per_step * args.steps
+    if batch:  # graph replays bypass the launch counter: the eager breakdown step's launches per step
+        per_step = sum(v[1] for v in class_work.values()) if class_work else launches_per_step
+        launches = per_step * args.steps
     pms, pn, pb, pf = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
-    lib.mrc_profile_end(ctypes.byref(pms), ctypes.byref(pn), ctypes.byref(pb), ctypes.byref(pf))
+    if not batch:
+        lib.mrc_profile_end(ctypes.byref(pms), ctypes.byref(pn), ctypes.byref(pb), ctypes.byref(pf))
+    elif dominant in class_work:
+        pms.value, pn.value, pb.value, pf.value = class_work[dominant]
     barrier()
     clocks = sampler.stop()
     ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps)

@@ -194,13 +194,21 @@ mrc_status mrc_inverse_host(mrc_ctx *ctx, int d, int64_t N, const double *A_host
  * their own d[b] and N[b] (host arrays), A[b]/psi[b] device pointers held in
  * HOST arrays of pointers (no counterpart in the paper beyond applying
  * Eq. (newton) to each model).
- * Scheduling: models are placed longest-first on the least-loaded of up to 8
- * internal streams (cost ~ N d^2 (log2 N + d)), each stream with its own slice
- * of the workspace, and the whole batch is captured once into a CUDA graph.
- * A later call with the same (d, N, A, psi, prec, sweeps) lists replays the
- * graph with one launch on `stream`; the context keeps the 8 most recent
- * graphs, and a workspace reallocation discards them.  The launch-count
- * counter counts kernels at capture time only.
+ * Scheduling, stage by stage: every launch covers all models of a wave at
+ * one stage -- one launch per FFT pass of each Newton level size m (every
+ * model with m0 <= m < N at once, whatever its d), one per FP32-pipe product
+ * tile configuration, one for all Gauss-Jordan inverses of the A(0), one for
+ * the direct recursions, one per conversion; the tensor-core products
+ * (square 32 <= d, one CTA per SM) run model after model.  The residual and
+ * correction stages group models by transform length pow2ceil(N).  Models
+ * enter waves in decreasing cost (~ N d^2 (log2 N + d)) while the waves'
+ * buffers (mrc_inverse_workspace_bytes per model) fit the budget: the
+ * context cap if set, else min(96 GB, half the free device memory), at
+ * least the largest model.  The whole batch is captured once into a CUDA
+ * graph; a later call with the same (d, N, A, psi, prec, sweeps) lists
+ * replays it with one launch on `stream`.  The context keeps the 8 most
+ * recent graphs, and a workspace reallocation discards them.  The
+ * launch-count counter counts kernels at capture time only.
  * report (nullable, host) receives one mrc_report per model (ms = the whole
  * batch); with a report the call synchronises and returns the first nonzero
  * per-model status (e.g. MRC_ERR_SINGULAR_A0).

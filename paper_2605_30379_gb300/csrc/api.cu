@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <map>
+#include <memory>
 #include <vector>
 
 #include "../../include/mrc.h"
@@ -25,6 +26,7 @@ struct BatchGraph {
     std::vector<const double *> A;
     std::vector<double *> psi;
     int prec = 0, sweeps = 0;
+    void *ws = nullptr;  // the workspace the graph's buffers live in
     cudaGraphExec_t exec = nullptr;
 };
 
@@ -65,6 +67,8 @@ struct mrc_ctx {
 
 void mrc_prof_set_capturing(bool on);
 void mrc_prof_set_untimed(cudaStream_t st);
+bool mrc_prof_timing();
+static mrc_status ensure_split_streams(mrc_ctx *c);
 
 namespace {
 
@@ -676,6 +680,333 @@ void tune_save(mrc_ctx *cx)
     cx->tune_dirty = false;
 }
 
+// ===========================================================================
+// The batched inverse, stage by stage (mrc_inverse_batched): each launch of a
+// stage covers every model of a wave at that stage -- one segmented launch
+// per FFT pass and per product tile configuration, one batched launch for
+// the Gauss-Jordan inverses of the A(0), one for the direct recursions and
+// one per conversion.  The tensor-core products (persistent kernels over one
+// product's frequency pairs, one CTA per SM) run model after model.  Models
+// are taken in decreasing cost into waves whose buffers fit the workspace
+// budget; inside a wave each model owns the buffers inverse_impl would give
+// it, laid out the same way.
+
+struct SegOps {
+    cudaError_t (*build)(const FftSrc &, const FftDst &, int64_t, int, int, void *, const void *, int, FftPasses &);
+    cudaError_t (*fft_seg)(int, const SegParams<FftArgs> &, unsigned, double, double, cudaStream_t);
+    cudaError_t (*pair_seg)(int, const SegParams<PairArgs> &, unsigned, double, double, cudaStream_t);
+};
+const SegOps SOPS[3] = {
+    {mrc_fft_build_f64, mrc_fft_seg_f64, mrc_pairmul_seg_f64},
+    {mrc_fft_build_f32, mrc_fft_seg_f32, mrc_pairmul_seg_f32},
+    {mrc_fft_build_dd, mrc_fft_seg_dd, mrc_pairmul_seg_dd},
+};
+
+struct BModel {
+    int d = 0, E = 0;
+    int64_t N = 0, m0 = 0, Mr = 0, Mmax = 0;
+    const double *A = nullptr;
+    double *psi = nullptr;
+    int *status = nullptr;
+    double cost = 0;
+    size_t ws = 0;
+    double *gjw = nullptr;
+    float *A32 = nullptr, *psi32 = nullptr, *rho32 = nullptr;
+    void *b0 = nullptr, *b1 = nullptr, *b2 = nullptr, *bt = nullptr;  // Newton level spectra and scratch
+    void *ahat = nullptr, *ascr = nullptr;                              // double-float spectrum of A, scratch
+    void *psihat32 = nullptr, *rY = nullptr, *rC = nullptr;             // residual
+    void *cY = nullptr, *cC = nullptr, *cT = nullptr;                   // correction
+};
+
+// the model's buffers from `base`, in inverse_impl's order (ws_inverse bytes)
+void bmodel_layout(BModel &m, int prec, char *base)
+{
+    const size_t E = (size_t)m.E, Mr = (size_t)m.Mr, Mm = (size_t)m.Mmax, N = (size_t)m.N;
+    Arena ar{base};
+    m.gjw = (double *)ar.take(sizeof(double) * 2 * E);
+    if (prec == MRC_FP64) {
+        m.b0 = ar.take(Mm * E * 16);
+        m.b1 = ar.take(Mm * E * 16);
+        m.b2 = ar.take(Mm * E * 16);
+        m.bt = ar.take(mrc_fft_scratch_elems(m.Mmax, m.E) * 16);
+        return;
+    }
+    m.ahat = ar.take(Mr * E * 16);
+    m.ascr = ar.take(mrc_fft_scratch_elems(m.Mr, m.E) * 16);
+    m.psi32 = (float *)ar.take(N * E * sizeof(float));
+    const size_t mark = ar.off;
+    m.A32 = (float *)ar.take(N * E * sizeof(float));
+    m.b0 = ar.take(Mm * E * 8);
+    m.b1 = ar.take(Mm * E * 8);
+    m.b2 = ar.take(Mm * E * 8);
+    m.bt = ar.take(mrc_fft_scratch_elems(m.Mmax, m.E) * 8);
+    ar.off = mark;  // the levels' buffers are free once the levels are done
+    m.rho32 = (float *)ar.take(N * E * sizeof(float));
+    m.psihat32 = ar.take(Mr * E * 8);
+    const size_t mark2 = ar.off;
+    m.rY = ar.take(Mr * E * 16);
+    m.rC = ar.take(Mr * E * 16);
+    ar.off = mark2;  // the residual's spectra are free before the correction
+    m.cY = ar.take(Mr * E * 8);
+    m.cC = ar.take(Mr * E * 8);
+    m.cT = ar.take(mrc_fft_scratch_elems(m.Mr, m.E) * 8);
+}
+
+struct FftJob {
+    FftSrc src;
+    FftDst dst;
+    int E;
+    void *scratch;
+};
+
+// One transform per job, all of packed length M and direction dir: one
+// segmented launch per pass (in groups of MRC_SEG_MAX transforms)
+mrc_status fft_stage(mrc_ctx *c, int prec, int64_t M, int dir, const std::vector<FftJob> &jobs, cudaStream_t st)
+{
+    if (jobs.empty()) return MRC_OK;
+    std::vector<FftPasses> ps(jobs.size());
+    for (size_t i = 0; i < jobs.size(); ++i)
+        CK(SOPS[prec].build(jobs[i].src, jobs[i].dst, M, jobs[i].E, dir, jobs[i].scratch, c->tw[prec], MRC_TW_LOG,
+                            ps[i]));
+    auto P = std::make_unique<SegParams<FftArgs>>();
+    for (int k = 0; k < ps[0].np; ++k)
+        for (size_t i0 = 0; i0 < jobs.size(); i0 += MRC_SEG_MAX) {
+            const size_t i1 = std::min(jobs.size(), i0 + (size_t)MRC_SEG_MAX);
+            unsigned total = 0;
+            double by = 0, fl = 0;
+            P->nseg = (int)(i1 - i0);
+            for (size_t i = i0; i < i1; ++i) {
+                P->first[i - i0] = total;
+                P->a[i - i0] = ps[i].a[k];
+                total += ps[i].nchunk * ps[i].nrow[k];
+                by += ps[i].bytes[k];
+                fl += ps[i].flops[k];
+            }
+            CK(SOPS[prec].fft_seg(ps[0].logR[k], *P, total, by, fl, st));
+        }
+    return MRC_OK;
+}
+
+// the product kernel choice pairmul_any makes for a square d x d product of M points
+int product_choice(mrc_ctx *cx, int prec, int64_t M, int d)
+{
+    if (cx->autotune) {
+        auto it = cx->tune.find(tune_key(prec, d, d, d, M));
+        if (it != cx->tune.end()) return it->second;
+    }
+    if (tensor_choice_exists(prec, d, d, d) && (prec == PREC_DD || M >= 256)) return 3;
+    return d <= 16 ? 0 : (d <= 32 ? 1 : 2);
+}
+
+struct PairJob {
+    const void *zx, *zy;
+    void *zc;
+    int d;
+    int *status;
+};
+
+// One square product per job, all of M points: the tensor-core ones of
+// d <= 64 in one persistent segmented launch per K-chunk count ceil(d / 16),
+// a timeout reported in the first product's status word;
+// d > 64 model by model; the FP32-pipe ones in one segmented launch per tile
+// configuration
+mrc_status product_stage(mrc_ctx *c, int prec, int64_t M, const std::vector<PairJob> &jobs, cudaStream_t st)
+{
+    std::vector<size_t> bycfg[3], tcp[5];
+    int *const old = c->cur_status;
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        const int ch = product_choice(c, prec, M, jobs[i].d);
+        if (ch == 3 && jobs[i].d <= 64) {
+            tcp[(jobs[i].d + 15) / 16].push_back(i);
+        } else if (ch == 3) {
+            c->cur_status = jobs[i].status;
+            const cudaError_t e = launch_tensor(c, prec, jobs[i].zx, jobs[i].zy, jobs[i].zc, M, jobs[i].d, c->tw[prec], st);
+            c->cur_status = old;
+            CK(e);
+        } else {
+            bycfg[ch].push_back(i);
+        }
+    }
+    auto P = std::make_unique<SegParams<PairArgs>>();
+    for (int g = 0; g < 5; ++g)
+        for (size_t i0 = 0; i0 < tcp[g].size(); i0 += MRC_SEG_MAX) {
+            const size_t i1 = std::min(tcp[g].size(), i0 + (size_t)MRC_SEG_MAX);
+            P->nseg = (int)(i1 - i0);
+            for (size_t q = i0; q < i1; ++q) {
+                const PairJob &j = jobs[tcp[g][q]];
+                P->first[q - i0] = 0;  // every product has the same pair count (same M)
+                P->a[q - i0] = mrc_tcp_args(j.zx, j.zy, j.zc, M, j.d, c->tw[prec], MRC_TW_LOG);
+            }
+            CK(mrc_tcp_seg(prec == PREC_DD, *P, jobs[tcp[g][i0]].status, st));
+        }
+    const int bsz[3] = {16, 32, 64};
+    for (int cfg = 0; cfg < 3; ++cfg)
+        for (size_t i0 = 0; i0 < bycfg[cfg].size(); i0 += MRC_SEG_MAX) {
+            const size_t i1 = std::min(bycfg[cfg].size(), i0 + (size_t)MRC_SEG_MAX);
+            unsigned total = 0;
+            double by = 0, fl = 0;
+            P->nseg = (int)(i1 - i0);
+            for (size_t q = i0; q < i1; ++q) {
+                const PairJob &j = jobs[bycfg[cfg][q]];
+                PairArgs a{};
+                a.zx = j.zx; a.zy = j.zy; a.zc = j.zc; a.tw = c->tw[prec]; a.tw_log = MRC_TW_LOG; a.M = M;
+                int l = 0;
+                while (((int64_t)1 << l) < M) ++l;
+                a.logM = l;
+                a.npairs = M >= 2 ? M / 2 + 1 : 1;
+                a.r = a.m = a.c = j.d;
+                const int nt = (j.d + bsz[cfg] - 1) / bsz[cfg];
+                P->first[q - i0] = total;
+                P->a[q - i0] = a;
+                total += (unsigned)a.npairs * (unsigned)(nt * nt);
+                by += (double)M * 3.0 * j.d * j.d * OPS[prec].cxb;
+                fl += 8.0 * (double)j.d * j.d * j.d * (double)(M + 1);
+            }
+            CK(SOPS[prec].pair_seg(cfg, *P, total, by, fl, st));
+        }
+    return MRC_OK;
+}
+
+// The whole inverse of one wave of models, stage by stage
+mrc_status batch_wave(mrc_ctx *c, std::vector<BModel> &W, int prec, int sweeps, cudaStream_t st)
+{
+    const int pl = prec == MRC_FP64 ? PREC_F64 : PREC_F32;
+    const bool f32 = prec == MRC_MIXED;
+    const size_t n = W.size();
+    int dmax = 1;
+    int64_t mmin = INT64_MAX, nmax = 0;  // mmin: the smallest first level (m0 < N: a power of two)
+    for (auto &m : W) {
+        dmax = std::max(dmax, m.d);
+        if (m.m0 < m.N) mmin = std::min(mmin, m.m0);
+        nmax = std::max(nmax, m.N);
+    }
+    // psi(0) = A(0)^(-1) and the direct recursion for psi(1 .. m0-1)
+    {
+        auto G = std::make_unique<SegParams<GjArgs>>();
+        auto B = std::make_unique<SegParams<BaseArgs>>();
+        for (size_t i0 = 0; i0 < n; i0 += MRC_SEG_MAX) {
+            const size_t i1 = std::min(n, i0 + (size_t)MRC_SEG_MAX);
+            G->nseg = B->nseg = (int)(i1 - i0);
+            for (size_t i = i0; i < i1; ++i) {
+                G->first[i - i0] = B->first[i - i0] = (unsigned)(i - i0);
+                G->a[i - i0] = GjArgs{W[i].A, W[i].psi, W[i].gjw, W[i].d, W[i].status};
+                B->a[i - i0] = BaseArgs{W[i].A, W[i].psi, W[i].d, (int)W[i].m0};
+            }
+            CK(mrc_gauss_jordan_batch(*G, dmax, st));
+            CK(mrc_base_case_batch(*B, dmax, st));
+        }
+    }
+    if (f32) {
+        // binary32 copies of A and of psi(0 .. m0-1) for the FP32 levels
+        auto C = std::make_unique<SegParams<CvtArgs>>();
+        std::vector<CvtArgs> cv;
+        for (auto &m : W) {
+            cv.push_back(CvtArgs{m.A, m.A32, m.N * m.E});
+            cv.push_back(CvtArgs{m.psi, m.psi32, m.m0 * m.E});
+        }
+        for (size_t i0 = 0; i0 < cv.size(); i0 += MRC_SEG_MAX) {
+            const size_t i1 = std::min(cv.size(), i0 + (size_t)MRC_SEG_MAX);
+            unsigned total = 0;
+            C->nseg = (int)(i1 - i0);
+            for (size_t i = i0; i < i1; ++i) {
+                C->first[i - i0] = total;
+                C->a[i - i0] = cv[i];
+                total += (unsigned)((cv[i].n + MRC_CVT_CHUNK - 1) / MRC_CVT_CHUNK);
+            }
+            CK(mrc_f64_to_f32_batch(*C, total, st));
+        }
+        // the double-float spectra of A that every residual sweep uses, by
+        // transform length, on the low-priority side stream while the FP32
+        // levels run (as in the single-model inverse)
+        mrc_status s = ensure_split_streams(c);
+        if (s != MRC_OK) return s;
+        CK(cudaEventRecord(c->ev_fork, st));
+        CK(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+        for (int64_t Mr = pow2ceil(nmax); Mr >= 1; Mr >>= 1) {
+            std::vector<FftJob> jobs;
+            for (auto &m : W)
+                if (m.Mr == Mr)
+                    jobs.push_back({FftSrc{SRC_REAL64, m.A, 0, m.N, m.E, 0}, FftDst{DST_CPLX, m.ahat, m.E, 0, 0, 0, 1.0, 0},
+                                    m.E, m.ascr});
+            if ((s = fft_stage(c, PREC_DD, Mr, -1, jobs, c->aux)) != MRC_OK) return s;
+        }
+        CK(cudaEventRecord(c->ev_join, c->aux));
+    }
+    // Newton levels m -> min(2m, N) of Eq. (newton), every model at level m at once
+    for (int64_t m = mmin; mmin < INT64_MAX && m < nmax; m <<= 1) {
+        std::vector<size_t> act;
+        for (size_t i = 0; i < n; ++i)
+            if (W[i].m0 <= m && m < W[i].N) act.push_back(i);
+        if (act.empty()) continue;
+        const int64_t M = m;
+        std::vector<FftJob> ja, jb, ji, jr, jo;
+        std::vector<PairJob> p1, p2;
+        for (size_t i : act) {
+            BModel &b = W[i];
+            const int64_t m2 = std::min<int64_t>(2 * m, b.N);
+            const void *Asrc = f32 ? (const void *)b.A32 : (const void *)b.A;
+            const void *Bsrc = f32 ? (const void *)b.psi32 : (const void *)b.psi;
+            const int sm = f32 ? SRC_REAL32 : SRC_REAL64;
+            ja.push_back({FftSrc{sm, Asrc, 0, m2, b.E, 0}, FftDst{DST_CPLX, b.b0, b.E, 0, 0, 0, 1.0, 0}, b.E, b.bt});
+            jb.push_back({FftSrc{sm, Bsrc, 0, m, b.E, 0}, FftDst{DST_CPLX, b.b1, b.E, 0, 0, 0, 1.0, 0}, b.E, b.bt});
+            p1.push_back({b.b0, b.b1, b.b2, b.d, b.status});
+            ji.push_back({FftSrc{SRC_CPLX, b.b2, 0, M, b.E, 0}, FftDst{DST_CPLX, b.b0, b.E, 0, 0, 0, 1.0 / (double)M, 0},
+                          b.E, b.bt});
+            jr.push_back({FftSrc{SRC_CPLX, b.b0, M / 2, M / 2, b.E, 1}, FftDst{DST_CPLX, b.b2, b.E, 0, 0, 0, 1.0, 0}, b.E,
+                          b.bt});
+            p2.push_back({b.b1, b.b2, b.b0, b.d, b.status});
+            jo.push_back({FftSrc{SRC_CPLX, b.b0, 0, M, b.E, 0},
+                          FftDst{f32 ? DST_REAL32 : DST_REAL64, f32 ? (void *)b.psi32 : (void *)b.psi, b.E, 0, m2 - m, m,
+                                 1.0 / (double)M, 0},
+                          b.E, b.bt});
+        }
+        mrc_status s;
+        if ((s = fft_stage(c, pl, M, -1, ja, st)) != MRC_OK) return s;      // A-hat
+        if ((s = fft_stage(c, pl, M, -1, jb, st)) != MRC_OK) return s;      // B-hat
+        if ((s = product_stage(c, pl, M, p1, st)) != MRC_OK) return s;      // (A B)-hat
+        if ((s = fft_stage(c, pl, M, +1, ji, st)) != MRC_OK) return s;      // A*B, packed time
+        if ((s = fft_stage(c, pl, M, -1, jr, st)) != MRC_OK) return s;      // R-hat, R = -(A*B)[m, 2m)
+        if ((s = product_stage(c, pl, M, p2, st)) != MRC_OK) return s;      // (B R)-hat
+        if ((s = fft_stage(c, pl, M, +1, jo, st)) != MRC_OK) return s;      // B[m, m2)
+    }
+    if (!f32) return MRC_OK;
+    CK(cudaStreamWaitEvent(st, c->ev_join, 0));  // the spectra of A
+    // residual rho_L = e0 - A * psi in double-float (Proposition 2.6) and the
+    // FP32 correction psi <- psi + psi * rho_L, by transform length
+    for (int sw = 0; sw < sweeps; ++sw) {
+        const bool first = sw == 0;
+        for (int64_t Mr = pow2ceil(nmax); Mr >= 1; Mr >>= 1) {
+            std::vector<FftJob> fy, fc, gy, gc;
+            std::vector<PairJob> pr, pc;
+            for (auto &b : W) {
+                if (b.Mr != Mr) continue;
+                fy.push_back({FftSrc{first ? SRC_REAL32 : SRC_REAL64, first ? (const void *)b.psi32 : (const void *)b.psi,
+                                     0, b.N, b.E, 0},
+                              FftDst{DST_CPLX, b.rY, b.E, 0, 0, 0, 1.0, 0, b.psihat32}, b.E, b.ascr});
+                pr.push_back({b.ahat, b.rY, b.rC, b.d, b.status});
+                fc.push_back({FftSrc{SRC_CPLX, b.rC, 0, Mr, b.E, 0},
+                              FftDst{DST_REAL32, b.rho32, b.E, 0, b.N, 0, -1.0 / (double)Mr, b.d}, b.E, b.ascr});
+                gy.push_back({FftSrc{SRC_REAL32, b.rho32, 0, b.N, b.E, 0}, FftDst{DST_CPLX, b.cY, b.E, 0, 0, 0, 1.0, 0},
+                              b.E, b.cT});
+                pc.push_back({b.psihat32, b.cY, b.cC, b.d, b.status});
+                gc.push_back({FftSrc{SRC_CPLX, b.cC, 0, Mr, b.E, 0},
+                              FftDst{first ? DST_REAL64_BASE32 : DST_REAL64_ADD, b.psi, b.E, 0, b.N, 0, 1.0 / (double)Mr, 0,
+                                     nullptr, first ? (const void *)b.psi32 : nullptr},
+                              b.E, b.cT});
+            }
+            if (fy.empty()) continue;
+            mrc_status s;
+            if ((s = fft_stage(c, PREC_DD, Mr, -1, fy, st)) != MRC_OK) return s;
+            if ((s = product_stage(c, PREC_DD, Mr, pr, st)) != MRC_OK) return s;
+            if ((s = fft_stage(c, PREC_DD, Mr, +1, fc, st)) != MRC_OK) return s;
+            if ((s = fft_stage(c, PREC_F32, Mr, -1, gy, st)) != MRC_OK) return s;
+            if ((s = product_stage(c, PREC_F32, Mr, pc, st)) != MRC_OK) return s;
+            if ((s = fft_stage(c, PREC_F32, Mr, +1, gc, st)) != MRC_OK) return s;
+        }
+    }
+    return MRC_OK;
+}
+
 } // namespace
 
 // ===========================================================================
@@ -1001,76 +1332,104 @@ mrc_status mrc_inverse_batched(mrc_ctx *c, int nmodels, const int *d, const int6
     if ((s = ensure_tw(c, prec == MRC_FP64 ? PREC_F64 : PREC_F32, st)) != MRC_OK) return s;
     if (prec == MRC_MIXED && (s = ensure_tw(c, PREC_DD, st)) != MRC_OK) return s;
 
-    // Longest-first onto the least-loaded of up to MRC_BATCH_STREAMS streams;
-    // cost model ~ N d^2 (log2 N + d), the FFT and product terms of Prop 2.4.
-    const int S = std::min(nmodels, MRC_BATCH_STREAMS);
-    std::vector<int> order(nmodels), assign(nmodels);
-    for (int b = 0; b < nmodels; ++b) order[b] = b;
-    auto cost = [&](int b) {
+    // Models in decreasing cost (~ N d^2 (log2 N + d), the FFT and product
+    // terms of Prop 2.4) into waves whose buffers fit the budget: the context
+    // cap if set, else at most 96 GB and half the free device memory (but
+    // always room for the largest model)
+    std::vector<BModel> bm(nmodels);
+    size_t wmax = 0;
+    for (int b = 0; b < nmodels; ++b) {
+        BModel &m = bm[b];
+        m.d = d[b];
+        m.E = d[b] * d[b];
+        m.N = N[b];
+        m.m0 = base_size(d[b], N[b]);
+        m.Mr = pow2ceil(N[b]);
+        m.Mmax = newton_maxM(d[b], N[b]);
+        m.A = A[b];
+        m.psi = psi[b];
         double lg = 1.0;
         for (int64_t x = 1; x < N[b]; x <<= 1) lg += 1.0;
-        return (double)N[b] * d[b] * d[b] * (lg + d[b]);
-    };
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
-    std::vector<double> load(S, 0.0);
-    std::vector<size_t> wsz(S, 0);
+        m.cost = (double)N[b] * d[b] * d[b] * (lg + d[b]);
+        m.ws = align_up(ws_inverse(d[b], N[b], prec));
+        wmax = std::max(wmax, m.ws);
+    }
+    std::vector<int> order(nmodels);
+    for (int b = 0; b < nmodels; ++b) order[b] = b;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return bm[x].cost > bm[y].cost; });
+    size_t budget = (size_t)96 << 30;
+    {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) budget = std::min(budget, fr / 2 + c->ws_size / 2);
+    }
+    const size_t head = align_up(sizeof(int) * nmodels);
+    if (c->cap) budget = std::min(budget, c->cap > head ? c->cap - head : 0);
+    budget = std::max(budget, wmax);
+    std::vector<std::vector<int>> waves;
+    std::vector<size_t> woff(nmodels, 0);
+    size_t used = 0, wsneed = 0;
     for (int b : order) {
-        int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-        assign[b] = k;
-        load[k] += cost(b);
-        wsz[k] = std::max(wsz[k], ws_inverse(d[b], N[b], prec));
+        if (waves.empty() || used + bm[b].ws > budget) {
+            waves.emplace_back();
+            used = 0;
+        }
+        woff[b] = used;
+        used += bm[b].ws;
+        waves.back().push_back(b);
+        wsneed = std::max(wsneed, used);
     }
-    std::vector<size_t> woff(S, 0);
-    size_t total = align_up(sizeof(int) * nmodels);
-    for (int k = 0; k < S; ++k) {
-        woff[k] = total;
-        total += align_up(wsz[k]);
-    }
-    if ((s = ensure_ws(c, total)) != MRC_OK) return s;
+    if ((s = ensure_ws(c, head + wsneed)) != MRC_OK) return s;
+    if (prec == MRC_MIXED && (s = ensure_split_streams(c)) != MRC_OK) return s;
     int *status = (int *)c->ws;
+    for (int b = 0; b < nmodels; ++b) bm[b].status = status + b;
 
+    auto run_waves = [&](cudaStream_t s0) -> mrc_status {
+        for (size_t w = 0; w < waves.size(); ++w) {
+            std::vector<BModel> W;
+            for (int b : waves[w]) {
+                W.push_back(bm[b]);
+                bmodel_layout(W.back(), prec, (char *)c->ws + head + woff[b]);
+            }
+            mrc_status r = batch_wave(c, W, prec, sweeps, s0);
+            if (r != MRC_OK) return r;
+        }
+        return MRC_OK;
+    };
+    if (mrc_prof_timing()) {
+        // a kernel class is being timed: run the stages eagerly on `stream`
+        // (a graph replay would not pass through the per-launch events)
+        if (report) CK(cudaEventRecord(c->ev0, st));
+        CK(cudaMemsetAsync(status, 0, sizeof(int) * nmodels, st));
+        if ((s = run_waves(st)) != MRC_OK) return s;
+    }
     BatchGraph *hit = nullptr;
     for (auto &g : c->graphs) {
-        if (g.prec != prec || g.sweeps != sweeps || (int)g.d.size() != nmodels) continue;
+        if (mrc_prof_timing()) break;
+        if (g.prec != prec || g.sweeps != sweeps || (int)g.d.size() != nmodels || g.ws != c->ws) continue;
         bool same = true;
         for (int b = 0; b < nmodels && same; ++b)
             same = g.d[b] == d[b] && g.N[b] == N[b] && g.A[b] == A[b] && g.psi[b] == psi[b];
         if (same) { hit = &g; break; }
     }
-    if (!hit) {
+    if (!hit && !mrc_prof_timing()) {
         if (c->autotune) {
             // tune each distinct shape now: the graph capture below cannot time kernels
-            const size_t off = align_up(sizeof(int) * nmodels);
             std::vector<std::pair<int, int64_t>> seen;
             for (int b = 0; b < nmodels; ++b) {
                 std::pair<int, int64_t> key{d[b], N[b]};
                 if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
                 seen.push_back(key);
-                pretune_model(c, prec, d[b], N[b], (char *)c->ws + off, total - off, st);
+                pretune_model(c, prec, d[b], N[b], (char *)c->ws + head, c->ws_size - head, st);
             }
         }
-        for (int k = 0; k < MRC_BATCH_STREAMS; ++k) {
-            if (!c->bst[k]) CK(cudaStreamCreateWithFlags(&c->bst[k], cudaStreamNonBlocking));
-            if (!c->bev[k]) CK(cudaEventCreateWithFlags(&c->bev[k], cudaEventDisableTiming));
-        }
+        if (!c->bst[0]) CK(cudaStreamCreateWithFlags(&c->bst[0], cudaStreamNonBlocking));
         cudaStream_t s0 = c->bst[0];
         CK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
         mrc_prof_set_capturing(true);
         c->capturing = true;
         mrc_status cs = MRC_OK;
-        cudaError_t ce = cudaMemsetAsync(status, 0, sizeof(int) * nmodels, s0);
-        if (ce == cudaSuccess) ce = cudaEventRecord(c->bev[0], s0);
-        for (int k = 1; k < S && ce == cudaSuccess; ++k) ce = cudaStreamWaitEvent(c->bst[k], c->bev[0], 0);
-        if (ce != cudaSuccess) cs = MRC_ERR_CUDA;
-        for (int b = 0; b < nmodels && cs == MRC_OK; ++b) {
-            Arena ar{(char *)c->ws + woff[assign[b]]};
-            cs = inverse_impl(c, ar, d[b], N[b], A[b], psi[b], prec, sweeps, nullptr, c->bst[assign[b]], status + b);
-        }
-        for (int k = 1; k < S && cs == MRC_OK; ++k) {
-            if (cudaEventRecord(c->bev[k], c->bst[k]) != cudaSuccess ||
-                cudaStreamWaitEvent(s0, c->bev[k], 0) != cudaSuccess)
-                cs = MRC_ERR_CUDA;
-        }
+        if (cudaMemsetAsync(status, 0, sizeof(int) * nmodels, s0) != cudaSuccess) cs = MRC_ERR_CUDA;
+        if (cs == MRC_OK) cs = run_waves(s0);
         mrc_prof_set_capturing(false);
         c->capturing = false;
         cudaGraph_t graph = nullptr;
@@ -1087,7 +1446,8 @@ mrc_status mrc_inverse_batched(mrc_ctx *c, int nmodels, const int *d, const int6
         g.psi.assign(psi, psi + nmodels);
         g.prec = prec;
         g.sweeps = sweeps;
-        ce = cudaGraphInstantiate(&g.exec, graph, 0);
+        g.ws = c->ws;
+        cudaError_t ce = cudaGraphInstantiate(&g.exec, graph, 0);
         cudaGraphDestroy(graph);
         if (ce != cudaSuccess) return MRC_ERR_CUDA;
         if (c->graphs.size() >= 8) {
@@ -1097,8 +1457,10 @@ mrc_status mrc_inverse_batched(mrc_ctx *c, int nmodels, const int *d, const int6
         c->graphs.push_back(std::move(g));
         hit = &c->graphs.back();
     }
-    if (report) CK(cudaEventRecord(c->ev0, st));
-    CK(cudaGraphLaunch(hit->exec, st));
+    if (hit) {
+        if (report) CK(cudaEventRecord(c->ev0, st));
+        CK(cudaGraphLaunch(hit->exec, st));
+    }
     if (!report) return MRC_OK;
     CK(cudaEventRecord(c->ev1, st));
     CK(cudaStreamSynchronize(st));

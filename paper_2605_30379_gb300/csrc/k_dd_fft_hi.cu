@@ -1,3 +1,3 @@
 // k_dd_fft_hi.cu -- FFT pass kernels for dd, radices 2^7 .. 2^10.
 #include "kernels.cuh"
-void mrc_fft_fill_dd_hi(FftEntry (*t)[11]) { fft_fill_shifted<dd, 7>(t, std::make_integer_sequence<int, 4>{}); }
+void mrc_fft_fill_dd_hi(FftEntry (*t)[11], FftSegEntry *ts) { fft_fill_shifted<dd, 7>(t, ts, std::make_integer_sequence<int, 4>{}); }

@@ -1,3 +1,3 @@
 // k_f32_fft_lo.cu -- FFT pass kernels for float, radices 2^0 .. 2^6.
 #include "kernels.cuh"
-void mrc_fft_fill_f32_lo(FftEntry (*t)[11]) { fft_fill_shifted<float, 0>(t, std::make_integer_sequence<int, 7>{}); }
+void mrc_fft_fill_f32_lo(FftEntry (*t)[11], FftSegEntry *ts) { fft_fill_shifted<float, 0>(t, ts, std::make_integer_sequence<int, 7>{}); }

@@ -353,7 +353,7 @@ __device__ __forceinline__ void fft_stage(const FftArgs &a, cx<T> *sm, const cx<
 }
 
 template <class T, int LOGR, int EC, bool INV>
-__device__ __forceinline__ void fft_pass_body(const FftArgs &a)
+__device__ __forceinline__ void fft_pass_body(const FftArgs &a, int64_t j, int e0)
 {
     using P = FftPlan<T, LOGR, EC>;
     constexpr int R = P::R;
@@ -363,8 +363,6 @@ __device__ __forceinline__ void fft_pass_body(const FftArgs &a)
     cx<T> *spt = stw + R;                             // [R]  inter-pass twiddles
     const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
     const int tid = threadIdx.x;
-    const int64_t j = blockIdx.y;   // entry chunk fastest: CTAs launched together cover whole rows
-    const int e0 = blockIdx.x * EC;
     const int ecount = min(EC, a.E - e0);
     const int64_t jm = j & (a.Ns - 1);
     // first-stage global loads before the twiddle tables are filled (both latencies overlap)
@@ -399,8 +397,9 @@ __device__ __forceinline__ void fft_pass_body(const FftArgs &a)
 template <class T, int LOGR, int EC>
 __global__ void __launch_bounds__(FftPlan<T, LOGR, EC>::NT) fft_pass_kernel(FftArgs a)
 {
-    if (a.dir > 0) fft_pass_body<T, LOGR, EC, true>(a);
-    else fft_pass_body<T, LOGR, EC, false>(a);
+    // entry chunk fastest: CTAs launched together cover whole rows
+    if (a.dir > 0) fft_pass_body<T, LOGR, EC, true>(a, blockIdx.y, blockIdx.x * EC);
+    else fft_pass_body<T, LOGR, EC, false>(a, blockIdx.y, blockIdx.x * EC);
 }
 
 // The same pass with a minimum of resident CTAs per SM (MRC_FFT32_MINB x 512
@@ -418,8 +417,43 @@ __global__ void __launch_bounds__(FftPlan<T, LOGR, EC>::NT,
                                   MRC_FFT32_MINB > 0 ? (MRC_FFT32_MINB * 512) / FftPlan<T, LOGR, EC>::NT : 1)
     fft_pass_kernel_mb(FftArgs a)
 {
-    if (a.dir > 0) fft_pass_body<T, LOGR, EC, true>(a);
-    else fft_pass_body<T, LOGR, EC, false>(a);
+    if (a.dir > 0) fft_pass_body<T, LOGR, EC, true>(a, blockIdx.y, blockIdx.x * EC);
+    else fft_pass_body<T, LOGR, EC, false>(a, blockIdx.y, blockIdx.x * EC);
+}
+
+// ---------------------------------------------------------------------------
+// Segmented launches: one launch covers several independent transforms (or
+// products) of one shape class -- the models of a batch at one Newton level.
+// The segments' argument blocks travel in the kernel's parameter space (a
+// __grid_constant__ block of at most MRC_SEG_MAX segments, read through the
+// constant cache like a single launch's arguments); CTA b runs CTA
+// b - first[s] of segment s = max{s : first[s] <= b}, in the order of the
+// single-segment launch.
+template <class T, int LOGR, int EC>
+__device__ __forceinline__ void fft_seg_run(const SegParams<FftArgs> &P)
+{
+    const int s = seg_find(P, blockIdx.x);
+    const FftArgs &a = P.a[s];
+    const unsigned loc = blockIdx.x - P.first[s];
+    const unsigned nchunk = (unsigned)((a.E + EC - 1) / EC);
+    const unsigned j = loc / nchunk;
+    const int e0 = (int)(loc - j * nchunk) * EC;
+    if (a.dir > 0) fft_pass_body<T, LOGR, EC, true>(a, j, e0);
+    else fft_pass_body<T, LOGR, EC, false>(a, j, e0);
+}
+
+template <class T, int LOGR, int EC>
+__global__ void __launch_bounds__(FftPlan<T, LOGR, EC>::NT) fft_seg_kernel(const __grid_constant__ SegParams<FftArgs> P)
+{
+    fft_seg_run<T, LOGR, EC>(P);
+}
+
+template <class T, int LOGR, int EC>
+__global__ void __launch_bounds__(FftPlan<T, LOGR, EC>::NT,
+                                  MRC_FFT32_MINB > 0 ? (MRC_FFT32_MINB * 512) / FftPlan<T, LOGR, EC>::NT : 1)
+    fft_seg_kernel_mb(const __grid_constant__ SegParams<FftArgs> P)
+{
+    fft_seg_run<T, LOGR, EC>(P);
 }
 
 // ---------------------------------------------------------------------------
@@ -451,7 +485,7 @@ __device__ __forceinline__ cx<T> merge_real(cx<T> cf, cx<T> cg, cx<T> wconj)
 }
 
 template <class T, int BM, int BN, int BK, int TM, int TN>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN)) pairmul_kernel(PairArgs a)
+__device__ __forceinline__ void pairmul_body(const PairArgs &a, int64_t p, int tile)
 {
     constexpr int NTX = BN / TN, NTY = BM / TM, NT = NTX * NTY;
     __shared__ cx<T> Xf[BK][BM + 1], Xg[BK][BM + 1];
@@ -461,14 +495,13 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) pairmul_kernel(PairArgs
     cx<T> *ZC = reinterpret_cast<cx<T> *>(a.zc);
     const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
 
-    const int64_t p = blockIdx.x;
     const int64_t M = a.M;
     const int64_t f = p;
     const int64_t gL = M - p;        // partner frequency of the length-L spectrum
     const int64_t gZ = gL & (M - 1);  // its packed index
     const int ntile_c = (a.c + BN - 1) / BN;
-    const int i0 = (blockIdx.y / ntile_c) * BM;
-    const int j0 = (blockIdx.y % ntile_c) * BN;
+    const int i0 = (tile / ntile_c) * BM;
+    const int j0 = (tile % ntile_c) * BN;
     const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
     // W_L^f with L = 2M; W_L^{gL} = -conj(W_L^f)
     const cx<T> wf = tw[f << (a.tw_log - a.logM - 1)];
@@ -542,6 +575,22 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) pairmul_kernel(PairArgs
         }
 }
 
+template <class T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN)) pairmul_kernel(PairArgs a)
+{
+    pairmul_body<T, BM, BN, BK, TM, TN>(a, blockIdx.x, blockIdx.y);
+}
+
+// segmented: CTA (pair p, tile) of segment s at local index tile * npairs + p
+template <class T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN)) pairmul_seg_kernel(const __grid_constant__ SegParams<PairArgs> P)
+{
+    const int s = seg_find(P, blockIdx.x);
+    const PairArgs &a = P.a[s];
+    const unsigned loc = blockIdx.x - P.first[s], np = (unsigned)a.npairs;
+    pairmul_body<T, BM, BN, BK, TM, TN>(a, loc % np, (int)(loc / np));
+}
+
 // The same product with the two frequencies of the pair on two halves of
 // the CTA (2 x NTX x NTY threads): thread group fq in {0: f, 1: g} keeps only
 // its own TM x TN accumulators, which halves the registers per thread and
@@ -561,7 +610,7 @@ __device__ __forceinline__ int pm2_ycol(int jj)
 }
 
 template <class T, int BM, int BN, int BK, int TM, int TN>
-__global__ void __launch_bounds__(2 * (BM / TM) * (BN / TN), 2) pairmul2_kernel(PairArgs a)
+__device__ __forceinline__ void pairmul2_body(const PairArgs &a, int64_t p, int tile)
 {
     constexpr int NTX = BN / TN, NTY = BM / TM, NTF = NTX * NTY, NT = 2 * NTF;
     constexpr int XLD = BM + (sizeof(cx<T>) == 8 ? 2 : 1), YLD = BN + (sizeof(cx<T>) == 8 ? 2 : 1);
@@ -575,10 +624,10 @@ __global__ void __launch_bounds__(2 * (BM / TM) * (BN / TN), 2) pairmul2_kernel(
     cx<T> *ZC = reinterpret_cast<cx<T> *>(a.zc);
     const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
 
-    const int64_t p = blockIdx.x, M = a.M;
+    const int64_t M = a.M;
     const int64_t f = p, gL = M - p, gZ = gL & (M - 1);
     const int ntile_c = (a.c + BN - 1) / BN;
-    const int i0 = (blockIdx.y / ntile_c) * BM, j0 = (blockIdx.y % ntile_c) * BN;
+    const int i0 = (tile / ntile_c) * BM, j0 = (tile % ntile_c) * BN;
     const int fq = threadIdx.x / NTF, lt = threadIdx.x - fq * NTF;
     const int tx = lt % NTX, ty = lt / NTX;
     const cx<T> wf = tw[f << (a.tw_log - a.logM - 1)];
@@ -691,6 +740,22 @@ __global__ void __launch_bounds__(2 * (BM / TM) * (BN / TN), 2) pairmul2_kernel(
     }
 }
 
+template <class T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__(2 * (BM / TM) * (BN / TN), 2) pairmul2_kernel(PairArgs a)
+{
+    pairmul2_body<T, BM, BN, BK, TM, TN>(a, blockIdx.x, blockIdx.y);
+}
+
+template <class T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__(2 * (BM / TM) * (BN / TN), 2)
+    pairmul2_seg_kernel(const __grid_constant__ SegParams<PairArgs> P)
+{
+    const int s = seg_find(P, blockIdx.x);
+    const PairArgs &a = P.a[s];
+    const unsigned loc = blockIdx.x - P.first[s], np = (unsigned)a.npairs;
+    pairmul2_body<T, BM, BN, BK, TM, TN>(a, loc % np, (int)(loc / np));
+}
+
 // Frequency-pair product with a diagonal right factor:
 //   Ch(f)_{ij} = Xh(f)_{ij} * Yh(f)_j   (X: [E = r*c], Y: [c]),
 // the per-entry scalar convolutions P_ij = psi_ij * h_j of Eq. (transition-discrete).
@@ -740,6 +805,11 @@ struct FftEntry {
     FftKernel fn;
     int nt;
 };
+using FftSegKernel = void (*)(SegParams<FftArgs>);
+struct FftSegEntry {
+    FftSegKernel fn;
+    int nt;
+};
 
 template <class T, int L, int EC>
 constexpr FftKernel fft_pass_or_mb()
@@ -750,10 +820,21 @@ constexpr FftKernel fft_pass_or_mb()
     else return fft_pass_kernel<T, L, EC>;
 }
 
+template <class T, int L, int EC>
+constexpr FftSegKernel fft_seg_or_mb()
+{
+    if constexpr (MRC_FFT32_MINB > 0 && sizeof(cx<T>) == 8 && FftPlan<T, L, EC>::EPT <= 8 &&
+                  FftPlan<T, L, EC>::NT <= MRC_FFT32_MINB * 512)
+        return fft_seg_kernel_mb<T, L, EC>;
+    else return fft_seg_kernel<T, L, EC>;
+}
+
+// t: the single-transform passes; ts: the segmented ones (default entries per CTA)
 template <class T, int OFF, int... L>
-void fft_fill_shifted(FftEntry (*t)[11], std::integer_sequence<int, L...>)
+void fft_fill_shifted(FftEntry (*t)[11], FftSegEntry *ts, std::integer_sequence<int, L...>)
 {
     constexpr int ECD = fft_default_ec<T>();
     ((t[0][OFF + L] = FftEntry{fft_pass_or_mb<T, OFF + L, ECD>(), FftPlan<T, OFF + L, ECD>::NT}), ...);
     ((t[1][OFF + L] = FftEntry{fft_pass_kernel<T, OFF + L, 4>, FftPlan<T, OFF + L, 4>::NT}), ...);
+    ((ts[OFF + L] = FftSegEntry{fft_seg_or_mb<T, OFF + L, ECD>(), FftPlan<T, OFF + L, ECD>::NT}), ...);
 }

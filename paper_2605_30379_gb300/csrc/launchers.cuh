@@ -13,6 +13,8 @@
 // specialised once per precision by MRC_DEFINE_PREC.
 template <class T>
 const FftEntry (&fft_table())[2][11];
+template <class T>
+const FftSegEntry (&fft_seg_table())[11];
 
 namespace {
 
@@ -72,22 +74,27 @@ inline int fft_plan_apply(int logM, int plan, int *logRs, bool *ec4)
     return fft_plan(logM, logRs);
 }
 
+// The argument blocks of a transform's passes and the algorithmic charge of
+// each (the valid source rows read once, the kept output written once,
+// 5 M log2(R) real flops per entry, radix-2 convention).  seg: the default
+// entries per CTA whatever E (the segmented passes exist for it only).
 template <class T>
-cudaError_t fft_run(const FftSrc &src, const FftDst &dst, int64_t M, int E, int dir, void *scratch,
-                    const void *tw, int tw_log, cudaStream_t st, int plan)
+cudaError_t fft_build(const FftSrc &src, const FftDst &dst, int64_t M, int E, int dir, void *scratch, const void *tw,
+                      int tw_log, int plan, bool seg, FftPasses &ps)
 {
     const int logM = ilog2_i64(M);
     if (((int64_t)1 << logM) != M || logM > 20 || logM + 1 > tw_log) return cudaErrorInvalidValue;
-    int logRs[2];
     bool ec4 = false;
-    const int np = fft_plan_apply(logM, plan, logRs, &ec4);
-    const int ec = ec4 ? 4 : pick_ec<T>(E);
+    ps.np = fft_plan_apply(logM, seg ? -1 : plan, ps.logR, &ec4);
+    const int ec = seg ? default_ec<T>() : (ec4 ? 4 : pick_ec<T>(E));
+    ps.ec = ec;
     const int sld = E;  // scratch row length (complex elements)
     int logNs = 0;
-    for (int ps = 0; ps < np; ++ps) {
-        FftArgs a{};
+    for (int k = 0; k < ps.np; ++k) {
+        FftArgs &a = ps.a[k];
+        a = FftArgs{};
         a.M = M;
-        a.logR = logRs[ps];
+        a.logR = ps.logR[k];
         a.logNs = logNs;
         a.Ns = (int64_t)1 << logNs;
         a.E = E;
@@ -95,13 +102,13 @@ cudaError_t fft_run(const FftSrc &src, const FftDst &dst, int64_t M, int E, int 
         a.dir = dir;
         a.tw = tw;
         a.tw_log = tw_log;
-        if (ps == 0) {
+        if (k == 0) {
             a.src_mode = src.mode; a.src = src.ptr; a.src_row0 = src.row0; a.src_nvalid = src.nvalid;
             a.src_ld = src.ld; a.src_neg = src.neg;
         } else {
             a.src_mode = SRC_CPLX; a.src = scratch; a.src_row0 = 0; a.src_nvalid = M; a.src_ld = sld; a.src_neg = 0;
         }
-        if (ps == np - 1) {
+        if (k == ps.np - 1) {
             a.dst_mode = dst.mode; a.dst = dst.ptr; a.dst_ld = dst.ld; a.dst_lo = dst.lo; a.dst_hi = dst.hi;
             a.dst_row0 = dst.row0; a.dst_scale = dst.scale; a.dst_eye_d = dst.eye_d;
             a.dst2 = (std::is_same<T, dd>::value && dst.mode == DST_CPLX) ? dst.ptr2 : nullptr;
@@ -125,10 +132,8 @@ cudaError_t fft_run(const FftSrc &src, const FftDst &dst, int64_t M, int E, int 
         // together cover whole rows j + rho M / R (d = 64, N = 2^18: double-float
         // FFT 67.9 -> 66.6 ms against the other order, FP32 unchanged);
         // nrow = M / R <= 2^10 in every plan
-        const unsigned nrow = (unsigned)(M >> a.logR), nchunk = (unsigned)((E + ec - 1) / ec);
-        const dim3 grid(nchunk, nrow);
-        // algorithmic charge: the valid source rows read once, the kept output written once,
-        // 5 M log2(R) real flops per entry (radix-2 convention)
+        ps.nrow[k] = (unsigned)(M >> a.logR);
+        ps.nchunk = (unsigned)((E + ec - 1) / ec);
         double rd, wr;
         if (a.src_mode == SRC_REAL64) rd = (double)std::min<int64_t>(a.src_nvalid, 2 * M) * E * 8.0;
         else if (a.src_mode == SRC_REAL32) rd = (double)std::min<int64_t>(a.src_nvalid, 2 * M) * E * 4.0;
@@ -138,12 +143,40 @@ cudaError_t fft_run(const FftSrc &src, const FftDst &dst, int64_t M, int E, int 
         else if (a.dst_mode == DST_REAL32) wr = rows * 4.0;
         else if (a.dst_mode == DST_REAL64_BASE32) wr = rows * 12.0;
         else wr = rows * 8.0 * (a.dst_mode == DST_REAL64_ADD ? 2.0 : 1.0);
-        const FftEntry &k = fft_table<T>()[ec_index<T>(ec)][a.logR];
-        mrc_prof_pre(kclass_fft<T>(), st);
-        k.fn<<<grid, k.nt, fft_smem_bytes<T>(a.logR, ec), st>>>(a);
-        mrc_prof_post(kclass_fft<T>(), st, rd + wr, 5.0 * (double)M * a.logR * E);
+        ps.bytes[k] = rd + wr;
+        ps.flops[k] = 5.0 * (double)M * a.logR * E;
         logNs += a.logR;
     }
+    return cudaSuccess;
+}
+
+template <class T>
+cudaError_t fft_run(const FftSrc &src, const FftDst &dst, int64_t M, int E, int dir, void *scratch,
+                    const void *tw, int tw_log, cudaStream_t st, int plan)
+{
+    FftPasses ps;
+    cudaError_t e = fft_build<T>(src, dst, M, E, dir, scratch, tw, tw_log, plan, false, ps);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < ps.np; ++k) {
+        const FftEntry &kn = fft_table<T>()[ec_index<T>(ps.ec)][ps.logR[k]];
+        mrc_prof_pre(kclass_fft<T>(), st);
+        kn.fn<<<dim3(ps.nchunk, ps.nrow[k]), kn.nt, fft_smem_bytes<T>(ps.logR[k], ps.ec), st>>>(ps.a[k]);
+        mrc_prof_post(kclass_fft<T>(), st, ps.bytes[k], ps.flops[k]);
+    }
+    return cudaGetLastError();
+}
+
+// One segmented pass of radix 2^logR over nseg transforms (device tables of
+// their argument blocks and first CTAs; nctas CTAs in all)
+template <class T>
+cudaError_t fft_seg_run(int logR, const SegParams<FftArgs> &P, unsigned nctas, double bytes, double flops,
+                        cudaStream_t st)
+{
+    if (P.nseg <= 0 || nctas == 0) return cudaSuccess;
+    const FftSegEntry &kn = fft_seg_table<T>()[logR];
+    mrc_prof_pre(kclass_fft<T>(), st);
+    kn.fn<<<nctas, kn.nt, fft_smem_bytes<T>(logR, default_ec<T>()), st>>>(P);
+    mrc_prof_post(kclass_fft<T>(), st, bytes, flops);
     return cudaGetLastError();
 }
 
@@ -173,18 +206,35 @@ cudaError_t pairmul2_launch(const PairArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <class T>
-cudaError_t pairmul_run(const void *zx, const void *zy, void *zc, int64_t M, int r, int m, int c, int cfg, const void *tw,
-                        int tw_log, cudaStream_t st)
+// product argument block and tile configuration: 0 = 16x16 (64 threads),
+// 1 = 32x32 (256), 2 = 64x64 (256); cfg < 0 picks by the larger output dimension
+inline PairArgs pairmul_args(const void *zx, const void *zy, void *zc, int64_t M, int r, int m, int c, const void *tw,
+                             int tw_log)
 {
     PairArgs a{};
     a.zx = zx; a.zy = zy; a.zc = zc; a.tw = tw; a.tw_log = tw_log; a.M = M; a.logM = ilog2_i64(M);
     a.npairs = M >= 2 ? M / 2 + 1 : 1;
     a.r = r; a.m = m; a.c = c;
-    // tile configuration: 0 = 16x16 (64 threads), 1 = 32x32 (256), 2 = 64x64 (256);
-    // cfg < 0 picks by the larger output dimension
+    return a;
+}
+inline int pairmul_cfg_for(int r, int c, int cfg)
+{
     const int mx = r > c ? r : c;
-    if (cfg < 0) cfg = mx <= 16 ? 0 : (mx <= 32 ? 1 : 2);
+    return cfg >= 0 ? cfg : (mx <= 16 ? 0 : (mx <= 32 ? 1 : 2));
+}
+// CTAs of one product: pairs x output tiles
+inline unsigned pairmul_ctas(const PairArgs &a, int cfg)
+{
+    const int b = cfg == 0 ? 16 : (cfg == 1 ? 32 : 64);
+    return (unsigned)a.npairs * (unsigned)(((a.r + b - 1) / b) * ((a.c + b - 1) / b));
+}
+
+template <class T>
+cudaError_t pairmul_run(const void *zx, const void *zy, void *zc, int64_t M, int r, int m, int c, int cfg, const void *tw,
+                        int tw_log, cudaStream_t st)
+{
+    const PairArgs a = pairmul_args(zx, zy, zc, M, r, m, c, tw, tw_log);
+    cfg = pairmul_cfg_for(r, c, cfg);
     if (cfg == 0) return pairmul_launch<T, 16, 16, 16, 2, 2>(a, st);
     if (cfg == 1) return pairmul_launch<T, 32, 32, 16, 2, 2>(a, st);
     // FP32, 64 x 64 tiles: the frequencies of a pair on two halves of the CTA
@@ -192,6 +242,22 @@ cudaError_t pairmul_run(const void *zx, const void *zy, void *zc, int64_t M, int
     // 49.4 ms at d = 64, N = 2^18 against both frequencies in every thread)
     if constexpr (std::is_same<T, float>::value) return pairmul2_launch<T, 64, 64, 8, 4, 4>(a, st);
     else return pairmul_launch<T, 64, 64, 8, 4, 4>(a, st);
+}
+
+// One segmented product launch of tile configuration cfg (resolved) over
+// nseg products (device tables; nctas CTAs in all)
+template <class T>
+cudaError_t pairmul_seg_run(int cfg, const SegParams<PairArgs> &P, unsigned nctas, double bytes, double flops,
+                            cudaStream_t st)
+{
+    if (P.nseg <= 0 || nctas == 0) return cudaSuccess;
+    mrc_prof_pre(kclass_pair<T>(), st);
+    if (cfg == 0) pairmul_seg_kernel<T, 16, 16, 16, 2, 2><<<nctas, 64, 0, st>>>(P);
+    else if (cfg == 1) pairmul_seg_kernel<T, 32, 32, 16, 2, 2><<<nctas, 256, 0, st>>>(P);
+    else if constexpr (std::is_same<T, float>::value) pairmul2_seg_kernel<T, 64, 64, 8, 4, 4><<<nctas, 512, 0, st>>>(P);
+    else pairmul_seg_kernel<T, 64, 64, 8, 4, 4><<<nctas, 256, 0, st>>>(P);
+    mrc_prof_post(kclass_pair<T>(), st, bytes, flops);
+    return cudaGetLastError();
 }
 
 template <class T>
@@ -230,25 +296,51 @@ cudaError_t init_run()
             cudaError_t e = cudaFuncSetAttribute(t[i][l].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             if (e != cudaSuccess) return e;
         }
+    const auto &ts = fft_seg_table<T>();
+    for (int l = 0; l < 11; ++l) {
+        cudaError_t e = cudaFuncSetAttribute(ts[l].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+    }
     return cudaSuccess;
 }
 
 } // namespace
 
 #define MRC_DEFINE_PREC(T, SUF)                                                                             \
-    void mrc_fft_fill_##SUF##_lo(FftEntry (*t)[11]);                                                        \
-    void mrc_fft_fill_##SUF##_hi(FftEntry (*t)[11]);                                                        \
-    template <>                                                                                             \
-    const FftEntry (&fft_table<T>())[2][11]                                                                 \
-    {                                                                                                       \
-        static FftEntry t[2][11];                                                                           \
-        static bool init = false;                                                                           \
-        if (!init) {                                                                                        \
-            mrc_fft_fill_##SUF##_lo(t);                                                                     \
-            mrc_fft_fill_##SUF##_hi(t);                                                                     \
-            init = true;                                                                                    \
+    void mrc_fft_fill_##SUF##_lo(FftEntry (*t)[11], FftSegEntry *ts);                                       \
+    void mrc_fft_fill_##SUF##_hi(FftEntry (*t)[11], FftSegEntry *ts);                                       \
+    struct FftTables_##SUF {                                                                                \
+        FftEntry t[2][11];                                                                                  \
+        FftSegEntry ts[11];                                                                                 \
+        FftTables_##SUF()                                                                                   \
+        {                                                                                                   \
+            mrc_fft_fill_##SUF##_lo(t, ts);                                                                 \
+            mrc_fft_fill_##SUF##_hi(t, ts);                                                                 \
         }                                                                                                   \
-        return t;                                                                                           \
+    };                                                                                                      \
+    static const FftTables_##SUF &fft_tables_##SUF()                                                        \
+    {                                                                                                       \
+        static const FftTables_##SUF tb;                                                                    \
+        return tb;                                                                                          \
+    }                                                                                                       \
+    template <>                                                                                             \
+    const FftEntry (&fft_table<T>())[2][11] { return fft_tables_##SUF().t; }                                \
+    template <>                                                                                             \
+    const FftSegEntry (&fft_seg_table<T>())[11] { return fft_tables_##SUF().ts; }                           \
+    cudaError_t mrc_fft_build_##SUF(const FftSrc &src, const FftDst &dst, int64_t M, int E, int dir,          \
+                                    void *scratch, const void *tw, int tw_log, FftPasses &ps)               \
+    {                                                                                                       \
+        return fft_build<T>(src, dst, M, E, dir, scratch, tw, tw_log, -1, true, ps);                        \
+    }                                                                                                       \
+    cudaError_t mrc_fft_seg_##SUF(int logR, const SegParams<FftArgs> &P, unsigned nctas, double bytes,       \
+                                  double flops, cudaStream_t st)                                            \
+    {                                                                                                       \
+        return fft_seg_run<T>(logR, P, nctas, bytes, flops, st);                                            \
+    }                                                                                                       \
+    cudaError_t mrc_pairmul_seg_##SUF(int cfg, const SegParams<PairArgs> &P, unsigned nctas, double bytes,   \
+                                      double flops, cudaStream_t st)                                        \
+    {                                                                                                       \
+        return pairmul_seg_run<T>(cfg, P, nctas, bytes, flops, st);                                         \
     }                                                                                                       \
     cudaError_t mrc_fft_##SUF(const FftSrc &src, const FftDst &dst, int64_t M, int E, int dir, void *scratch, \
                               const void *tw, int tw_log, cudaStream_t st, int plan)                        \

@@ -41,8 +41,8 @@ __device__ void block_argmax(double &v, int &i, double *sv, int *si)
 // Gauss-Jordan with partial pivoting on [A0 | I] (d x 2d, row-major in W).
 // One CTA.  A pivot with |p| <= d 2^-52 max|A0| marks A0 singular: the
 // status word is set, `out` is filled with NaN and the kernel returns.
-__global__ void __launch_bounds__(1024) gj_kernel(const double *__restrict__ A0, double *__restrict__ out,
-                                                  double *__restrict__ W, int d, int *status)
+__device__ __forceinline__ void gj_run(const double *__restrict__ A0, double *__restrict__ out,
+                                       double *__restrict__ W, int d, int *status)
 {
     __shared__ double sv[32];
     __shared__ int si[32];
@@ -96,14 +96,27 @@ __global__ void __launch_bounds__(1024) gj_kernel(const double *__restrict__ A0,
     }
 }
 
+__global__ void __launch_bounds__(1024) gj_kernel(const double *__restrict__ A0, double *__restrict__ out,
+                                                  double *__restrict__ W, int d, int *status)
+{
+    gj_run(A0, out, W, d, status);
+}
+
+// one CTA per model of a batch
+__global__ void __launch_bounds__(1024) gj_batch_kernel(const __grid_constant__ SegParams<GjArgs> P)
+{
+    const GjArgs &g = P.a[blockIdx.x];
+    gj_run(g.A0, g.out, g.W, g.d, g.status);
+}
+
 // Direct recursion for the first m0 coefficients (left form, Theorem 2.2):
 //   psi(k) = A(0)^{-1} [ - sum_{l=1..k} A(l) psi(k-l) ],  k = 1..m0-1,
 // with psi(0) = A(0)^{-1} already in place.  CTA j owns column j (columns
 // are independent in the left recursion), thread i owns row i.
-__global__ void base_case_kernel(const double *__restrict__ A, double *__restrict__ psi, int d, int m0)
+__device__ __forceinline__ void base_case_run(const double *__restrict__ A, double *__restrict__ psi, int d, int m0,
+                                              int j)
 {
     extern __shared__ double t[];  // [d]
-    const int j = blockIdx.x;
     const int64_t E = (int64_t)d * d;
     for (int k = 1; k < m0; ++k) {
         for (int i = threadIdx.x; i < d; i += blockDim.x) {
@@ -123,6 +136,19 @@ __global__ void base_case_kernel(const double *__restrict__ A, double *__restric
         }
         __syncthreads();
     }
+}
+
+__global__ void base_case_kernel(const double *__restrict__ A, double *__restrict__ psi, int d, int m0)
+{
+    base_case_run(A, psi, d, m0, blockIdx.x);
+}
+
+// column blockIdx.x of model blockIdx.y of a batch
+__global__ void base_case_batch_kernel(const __grid_constant__ SegParams<BaseArgs> P)
+{
+    const BaseArgs &g = P.a[blockIdx.y];
+    if ((int)blockIdx.x >= g.d || g.m0 <= 1) return;
+    base_case_run(g.A, g.psi, g.d, g.m0, blockIdx.x);
 }
 
 // rs[k][i] = sum_j q[k][i][j] for k >= 1, rs[0][i] = 0.
@@ -518,6 +544,46 @@ __global__ void f64_to_f32_kernel(const double *__restrict__ x, float *__restric
         for (int u = 0; u < 4; ++u) y[i + u * stride] = f64_to_f32_rn(v[u]);
     }
     for (; i < n; i += stride) y[i] = f64_to_f32_rn(x[i]);
+}
+
+// conversion of segment s's elements [loc C, (loc + 1) C) by CTA loc of the segment
+__global__ void f64_to_f32_batch_kernel(const __grid_constant__ SegParams<CvtArgs> P)
+{
+    const int s = seg_find(P, blockIdx.x);
+    const CvtArgs &g = P.a[s];
+    const int64_t e0 = (int64_t)(blockIdx.x - P.first[s]) * MRC_CVT_CHUNK;
+    const int64_t e1 = min(g.n, e0 + MRC_CVT_CHUNK);
+    for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) g.y[i] = f64_to_f32_rn(g.x[i]);
+}
+
+cudaError_t mrc_gauss_jordan_batch(const SegParams<GjArgs> &P, int dmax, cudaStream_t st)
+{
+    if (P.nseg <= 0) return cudaSuccess;
+    mrc_prof_pre(7, st);
+    gj_batch_kernel<<<P.nseg, 1024, sizeof(double) * dmax, st>>>(P);
+    mrc_prof_post(7, st, 0, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t mrc_base_case_batch(const SegParams<BaseArgs> &P, int dmax, cudaStream_t st)
+{
+    if (P.nseg <= 0) return cudaSuccess;
+    const int bs = dmax < 32 ? 32 : (dmax > 512 ? 512 : ((dmax + 31) / 32) * 32);
+    mrc_prof_pre(7, st);
+    base_case_batch_kernel<<<dim3(dmax, P.nseg), bs, sizeof(double) * dmax, st>>>(P);
+    mrc_prof_post(7, st, 0, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t mrc_f64_to_f32_batch(const SegParams<CvtArgs> &P, unsigned nctas, cudaStream_t st)
+{
+    if (P.nseg <= 0 || nctas == 0) return cudaSuccess;
+    double n = 0;
+    for (int s = 0; s < P.nseg; ++s) n += (double)P.a[s].n;
+    mrc_prof_pre(7, st);
+    f64_to_f32_batch_kernel<<<nctas, 256, 0, st>>>(P);
+    mrc_prof_post(7, st, n * 12.0, 0);
+    return cudaGetLastError();
 }
 
 cudaError_t mrc_f64_to_f32(const double *x, float *y, int64_t n, cudaStream_t st)

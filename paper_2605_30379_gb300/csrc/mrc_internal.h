@@ -73,11 +73,50 @@ struct FftDst {
     const void *base = nullptr;  // DST_REAL64_BASE32: binary32 rows (FftArgs::dst_base)
 };
 
-// Segments per segmented launch: the argument blocks of a launch live in its
-// parameter space (at most 32764 bytes: MRC_SEG_MAX x (sizeof(FftArgs) + 4))
+// Segmented launches: one launch over several independent pieces of work of
+// one shape class (the models of a batch at one stage).  The pieces'
+// argument blocks travel in the kernel's parameter space as one
+// __grid_constant__ block (at most 32764 bytes: MRC_SEG_MAX x
+// (sizeof(FftArgs) + 4)), read through the constant cache like a single
+// launch's arguments.  CTA b belongs to segment s = max{s : first[s] <= b}.
 #define MRC_SEG_MAX 144
 template <class A>
-struct SegParams;
+struct SegParams {
+    int nseg;
+    unsigned first[MRC_SEG_MAX];
+    A a[MRC_SEG_MAX];
+};
+
+template <class A>
+__device__ __forceinline__ int seg_find(const SegParams<A> &P, unsigned b)
+{
+    int lo = 0, hi = P.nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.first[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// argument blocks of the batched Gauss-Jordan, base-case and conversion kernels
+struct GjArgs {
+    const double *A0;
+    double *out, *W;
+    int d;
+    int *status;
+};
+struct BaseArgs {
+    const double *A;
+    double *psi;
+    int d, m0;
+};
+struct CvtArgs {
+    const double *x;
+    float *y;
+    int64_t n;
+};
+#define MRC_CVT_CHUNK 8192  // elements per CTA of the segmented conversion
 
 // The passes of one transform (at most two): argument blocks, radices, the
 // algorithmic charge of each, and the launch shape (nchunk entry chunks of ec
@@ -147,6 +186,10 @@ cudaError_t mrc_pairmul_dd_tcp(const void *zx, const void *zy, void *zc, int64_t
                                int *status, cudaStream_t st);
 cudaError_t mrc_pairmul_f32_tcp(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
                                 int *status, cudaStream_t st);
+// the same over the products of one segmented launch (all of the same M and
+// of the same ceil(d / 16)); a timeout is reported in *status
+cudaError_t mrc_tcp_seg(int dd_prec, const SegParams<PairArgs> &P, int *status, cudaStream_t st);
+PairArgs mrc_tcp_args(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log);
 // the kernels' bounded mbarrier wait on a barrier nothing arrives on: writes 6 to *status
 cudaError_t mrc_tc_wait_selftest(int *status, int spins, cudaStream_t st);
 
@@ -206,6 +249,12 @@ cudaError_t mrc_occupation_k(const double *P, int d, int64_t N, const double *al
                              cudaStream_t st);
 cudaError_t mrc_one_minus(const double *x, double *y, int64_t n, cudaStream_t st);
 cudaError_t mrc_f64_to_f32(const double *x, float *y, int64_t n, cudaStream_t st);
+// batched: Gauss-Jordan of every segment's A(0) (one CTA each, dmax the
+// largest d), the direct recursion (dmax x nseg CTAs), and conversions
+// (P.first: CTA starts in MRC_CVT_CHUNK elements; nctas in all)
+cudaError_t mrc_gauss_jordan_batch(const SegParams<GjArgs> &P, int dmax, cudaStream_t st);
+cudaError_t mrc_base_case_batch(const SegParams<BaseArgs> &P, int dmax, cudaStream_t st);
+cudaError_t mrc_f64_to_f32_batch(const SegParams<CvtArgs> &P, unsigned nctas, cudaStream_t st);
 // series Gauss-Jordan on W = [P_A | I] ([N][d][2d]): build W (clearing the
 // call's singular flag), choose the pivot of column col and exchange rows
 // (with the pivot series u [N] and the elimination factors cv [N][d]), take

@@ -559,8 +559,14 @@ __device__ __forceinline__ void st_cx<float>(cx<float> *p, cx<float> v)
     *reinterpret_cast<float2 *>(p) = make_float2(v.re, v.im);
 }
 
-template <class T>
-__global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *status)
+// P: the products of one launch, all of M points (a single one, or every
+// model of a batch at one stage); global pair gp is pair gp % npairs of
+// product gp / npairs.  NCK: the K chunks of KC per frequency, ceil(d / KC)
+// for every product of the launch (the chunks that hold k < d; d = 48 runs 3
+// of 4).  With the chunk count a run-time value the double-float product took
+// 46.9 ms at d = 64, N = 2^18 against 41.4.
+template <class T, int NCK>
+__global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(const __grid_constant__ SegParams<PairArgs> P, int *status)
 {
     using L = TcL<T>;
     constexpr int S = L::S, GMIN = L::GMIN, NG = L::NG, NSLOT = L::NSLOT, NF = L::NF;
@@ -590,17 +596,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
     fence_after();
     const unsigned tmem = tslot;
 
-    const cx<T> *ZX = reinterpret_cast<const cx<T> *>(a.zx);
-    const cx<T> *ZY = reinterpret_cast<const cx<T> *>(a.zy);
-    cx<T> *ZC = reinterpret_cast<cx<T> *>(a.zc);
+    const PairArgs &a = P.a[0];  // M, twiddles: common to the launch
     const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
-    const int d = a.r;
-    const int64_t E = (int64_t)d * d, M = a.M;
-    // K chunks of KC per frequency: FP32 takes the ones that hold k < d (the
-    // others' digit tiles are zero: d = 48 runs 3 of 4); double-float keeps
-    // all four (with its chunk count left to run time the product went from
-    // 41.4 to 46.9 ms at d = 64, N = 2^18)
-    const int nck = __is_same(T, dd) ? NCH : (d + KC - 1) / KC;
+    const int64_t M = a.M;
+    // pair indices in 32 bits (a launch holds fewer than 2^32 pairs)
+    const unsigned npairs = (unsigned)a.npairs, total = npairs * (unsigned)P.nseg;
+    // product sg's spectra, output and d, read from the parameter block at
+    // each use (no registers held across the chunk loop)
+    auto zx_of = [&](int sg) { return reinterpret_cast<const cx<T> *>(P.a[sg].zx); };
+    auto zy_of = [&](int sg) { return reinterpret_cast<const cx<T> *>(P.a[sg].zy); };
+    auto zc_of = [&](int sg) { return reinterpret_cast<cx<T> *>(P.a[sg].zc); };
+    auto d_of = [&](int sg) { return P.a[sg].r; };
+    constexpr int nck = NCK;
     bool failed = false;
     auto give_up = [&]() {
         failed = true;
@@ -625,46 +632,52 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
         // over its 16-byte aligned interior (a bulk copy must start on a
         // 16-byte boundary and span a multiple of 16 bytes; FP32 rows of odd
         // E start and end on 8-byte ones), so it never leaves the row
-        auto prefetch_pair = [&](int64_t q) {
-            if (t < 4 && q < a.npairs) {
+        auto prefetch_pair = [&](unsigned gq) {
+            if (t < 4 && gq < total) {
+                const int sq = (int)(gq / npairs);
+                const int64_t q = gq - (unsigned)sq * npairs, E = (int64_t)d_of(sq) * d_of(sq);
                 const int64_t r = (t & 1) ? ((M - q) & (M - 1)) : q;
-                const uintptr_t b0 = (uintptr_t)((t < 2 ? ZX : ZY) + r * E);
+                const uintptr_t b0 = (uintptr_t)((t < 2 ? zx_of(sq) : zy_of(sq)) + r * E);
                 const uintptr_t lo = (b0 + 15) & ~(uintptr_t)15, hi = (b0 + E * sizeof(cx<T>)) & ~(uintptr_t)15;
                 if (hi > lo) prefetch_l2((const void *)lo, (unsigned)(hi - lo));
             }
         };
-        for (int k = 1; k < L::PF; ++k) prefetch_pair((int64_t)blockIdx.x + (int64_t)k * gridDim.x);
+        for (int k = 1; k < L::PF; ++k) prefetch_pair(blockIdx.x + (unsigned)k * gridDim.x);
         bxy[t] = 0u;  // both bound buffers (256 threads, 256 words)
         bar_sync(BAR_SPLIT, NSPLIT);
-        if (blockIdx.x < a.npairs) {
-            const int64_t f = blockIdx.x, gZ = (M - f) & (M - 1);
+        if (blockIdx.x < total) {
+            const int s0 = (int)(blockIdx.x / npairs);
+            const int64_t f = blockIdx.x - (unsigned)s0 * npairs, gZ = (M - f) & (M - 1);
             float my = 0.0f;
             for (int n0 = 0; n0 < 4 * nck; n0 += 2) {
-                bnd_issue(bi, ZX, ZY, f, gZ, d, t, n0);
+                bnd_issue(bi, zx_of(s0), zy_of(s0), f, gZ, d_of(s0), t, n0);
                 bnd_reduce(bi, bxy, my, t, n0);
             }
             atomicMax(&bxy[64 + (t & 63)], __float_as_uint(my));
         }
         bar_sync(BAR_SPLIT, NSPLIT);
-        if (t < 64) bnd_scales(bxy, bxy + 64, scb, d, t);
+        if (t < 64 && blockIdx.x < total) bnd_scales(bxy, bxy + 64, scb, d_of((int)(blockIdx.x / npairs)), t);
         bar_sync(BAR_SPLIT, NSPLIT);
-        for (int64_t p = blockIdx.x; p < a.npairs; p += gridDim.x, ++pl) {
-            const int64_t f = p, gZ = (M - p) & (M - 1);
+        for (unsigned gp = blockIdx.x; gp < total; gp += gridDim.x, ++pl) {
+            const int sg = (int)(gp / npairs);
+            const int64_t p = gp - (unsigned)sg * npairs, f = p, gZ = (M - p) & (M - 1);
             const cx<T> wf = tw[f << (a.tw_log - a.logM - 1)];
             const cx<T> wg = c_neg(c_conj(wf));
             const float *sc = scb + 4 * 64 * (pl % L::NB);
-            const int64_t pn = p + gridDim.x, fn = pn, gn = (M - pn) & (M - 1);
-            const bool next = pn < a.npairs;
+            const unsigned gpn = gp + gridDim.x;
+            const bool next = gpn < total;
+            const int sn = next ? (int)(gpn / npairs) : sg;
+            const int64_t pn = gpn - (unsigned)sn * npairs, fn = pn, gn = (M - pn) & (M - 1);
             unsigned *bn = bxy + 128 * ((pl + 1) & 1);  // the next pair's bounds
             float myn = 0.0f;
             const int nch = npass(p) * nck;
             const int cb = L::PF == 1 ? nch / 2 : 0;  // first chunk that gathers the next pair's bounds
-            if (L::PF > 0) prefetch_pair(p + (int64_t)L::PF * gridDim.x);
+            if (L::PF > 0) prefetch_pair(gp + (unsigned)L::PF * gridDim.x);
             // bound rows n per gathering chunk (2, 4 or 8): the 4 nck row steps that cover
             // k < d over the nch - cb gathering chunks (nck per pass, half of them with PF = 1)
             const int ns = (L::PF == 1 ? 8 : 4) >> (npass(p) - 1);
-            load_x(raw, ZX, f, gZ, d, 0, t);
-            load_y(raw, ZY, f, gZ, d, 0, t);
+            load_x(raw, zx_of(sg), f, gZ, d_of(sg), 0, t);
+            load_y(raw, zy_of(sg), f, gZ, d_of(sg), 0, t);
             for (int c = 0; c < nch; ++c, ++it) {
                 const cx<T> w = c < nck ? wf : wg;
                 const int slot = it % NSLOT, use = it / NSLOT;
@@ -679,20 +692,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
                 const bool first = cn < nck;
                 const int64_t na = first ? f : gZ, nb = first ? gZ : f;
                 const int kn = (first ? cn : cn - nck) * KC;
-                if (gather) bnd_issue(bi, ZX, ZY, fn, gn, d, t, n0);
+                if (gather) bnd_issue(bi, zx_of(sn), zy_of(sn), fn, gn, d_of(sn), t, n0);
                 if (!failed) split_chunk_x<T>(raw, sp, sc, w, t);
-                if (cn < nch) load_x(raw, ZX, na, nb, d, kn, t);
+                if (cn < nch) load_x(raw, zx_of(sg), na, nb, d_of(sg), kn, t);
                 asm volatile("" ::: "memory");  // the loads above stay ahead of the Y digit stores
                 if (gather) {
                     bnd_reduce(bi, bn, myn, t, n0);
                     for (int u = 2; u < ns - 2; u += 2) {
-                        bnd_issue(bi, ZX, ZY, fn, gn, d, t, n0 + u);
+                        bnd_issue(bi, zx_of(sn), zy_of(sn), fn, gn, d_of(sn), t, n0 + u);
                         bnd_reduce(bi, bn, myn, t, n0 + u);
                     }
-                    if (ns > 2) bnd_issue(bi, ZX, ZY, fn, gn, d, t, n0 + ns - 2);
+                    if (ns > 2) bnd_issue(bi, zx_of(sn), zy_of(sn), fn, gn, d_of(sn), t, n0 + ns - 2);
                 }
                 if (!failed) split_chunk_y<T>(raw, sp, sc + 64, w, t);
-                if (cn < nch) load_y(raw, ZY, na, nb, d, kn, t);
+                if (cn < nch) load_y(raw, zy_of(sg), na, nb, d_of(sg), kn, t);
                 asm volatile("" ::: "memory");
                 if (gather && ns > 2) bnd_reduce(bi, bn, myn, t, n0 + ns - 2);
                 if (!failed) {
@@ -702,7 +715,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
             }
             if (next) atomicMax(&bn[64 + (t & 63)], __float_as_uint(myn));
             if (bar_or(BAR_SPLIT, NSPLIT, failed || abort_flag)) break;  // the next pair's bounds complete
-            if (next && t < 64) bnd_scales(bn, bn + 64, scb + 4 * 64 * ((pl + 1) % L::NB), d, t);
+            if (next && t < 64) bnd_scales(bn, bn + 64, scb + 4 * 64 * ((pl + 1) % L::NB), d_of(sn), t);
             if (t < 128) bxy[128 * (pl & 1) + t] = 0u;  // this pair's buffer: free for pair p + 2 grid
             bar_sync(BAR_SPLIT, NSPLIT);
         }
@@ -711,8 +724,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
         const int et = tid - WEPI0 * 32;
         const int q = warp & 3;  // TMEM lanes 32 q .. 32 q + 31
         int fi = 0, pl = 0;      // passes drained, pairs
-        for (int64_t p = blockIdx.x; p < a.npairs; p += gridDim.x, ++pl) {
-            const int64_t f = p, gZ = (M - p) & (M - 1);
+        for (unsigned gp = blockIdx.x; gp < total; gp += gridDim.x, ++pl) {
+            const int sg = (int)(gp / npairs);
+            const int64_t p = gp - (unsigned)sg * npairs, f = p, gZ = (M - p) & (M - 1);
+            cx<T> *ZC = zc_of(sg);
+            const int d = d_of(sg);
+            const int64_t E = (int64_t)d * d;
             const int np = npass(p);
             const bool self = (M - p) == p;  // p = M/2 pairs with itself
             const bool two = (gZ != f);
@@ -793,8 +810,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(PairArgs a, int *statu
         // -------------------------------------------------------------- MMA
         int it = 0, fi = 0;
         bool issued = false;
-        for (int64_t p = blockIdx.x; p < a.npairs && !failed; p += gridDim.x) {
-            const int np = npass(p);
+        for (unsigned gp = blockIdx.x; gp < total && !failed; gp += gridDim.x) {
+            const int np = npass(gp % npairs);
             for (int phase = 0; phase < np && !failed; ++phase, ++fi) {
                 if (fi > 0 && (abort_flag || !mbar_wait(smem_u32(&bar_tempty), (fi - 1) & 1))) {
                     give_up();
@@ -862,8 +879,32 @@ int sm_count()
 }
 
 template <class T>
-cudaError_t tcp_run(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
-                    int *status, cudaStream_t st, int kclass)
+using TcpKernel = void (*)(SegParams<PairArgs>, int *);
+template <class T>
+TcpKernel<T> tcp_kernel_for(int nck)
+{
+    return nck <= 2 ? tcp_kernel<T, 2> : (nck == 3 ? tcp_kernel<T, 3> : tcp_kernel<T, 4>);
+}
+
+template <class T>
+cudaError_t tcp_launch(const SegParams<PairArgs> &P, int *status, cudaStream_t st, int kclass)
+{
+    if (P.nseg <= 0) return cudaSuccess;
+    const int64_t total = P.a[0].npairs * P.nseg;
+    const unsigned grid = (unsigned)std::min<int64_t>(total, sm_count());
+    double bytes = 0, flops = 0;
+    for (int s = 0; s < P.nseg; ++s) {
+        const double d = P.a[s].r, M = (double)P.a[s].M;
+        bytes += M * 3.0 * d * d * sizeof(cx<T>);
+        flops += 8.0 * d * d * d * (M + 1);
+    }
+    mrc_prof_pre(kclass, st);
+    tcp_kernel_for<T>((P.a[0].r + KC - 1) / KC)<<<grid, NTHREADS, TcL<T>::SMEM, st>>>(P, status);
+    mrc_prof_post(kclass, st, bytes, flops);
+    return cudaGetLastError();
+}
+
+PairArgs tcp_args(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log)
 {
     PairArgs a{};
     a.zx = zx; a.zy = zy; a.zc = zc; a.tw = tw; a.tw_log = tw_log; a.M = M;
@@ -872,13 +913,18 @@ cudaError_t tcp_run(const void *zx, const void *zy, void *zc, int64_t M, int d, 
     a.logM = l;
     a.npairs = M >= 2 ? M / 2 + 1 : 1;
     a.r = a.m = a.c = d;
-    const unsigned grid = (unsigned)std::min<int64_t>(a.npairs, sm_count());
-    const double bytes = (double)M * 3.0 * d * d * sizeof(cx<T>);
-    const double flops = 8.0 * d * d * d * (double)(M + 1);
-    mrc_prof_pre(kclass, st);
-    tcp_kernel<T><<<grid, NTHREADS, TcL<T>::SMEM, st>>>(a, status);
-    mrc_prof_post(kclass, st, bytes, flops);
-    return cudaGetLastError();
+    return a;
+}
+
+template <class T>
+cudaError_t tcp_run(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
+                    int *status, cudaStream_t st, int kclass)
+{
+    SegParams<PairArgs> P;  // the launch's parameter block (one product)
+    P.nseg = 1;
+    P.first[0] = 0;
+    P.a[0] = tcp_args(zx, zy, zc, M, d, tw, tw_log);
+    return tcp_launch<T>(P, status, st, kclass);
 }
 
 } // namespace
@@ -887,10 +933,15 @@ bool mrc_tcp_supported(int r, int m, int c) { return r == m && m == c && r >= 32
 
 cudaError_t mrc_tcp_init(void)
 {
-    cudaError_t e = cudaFuncSetAttribute(tcp_kernel<dd>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcL<dd>::SMEM);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tcp_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcL<float>::SMEM);
-    return e;
+    for (int k = 2; k <= 4; ++k) {
+        cudaError_t e = cudaFuncSetAttribute(tcp_kernel_for<dd>(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             TcL<dd>::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(tcp_kernel_for<float>(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     TcL<float>::SMEM);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t mrc_pairmul_dd_tcp(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
@@ -903,4 +954,14 @@ cudaError_t mrc_pairmul_f32_tcp(const void *zx, const void *zy, void *zc, int64_
                                 int *status, cudaStream_t st)
 {
     return tcp_run<float>(zx, zy, zc, M, d, tw, tw_log, status, st, 5);
+}
+
+cudaError_t mrc_tcp_seg(int dd_prec, const SegParams<PairArgs> &P, int *status, cudaStream_t st)
+{
+    return dd_prec ? tcp_launch<dd>(P, status, st, 6) : tcp_launch<float>(P, status, st, 5);
+}
+
+PairArgs mrc_tcp_args(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log)
+{
+    return tcp_args(zx, zy, zc, M, d, tw, tw_log);
 }

@@ -29,6 +29,7 @@ constexpr size_t kPool = 16384;
 } // namespace
 
 void mrc_prof_set_capturing(bool on) { g_prof.capturing = on; }
+bool mrc_prof_timing() { return g_prof.kclass != 0; }
 
 namespace {
 cudaStream_t g_untimed = nullptr;

@@ -82,7 +82,7 @@ def load():
         lib.mrc_reward.argtypes = [P, I, I, I64, P, P, P, I, P]
         lib.mrc_renewal_visits.argtypes = [P, I, I64, P, P, P, I, P, P]
         lib.mrc_selftest_timeout.argtypes = [P, I, P]
-        for name in ("mrc_create", "mrc_destroy", "mrc_sync_status", "mrc_inverse", "mrc_inverse_batched",
+        for name in ("mrc_create", "mrc_destroy", "mrc_sync_status", "mrc_inverse", "mrc_inverse_gj", "mrc_inverse_batched",
                      "mrc_residual", "mrc_transition", "mrc_first_entrance", "mrc_occupation", "mrc_reward",
                      "mrc_renewal_visits", "mrc_selftest_timeout"):
             getattr(lib, name).restype = I
@@ -105,6 +105,25 @@ def context(device=None):
             _check(lib.mrc_create(ctypes.byref(h), dev, 0), "mrc_create")
             _ctx[dev] = h
         return _ctx[dev]
+
+
+def create_context(device=None, max_workspace_bytes=0):
+    """A context of its own (mrc_create) with a workspace cap; free it with
+    destroy_context."""
+    lib = load()
+    dev = torch.cuda.current_device() if device is None else int(device)
+    h = ctypes.c_void_p()
+    _check(lib.mrc_create(ctypes.byref(h), dev, int(max_workspace_bytes)), "mrc_create")
+    return h
+
+
+def destroy_context(h):
+    _check(load().mrc_destroy(h), "mrc_destroy")
+
+
+def workspace_bytes(d, N, prec="fp64"):
+    """mrc_inverse_workspace_bytes."""
+    return int(load().mrc_inverse_workspace_bytes(int(d), int(N), _PREC[prec]))
 
 
 def release():
@@ -210,8 +229,9 @@ def mre_solve(Q, L, scheme="mean_value", prec="fp64", sweeps=1, stream=None):
     return K
 
 
-def inverse_batched(As, prec="fp64", sweeps=1, outs=None, report=False, stream=None, autotune=False):
-    """mrc_inverse over a list of independent models (one stream, in order)."""
+def inverse_batched(As, prec="fp64", sweeps=1, outs=None, report=False, stream=None, autotune=False, ctx=None):
+    """mrc_inverse_batched over a list of independent models (ctx: a context
+    from create_context, else the device's default one)."""
     As = [_seq(a, "A") for a in As]
     outs = [torch.empty_like(a) for a in As] if outs is None else outs
     n = len(As)
@@ -221,8 +241,8 @@ def inverse_batched(As, prec="fp64", sweeps=1, outs=None, report=False, stream=N
     Pp = (ctypes.c_void_p * n)(*[p.data_ptr() for p in outs])
     reps = (_Report * n)() if report else None
     dev = As[0].device.index if n else None
-    st = load().mrc_inverse_batched(context(dev), n, dv, Nv, Ap, Pp, ctypes.byref(_opts(prec, sweeps, 0.0, autotune)),
-                                    _stream(stream), reps)
+    st = load().mrc_inverse_batched(context(dev) if ctx is None else ctx, n, dv, Nv, Ap, Pp,
+                                    ctypes.byref(_opts(prec, sweeps, 0.0, autotune)), _stream(stream), reps)
     _check(st, "mrc_inverse_batched")
     return (outs, [r.as_dict() for r in reps]) if report else outs
 

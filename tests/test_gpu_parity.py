@@ -215,7 +215,8 @@ def test_bounded_wait_times_out_and_context_stays_usable(mrc):
 
 # ------------------------------------------------------------ inverse mixed
 @pytest.mark.parametrize("d,N,seed", [(4, 1024, 0), (3, 777, 1), (16, 2048, 2), (33, 300, 3),
-                                      (20, 1500, 4), (48, 2000, 5), (64, 1300, 6)])
+                                      (20, 1500, 4), (48, 2000, 5), (64, 1300, 6),
+                                      (2, 1, 7), (40, 1, 8), (40, 2, 9), (5, 3, 10)])
 def test_inverse_mixed_matches_oracle(mrc, d, N, seed):
     q, _ = synth.weibull_model(d, N, seed=seed)
     A = synth.identity_minus(q)
@@ -351,6 +352,38 @@ def test_batched_mixed_and_graph_replay(mrc):
     torch.cuda.synchronize()
     for a, b in zip(first, outs2):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batched_waves_and_segment_groups(mrc, prec):
+    """170 models (more than one segmented launch holds: 144) with d from 1 to
+    40 and ragged N, on a context whose workspace cap splits them into several
+    waves: every model against the oracle."""
+    rng = np.random.default_rng(17)
+    models = []
+    for b in range(170):
+        d = int(rng.integers(1, 41)) if b % 10 == 0 else int(rng.integers(1, 9))
+        N = int(rng.integers(1, 300))
+        q, _ = synth.weibull_model(d, N, seed=100 + b) if d > 1 else (None, None)
+        if d == 1:
+            q = np.zeros((N, 1, 1))
+            q[1:, 0, 0] = rng.uniform(0, 1, N - 1) / max(1, N)
+        models.append(synth.identity_minus(q))
+    cap = 4 * max(mrc.workspace_bytes(a.shape[1], a.shape[0], prec) for a in models)
+    ctx = mrc.create_context(max_workspace_bytes=cap + (1 << 20))
+    try:
+        As = [dev(a) for a in models]
+        outs = mrc.inverse_batched(As, prec=prec, ctx=ctx)
+        torch.cuda.synchronize()
+        for a, o in zip(models, outs):
+            ref = oracle.inverse_left(a)
+            got = o.cpu().numpy()
+            if prec == "fp64":
+                assert np.abs(got - ref).max() <= TOL64
+            else:
+                assert e_rel(got, ref) <= TOL_REL
+    finally:
+        mrc.destroy_context(ctx)
 
 
 def test_batched_reports_singular_model(mrc):
