@@ -177,6 +177,10 @@ size_t ws_product(int64_t Mr, size_t EX, size_t EY, size_t EC, int prec)
 // FP32 Newton buffers or, afterwards, rho_L (binary32) followed by the
 // residual's two other double-float spectra or the FP32 correction's
 // product buffers].
+// The mixed inverse's residual product with X prepared once (the
+// tensor-core double-float product, square 32 <= d <= 64)
+bool xpre_used(int d) { return mrc_tcp_supported(d, d, d); }
+
 size_t ws_inverse(int d, int64_t N, int prec)
 {
     const size_t E = (size_t)d * d;
@@ -195,7 +199,9 @@ size_t ws_inverse(int d, int64_t N, int prec)
     const size_t refine = align_up((size_t)N * E * sizeof(float)) + align_up((size_t)Mr * E * 8) +
                           std::max(2 * align_up((size_t)Mr * E * 16),
                                    2 * align_up((size_t)Mr * E * 8) + align_up(mrc_fft_scratch_elems(Mr, (int)E) * 8));
-    return gj + ahat + psi32 + std::max(newton, refine);
+    // the residual product's prepared X (digit tiles and scales of A's spectrum)
+    const size_t xpre = xpre_used(d) ? align_up(mrc_tcp_prep_bytes(Mr, d)) + align_up(mrc_tcp_prep_scale_bytes(Mr)) : 0;
+    return gj + ahat + xpre + psi32 + std::max(newton, refine);
 }
 
 // Product kernel choices: 0..2 the FP32-pipe tile configurations 16/32/64
@@ -361,7 +367,7 @@ mrc_status conv_product(mrc_ctx *c, Arena &ar, int prec, const double *X, int64_
                         int r, int m, int cc, int64_t N, void *out, double sign, int eye_d, int add,
                         bool diag, cudaStream_t st, void *preX = nullptr, void *preT = nullptr,
                         void *y_hi = nullptr, int y_mode = SRC_REAL64, int out_mode = -1,
-                        const float *out_base = nullptr)
+                        const float *out_base = nullptr, const void *xpt = nullptr, const void *xps = nullptr)
 {
     const PrecOps &op = OPS[prec];
     const int64_t Mr = pow2ceil(N);
@@ -380,8 +386,17 @@ mrc_status conv_product(mrc_ctx *c, Arena &ar, int prec, const double *X, int64_
     FftDst dy{DST_CPLX, bY, (int)EY, 0, 0, 0, 1.0, 0, y_hi};
     if (!preX) CK(fft_any(c, prec, sx, dx, Mr, (int)EX, -1, bT, tw, st));
     CK(fft_any(c, prec, sy, dy, Mr, (int)EY, -1, bT, tw, st));
-    if (diag) CK(op.pairdiag(bX, bY, bC, Mr, r, cc, tw, MRC_TW_LOG, st));
-    else CK(pairmul_any(c, prec, bX, bY, bC, Mr, r, m, cc, tw, st));
+    if (diag) {
+        CK(op.pairdiag(bX, bY, bC, Mr, r, cc, tw, MRC_TW_LOG, st));
+    } else if (xpt) {  // double-float with X prepared (xpt: tiles, xps: scales)
+        SegParams<PairArgs> P{};
+        P.nseg = 1;
+        P.a[0] = mrc_tcp_args(xpt, bY, bC, Mr, r, tw, MRC_TW_LOG);
+        P.a[0].xs = xps;
+        CK(mrc_tcp_seg(1, P, c->cur_status, st));
+    } else {
+        CK(pairmul_any(c, prec, bX, bY, bC, Mr, r, m, cc, tw, st));
+    }
     FftSrc sc{SRC_CPLX, bC, 0, Mr, (int)EC, 0};
     FftDst dc{out_mode >= 0 ? out_mode : (add ? DST_REAL64_ADD : DST_REAL64), out, (int)EC, 0, N, 0,
               sign / (double)Mr, eye_d, nullptr, out_base};
@@ -444,12 +459,16 @@ mrc_status inverse_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A
     } sscope{c, c->cur_status};
     c->cur_status = status ? status : c->d_status;
     double *gjw = (double *)ar.take(sizeof(double) * 2 * E);
-    void *ahat = nullptr, *ascr = nullptr;
+    void *ahat = nullptr, *ascr = nullptr, *xpt = nullptr, *xps = nullptr;
     cudaStream_t sn = st;  // Newton levels
     if (prec == MRC_MIXED) {
         const int64_t Mr = pow2ceil(N);
         ahat = ar.take((size_t)Mr * E * 16);
         ascr = ar.take(mrc_fft_scratch_elems(Mr, (int)E) * 16);
+        if (xpre_used(d)) {
+            xpt = ar.take(mrc_tcp_prep_bytes(Mr, d));
+            xps = ar.take(mrc_tcp_prep_scale_bytes(Mr));
+        }
         cudaStream_t sa = st;
         if (split) {
             CK(cudaEventRecord(c->ev_fork, st));
@@ -462,6 +481,13 @@ mrc_status inverse_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A
         FftSrc sx{SRC_REAL64, A, 0, N, (int)E, 0};
         FftDst dx{DST_CPLX, ahat, (int)E, 0, 0, 0, 1.0, 0};
         CK(fft_any(c, PREC_DD, sx, dx, Mr, (int)E, -1, ascr, c->tw[PREC_DD], sa));
+        if (xpt) {  // the residual product's X: digit tiles and scales of A's spectrum
+            SegParams<PairArgs> P{};
+            P.nseg = 1;
+            P.a[0] = mrc_tcp_args(ahat, nullptr, xpt, Mr, d, c->tw[PREC_DD], MRC_TW_LOG);
+            P.a[0].xs = xps;
+            CK(mrc_tcp_prep(P, sa));
+        }
         if (split) CK(cudaEventRecord(c->ev_join, c->aux));
     }
     // mixed: psi_0 is kept in binary32 (every entry the FP32 levels write is
@@ -495,7 +521,8 @@ mrc_status inverse_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A
             // needs.  The first sweep reads psi_0 from its binary32 copy.
             const bool first = sw == 0;
             s = conv_product(c, ar, PREC_DD, A, N, first ? (const void *)psi32 : psi, N, d, d, d, N, rho32, -1.0, d,
-                             0, false, st, ahat, ascr, psi_hat32, first ? SRC_REAL32 : SRC_REAL64, DST_REAL32);
+                             0, false, st, ahat, ascr, psi_hat32, first ? SRC_REAL32 : SRC_REAL64, DST_REAL32, nullptr,
+                             xpt, xps);
             if (s != MRC_OK) return s;
             ar.off = mark2;
             // psi <- psi + psi * rho_L (Eq. (newton) from a full-length
@@ -714,6 +741,7 @@ struct BModel {
     float *A32 = nullptr, *psi32 = nullptr, *rho32 = nullptr;
     void *b0 = nullptr, *b1 = nullptr, *b2 = nullptr, *bt = nullptr;  // Newton level spectra and scratch
     void *ahat = nullptr, *ascr = nullptr;                              // double-float spectrum of A, scratch
+    void *xpt = nullptr, *xps = nullptr;                                // its prepared digit tiles and scales
     void *psihat32 = nullptr, *rY = nullptr, *rC = nullptr;             // residual
     void *cY = nullptr, *cC = nullptr, *cT = nullptr;                   // correction
 };
@@ -733,6 +761,10 @@ void bmodel_layout(BModel &m, int prec, char *base)
     }
     m.ahat = ar.take(Mr * E * 16);
     m.ascr = ar.take(mrc_fft_scratch_elems(m.Mr, m.E) * 16);
+    if (xpre_used(m.d)) {
+        m.xpt = ar.take(mrc_tcp_prep_bytes(m.Mr, m.d));
+        m.xps = ar.take(mrc_tcp_prep_scale_bytes(m.Mr));
+    }
     m.psi32 = (float *)ar.take(N * E * sizeof(float));
     const size_t mark = ar.off;
     m.A32 = (float *)ar.take(N * E * sizeof(float));
@@ -803,6 +835,7 @@ struct PairJob {
     void *zc;
     int d;
     int *status;
+    const void *xs = nullptr;  // double-float with X prepared: zx the tiles, xs the scales
 };
 
 // One square product per job, all of M points: the tensor-core ones of
@@ -812,12 +845,12 @@ struct PairJob {
 // configuration
 mrc_status product_stage(mrc_ctx *c, int prec, int64_t M, const std::vector<PairJob> &jobs, cudaStream_t st)
 {
-    std::vector<size_t> bycfg[3], tcp[5];
+    std::vector<size_t> bycfg[3], tcp[10];  // tensor-core groups: K-chunk count, + 5 with X prepared
     int *const old = c->cur_status;
     for (size_t i = 0; i < jobs.size(); ++i) {
-        const int ch = product_choice(c, prec, M, jobs[i].d);
+        const int ch = jobs[i].xs ? 3 : product_choice(c, prec, M, jobs[i].d);
         if (ch == 3 && jobs[i].d <= 64) {
-            tcp[(jobs[i].d + 15) / 16].push_back(i);
+            tcp[(jobs[i].d + 15) / 16 + (jobs[i].xs ? 5 : 0)].push_back(i);
         } else if (ch == 3) {
             c->cur_status = jobs[i].status;
             const cudaError_t e = launch_tensor(c, prec, jobs[i].zx, jobs[i].zy, jobs[i].zc, M, jobs[i].d, c->tw[prec], st);
@@ -828,7 +861,7 @@ mrc_status product_stage(mrc_ctx *c, int prec, int64_t M, const std::vector<Pair
         }
     }
     auto P = std::make_unique<SegParams<PairArgs>>();
-    for (int g = 0; g < 5; ++g)
+    for (int g = 0; g < 10; ++g)
         for (size_t i0 = 0; i0 < tcp[g].size(); i0 += MRC_SEG_MAX) {
             const size_t i1 = std::min(tcp[g].size(), i0 + (size_t)MRC_SEG_MAX);
             P->nseg = (int)(i1 - i0);
@@ -836,6 +869,7 @@ mrc_status product_stage(mrc_ctx *c, int prec, int64_t M, const std::vector<Pair
                 const PairJob &j = jobs[tcp[g][q]];
                 P->first[q - i0] = 0;  // every product has the same pair count (same M)
                 P->a[q - i0] = mrc_tcp_args(j.zx, j.zy, j.zc, M, j.d, c->tw[prec], MRC_TW_LOG);
+                P->a[q - i0].xs = j.xs;
             }
             CK(mrc_tcp_seg(prec == PREC_DD, *P, jobs[tcp[g][i0]].status, st));
         }
@@ -929,6 +963,25 @@ mrc_status batch_wave(mrc_ctx *c, std::vector<BModel> &W, int prec, int sweeps, 
                     jobs.push_back({FftSrc{SRC_REAL64, m.A, 0, m.N, m.E, 0}, FftDst{DST_CPLX, m.ahat, m.E, 0, 0, 0, 1.0, 0},
                                     m.E, m.ascr});
             if ((s = fft_stage(c, PREC_DD, Mr, -1, jobs, c->aux)) != MRC_OK) return s;
+            // the prepared X of the tensor-core residual products, per K-chunk count
+            std::vector<PairArgs> pj[5];
+            for (auto &m : W)
+                if (m.Mr == Mr && m.xpt) {
+                    PairArgs a = mrc_tcp_args(m.ahat, nullptr, m.xpt, Mr, m.d, c->tw[PREC_DD], MRC_TW_LOG);
+                    a.xs = m.xps;
+                    pj[(m.d + 15) / 16].push_back(a);
+                }
+            auto P = std::make_unique<SegParams<PairArgs>>();
+            for (int g = 0; g < 5; ++g)
+                for (size_t i0 = 0; i0 < pj[g].size(); i0 += MRC_SEG_MAX) {
+                    const size_t i1 = std::min(pj[g].size(), i0 + (size_t)MRC_SEG_MAX);
+                    P->nseg = (int)(i1 - i0);
+                    for (size_t q = i0; q < i1; ++q) {
+                        P->first[q - i0] = 0;
+                        P->a[q - i0] = pj[g][q];
+                    }
+                    CK(mrc_tcp_prep(*P, c->aux));
+                }
         }
         CK(cudaEventRecord(c->ev_join, c->aux));
     }
@@ -983,7 +1036,8 @@ mrc_status batch_wave(mrc_ctx *c, std::vector<BModel> &W, int prec, int sweeps, 
                 fy.push_back({FftSrc{first ? SRC_REAL32 : SRC_REAL64, first ? (const void *)b.psi32 : (const void *)b.psi,
                                      0, b.N, b.E, 0},
                               FftDst{DST_CPLX, b.rY, b.E, 0, 0, 0, 1.0, 0, b.psihat32}, b.E, b.ascr});
-                pr.push_back({b.ahat, b.rY, b.rC, b.d, b.status});
+                if (b.xpt) pr.push_back({b.xpt, b.rY, b.rC, b.d, b.status, b.xps});
+                else pr.push_back({b.ahat, b.rY, b.rC, b.d, b.status});
                 fc.push_back({FftSrc{SRC_CPLX, b.rC, 0, Mr, b.E, 0},
                               FftDst{DST_REAL32, b.rho32, b.E, 0, b.N, 0, -1.0 / (double)Mr, b.d}, b.E, b.ascr});
                 gy.push_back({FftSrc{SRC_REAL32, b.rho32, 0, b.N, b.E, 0}, FftDst{DST_CPLX, b.cY, b.E, 0, 0, 0, 1.0, 0},
@@ -1069,7 +1123,7 @@ static mrc_status ensure_split_streams(mrc_ctx *c)
     if (c->aux) return MRC_OK;
     int least = 0, greatest = 0;
     CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-    CK(cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, least));
+    CK(cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, greatest));
     mrc_prof_set_untimed(c->aux);
     CK(cudaStreamCreateWithPriority(&c->hi, cudaStreamNonBlocking, greatest));
     CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));

@@ -52,6 +52,9 @@ struct PairArgs {
     int logM;
     int64_t npairs;
     int r, m, c; // X: r x m, Y: m x c (pairdiag: Y is a c-vector, m unused)
+    // tensor-core double-float product with X prepared (mrc_tcp_prep): zx
+    // holds X's digit tiles, xs its per-pair scale factors; else null
+    const void *xs;
 };
 
 // Source / destination descriptors used by the host-side FFT driver.
@@ -190,6 +193,15 @@ cudaError_t mrc_pairmul_f32_tcp(const void *zx, const void *zy, void *zc, int64_
 // of the same ceil(d / 16)); a timeout is reported in *status
 cudaError_t mrc_tcp_seg(int dd_prec, const SegParams<PairArgs> &P, int *status, cudaStream_t st);
 PairArgs mrc_tcp_args(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log);
+// The double-float product with X prepared once (X is the spectrum of A,
+// the same in every residual sweep): mrc_tcp_prep writes, for every product
+// of P (zx: X's packed spectrum, zc: tiles out, xs: scales out;
+// mrc_tcp_prep_bytes and mrc_tcp_prep_scale_bytes each), X's digit tiles and
+// row scales; a product whose PairArgs carry xs (zx: the tiles) then splits
+// only Y.
+size_t mrc_tcp_prep_bytes(int64_t M, int d);
+size_t mrc_tcp_prep_scale_bytes(int64_t M);
+cudaError_t mrc_tcp_prep(const SegParams<PairArgs> &P, cudaStream_t st);
 // the kernels' bounded mbarrier wait on a barrier nothing arrives on: writes 6 to *status
 cudaError_t mrc_tc_wait_selftest(int *status, int spins, cudaStream_t st);
 

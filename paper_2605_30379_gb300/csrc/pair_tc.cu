@@ -89,6 +89,7 @@ struct TcL {
     static constexpr int S = TcP<T>::S, GMIN = TcP<T>::GMIN, NG = 2 * (S - 1) - GMIN + 1;
     static constexpr int NSLOT = TcP<T>::NSLOT, NF = TcP<T>::NF, PF = TcP<T>::PF;
     static constexpr int SUB = S * (A_TILE + 2 * B_TILE);  // digit tiles of one frequency and chunk
+    static constexpr int XT = S * A_TILE;                   // the X part of them (the sub-slot's start)
     static constexpr int SLOT = NF * SUB;
     static constexpr int XCH = 2 * NF * 64 * XLD * (int)sizeof(T);  // [NF][C_r, C_i][64][XLD]
     static constexpr int OFF_XCH = NSLOT * SLOT;
@@ -565,7 +566,11 @@ __device__ __forceinline__ void st_cx<float>(cx<float> *p, cx<float> v)
 // for every product of the launch (the chunks that hold k < d; d = 48 runs 3
 // of 4).  With the chunk count a run-time value the double-float product took
 // 46.9 ms at d = 64, N = 2^18 against 41.4.
-template <class T, int NCK>
+// XPRE (double-float): X's digit tiles and row scales were prepared once
+// (tcp_prep_kernel: X is the spectrum of A, the same in every residual
+// sweep); the split warps bulk-copy them into the slot (on xfull[slot]) and
+// split only Y.
+template <class T, int NCK, bool XPRE>
 __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(const __grid_constant__ SegParams<PairArgs> P, int *status)
 {
     using L = TcL<T>;
@@ -575,6 +580,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(const __grid_constant_
     float *scb = reinterpret_cast<float *>(smem + L::OFF_SC);  // [NB][scx, scy, fx, fy][64]
     unsigned *bxy = reinterpret_cast<unsigned *>(scb + 4 * 64 * L::NB);  // [2][bx, by][64]
     __shared__ __align__(8) unsigned long long bar_full[NSLOT], bar_empty[NSLOT], bar_tfull, bar_tempty, bar_done;
+    __shared__ __align__(8) unsigned long long bar_xfull[NSLOT];  // XPRE: the slot's X tiles landed
     __shared__ unsigned tslot;
     __shared__ volatile int abort_flag;
 
@@ -583,6 +589,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(const __grid_constant_
         for (int s = 0; s < NSLOT; ++s) {
             mbar_init(smem_u32(&bar_full[s]), NSPLIT);
             mbar_init(smem_u32(&bar_empty[s]), 1);
+            mbar_init(smem_u32(&bar_xfull[s]), 1);
         }
         mbar_init(smem_u32(&bar_tfull), 1);
         mbar_init(smem_u32(&bar_tempty), NEPI);
@@ -607,6 +614,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(const __grid_constant_
     auto zy_of = [&](int sg) { return reinterpret_cast<const cx<T> *>(P.a[sg].zy); };
     auto zc_of = [&](int sg) { return reinterpret_cast<cx<T> *>(P.a[sg].zc); };
     auto d_of = [&](int sg) { return P.a[sg].r; };
+    // the spectrum the X bounds come from: X's own, or (XPRE: X's scales are
+    // prepared) Y's again, whose X half of the bounds is then replaced
+    auto bx_of = [&](int sg) { return XPRE ? zy_of(sg) : zx_of(sg); };
+    auto xs_of = [&](int sg) { return reinterpret_cast<const float *>(P.a[sg].xs); };
     constexpr int nck = NCK;
     bool failed = false;
     auto give_up = [&]() {
@@ -650,14 +661,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(const __grid_constant_
             const int64_t f = blockIdx.x - (unsigned)s0 * npairs, gZ = (M - f) & (M - 1);
             float my = 0.0f;
             for (int n0 = 0; n0 < 4 * nck; n0 += 2) {
-                bnd_issue(bi, zx_of(s0), zy_of(s0), f, gZ, d_of(s0), t, n0);
+                bnd_issue(bi, bx_of(s0), zy_of(s0), f, gZ, d_of(s0), t, n0);
                 bnd_reduce(bi, bxy, my, t, n0);
             }
             atomicMax(&bxy[64 + (t & 63)], __float_as_uint(my));
         }
         bar_sync(BAR_SPLIT, NSPLIT);
-        if (t < 64 && blockIdx.x < total) bnd_scales(bxy, bxy + 64, scb, d_of((int)(blockIdx.x / npairs)), t);
+        if (t < 64 && blockIdx.x < total) {
+            const int s0 = (int)(blockIdx.x / npairs);
+            bnd_scales(bxy, bxy + 64, scb, d_of(s0), t);
+            if (XPRE) scb[128 + t] = xs_of(s0)[(int64_t)(blockIdx.x - (unsigned)s0 * npairs) * 128 + 64 + t];
+        }
         bar_sync(BAR_SPLIT, NSPLIT);
+        unsigned nx = 0;  // XPRE: X tile copies issued (chunk it's copy goes to slot it % NSLOT)
         for (unsigned gp = blockIdx.x; gp < total; gp += gridDim.x, ++pl) {
             const int sg = (int)(gp / npairs);
             const int64_t p = gp - (unsigned)sg * npairs, f = p, gZ = (M - p) & (M - 1);
@@ -676,7 +692,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(const __grid_constant_
             // bound rows n per gathering chunk (2, 4 or 8): the 4 nck row steps that cover
             // k < d over the nch - cb gathering chunks (nck per pass, half of them with PF = 1)
             const int ns = (L::PF == 1 ? 8 : 4) >> (npass(p) - 1);
-            load_x(raw, zx_of(sg), f, gZ, d_of(sg), 0, t);
+            if (!XPRE) load_x(raw, zx_of(sg), f, gZ, d_of(sg), 0, t);
             load_y(raw, zy_of(sg), f, gZ, d_of(sg), 0, t);
             for (int c = 0; c < nch; ++c, ++it) {
                 const cx<T> w = c < nck ? wf : wg;
@@ -692,17 +708,28 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(const __grid_constant_
                 const bool first = cn < nck;
                 const int64_t na = first ? f : gZ, nb = first ? gZ : f;
                 const int kn = (first ? cn : cn - nck) * KC;
-                if (gather) bnd_issue(bi, zx_of(sn), zy_of(sn), fn, gn, d_of(sn), t, n0);
-                if (!failed) split_chunk_x<T>(raw, sp, sc, w, t);
-                if (cn < nch) load_x(raw, zx_of(sg), na, nb, d_of(sg), kn, t);
+                if (gather) bnd_issue(bi, bx_of(sn), zy_of(sn), fn, gn, d_of(sn), t, n0);
+                if constexpr (XPRE) {
+                    if (t == 0 && !failed) {  // X tiles of this chunk: pass c / nck, chunk c % nck
+                        const int ps = c < nck ? 0 : 1, cc = c - ps * nck;
+                        const unsigned char *src = reinterpret_cast<const unsigned char *>(P.a[sg].zx) +
+                                                   ((size_t)(p * 2 + ps) * NCK + cc) * (size_t)L::XT;
+                        mbar_arrive_expect_tx(smem_u32(&bar_xfull[slot]), L::XT);
+                        bulk_g2s(smem_u32(sp), src, L::XT, smem_u32(&bar_xfull[slot]));
+                        ++nx;
+                    }
+                } else {
+                    if (!failed) split_chunk_x<T>(raw, sp, sc, w, t);
+                    if (cn < nch) load_x(raw, zx_of(sg), na, nb, d_of(sg), kn, t);
+                }
                 asm volatile("" ::: "memory");  // the loads above stay ahead of the Y digit stores
                 if (gather) {
                     bnd_reduce(bi, bn, myn, t, n0);
                     for (int u = 2; u < ns - 2; u += 2) {
-                        bnd_issue(bi, zx_of(sn), zy_of(sn), fn, gn, d_of(sn), t, n0 + u);
+                        bnd_issue(bi, bx_of(sn), zy_of(sn), fn, gn, d_of(sn), t, n0 + u);
                         bnd_reduce(bi, bn, myn, t, n0 + u);
                     }
-                    if (ns > 2) bnd_issue(bi, zx_of(sn), zy_of(sn), fn, gn, d_of(sn), t, n0 + ns - 2);
+                    if (ns > 2) bnd_issue(bi, bx_of(sn), zy_of(sn), fn, gn, d_of(sn), t, n0 + ns - 2);
                 }
                 if (!failed) split_chunk_y<T>(raw, sp, sc + 64, w, t);
                 if (cn < nch) load_y(raw, zy_of(sg), na, nb, d_of(sg), kn, t);
@@ -715,9 +742,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(const __grid_constant_
             }
             if (next) atomicMax(&bn[64 + (t & 63)], __float_as_uint(myn));
             if (bar_or(BAR_SPLIT, NSPLIT, failed || abort_flag)) break;  // the next pair's bounds complete
-            if (next && t < 64) bnd_scales(bn, bn + 64, scb + 4 * 64 * ((pl + 1) % L::NB), d_of(sn), t);
+            if (next && t < 64) {
+                float *scn = scb + 4 * 64 * ((pl + 1) % L::NB);
+                bnd_scales(bn, bn + 64, scn, d_of(sn), t);
+                if (XPRE) scn[128 + t] = xs_of(sn)[pn * 128 + 64 + t];
+            }
             if (t < 128) bxy[128 * (pl & 1) + t] = 0u;  // this pair's buffer: free for pair p + 2 grid
             bar_sync(BAR_SPLIT, NSPLIT);
+        }
+        if (XPRE && t == 0) {
+            // every X tile copy has landed before the CTA may exit (bounded waits)
+            for (int sl = 0; sl < NSLOT; ++sl)
+                if (nx > (unsigned)sl && !mbar_wait(smem_u32(&bar_xfull[sl]), ((nx - 1 - sl) / NSLOT) & 1)) give_up();
         }
     } else if (warp < WMMA) {
         // --------------------------------------------------------- epilogue
@@ -820,7 +856,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tcp_kernel(const __grid_constant_
                 fence_after();
                 for (int c = 0; c < nck; ++c, ++it) {
                     const int slot = it % NSLOT, use = it / NSLOT;
-                    if (abort_flag || !mbar_wait(smem_u32(&bar_full[slot]), use & 1)) {
+                    if (abort_flag || !mbar_wait(smem_u32(&bar_full[slot]), use & 1) ||
+                        (XPRE && !mbar_wait(smem_u32(&bar_xfull[slot]), use & 1))) {
                         give_up();
                         break;
                     }
@@ -880,10 +917,10 @@ int sm_count()
 
 template <class T>
 using TcpKernel = void (*)(SegParams<PairArgs>, int *);
-template <class T>
+template <class T, bool XPRE>
 TcpKernel<T> tcp_kernel_for(int nck)
 {
-    return nck <= 2 ? tcp_kernel<T, 2> : (nck == 3 ? tcp_kernel<T, 3> : tcp_kernel<T, 4>);
+    return nck <= 2 ? tcp_kernel<T, 2, XPRE> : (nck == 3 ? tcp_kernel<T, 3, XPRE> : tcp_kernel<T, 4, XPRE>);
 }
 
 template <class T>
@@ -898,10 +935,69 @@ cudaError_t tcp_launch(const SegParams<PairArgs> &P, int *status, cudaStream_t s
         bytes += M * 3.0 * d * d * sizeof(cx<T>);
         flops += 8.0 * d * d * d * (M + 1);
     }
+    const int nck = (P.a[0].r + KC - 1) / KC;
+    TcpKernel<T> k = tcp_kernel_for<T, false>(nck);
+    if constexpr (__is_same(T, dd))
+        if (P.a[0].xs) k = tcp_kernel_for<T, true>(nck);
     mrc_prof_pre(kclass, st);
-    tcp_kernel_for<T>((P.a[0].r + KC - 1) / KC)<<<grid, NTHREADS, TcL<T>::SMEM, st>>>(P, status);
+    k<<<grid, NTHREADS, TcL<T>::SMEM, st>>>(P, status);
     mrc_prof_post(kclass, st, bytes, flops);
     return cudaGetLastError();
+}
+
+// The double-float X operand prepared once: for every pair of every product
+// of P (zx: X's packed spectrum; zc: the tiles out; xs: the scales out), its
+// row scales (xs[p][0..63] = 2^-sigma_i for the split, [64..127] =
+// 2^(sigma_i - 1) for the output, from the same bounds as the product's) and
+// per pass and chunk the X digit tiles exactly as the split warps would
+// leave them in a slot.  CTA (gp, pass); one staging sub-slot in shared memory.
+template <int NCK>
+__global__ void __launch_bounds__(NSPLIT) tcp_prep_kernel(const __grid_constant__ SegParams<PairArgs> P)
+{
+    using L = TcL<dd>;
+    extern __shared__ __align__(1024) unsigned char stage[];  // [XT]
+    __shared__ unsigned bxy[128];
+    __shared__ float scb[256];
+    const PairArgs &a = P.a[0];
+    const int64_t M = a.M;
+    const unsigned npairs = (unsigned)a.npairs, gp = blockIdx.x;
+    const int pass = blockIdx.y, t = threadIdx.x;
+    const int sg = (int)(gp / npairs);
+    const int64_t p = gp - (unsigned)sg * npairs, f = p, gZ = (M - p) & (M - 1);
+    if (pass == 1 && (M - p) == p) return;  // the self-paired frequency has one pass
+    const PairArgs &as = P.a[sg];
+    const cx<dd> *ZX = reinterpret_cast<const cx<dd> *>(as.zx);
+    const int d = as.r;
+    if (t < 128) bxy[t] = 0u;
+    __syncthreads();
+    BndIn bi;
+    float my = 0.0f;
+    for (int n0 = 0; n0 < 4 * NCK; n0 += 2) {
+        bnd_issue(bi, ZX, ZX, f, gZ, d, t, n0);
+        bnd_reduce(bi, bxy, my, t, n0);
+    }
+    __syncthreads();
+    if (t < 64) bnd_scales(bxy, bxy + 64, scb, d, t);  // bxy + 64: unused column bounds
+    __syncthreads();
+    if (pass == 0 && t < 64) {
+        float *xs = reinterpret_cast<float *>(const_cast<void *>(as.xs)) + p * 128;
+        xs[t] = scb[t];
+        xs[64 + t] = scb[128 + t];
+    }
+    const cx<dd> *tw = reinterpret_cast<const cx<dd> *>(a.tw);
+    const cx<dd> wf = tw[f << (a.tw_log - a.logM - 1)];
+    const cx<dd> w = pass ? c_neg(c_conj(wf)) : wf;
+    const int64_t na = pass ? gZ : f, nb = pass ? f : gZ;
+    unsigned char *out = reinterpret_cast<unsigned char *>(as.zc) + (size_t)(p * 2 + pass) * NCK * (size_t)L::XT;
+    Raw<dd> raw;
+    for (int c = 0; c < NCK; ++c) {
+        load_x(raw, ZX, na, nb, d, c * KC, t);
+        split_chunk_x<dd>(raw, stage, scb, w, t);
+        __syncthreads();
+        for (int o = t * 16; o < L::XT; o += NSPLIT * 16)
+            *reinterpret_cast<uint4 *>(out + (size_t)c * L::XT + o) = *reinterpret_cast<const uint4 *>(stage + o);
+        __syncthreads();
+    }
 }
 
 PairArgs tcp_args(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log)
@@ -920,7 +1016,7 @@ template <class T>
 cudaError_t tcp_run(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,
                     int *status, cudaStream_t st, int kclass)
 {
-    SegParams<PairArgs> P;  // the launch's parameter block (one product)
+    SegParams<PairArgs> P{};  // the launch's parameter block (one product)
     P.nseg = 1;
     P.first[0] = 0;
     P.a[0] = tcp_args(zx, zy, zc, M, d, tw, tw_log);
@@ -934,14 +1030,45 @@ bool mrc_tcp_supported(int r, int m, int c) { return r == m && m == c && r >= 32
 cudaError_t mrc_tcp_init(void)
 {
     for (int k = 2; k <= 4; ++k) {
-        cudaError_t e = cudaFuncSetAttribute(tcp_kernel_for<dd>(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(tcp_kernel_for<dd, false>(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              TcL<dd>::SMEM);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(tcp_kernel_for<float>(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(tcp_kernel_for<dd, true>(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     TcL<dd>::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(tcp_kernel_for<float, false>(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      TcL<float>::SMEM);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+size_t mrc_tcp_prep_bytes(int64_t M, int d)
+{
+    const int64_t npairs = M >= 2 ? M / 2 + 1 : 1;
+    const size_t nck = (size_t)(d + KC - 1) / KC;
+    return (size_t)npairs * 2 * nck * (size_t)TcL<dd>::XT;
+}
+
+size_t mrc_tcp_prep_scale_bytes(int64_t M)
+{
+    const int64_t npairs = M >= 2 ? M / 2 + 1 : 1;
+    return (size_t)npairs * 128 * sizeof(float);
+}
+
+cudaError_t mrc_tcp_prep(const SegParams<PairArgs> &P, cudaStream_t st)
+{
+    if (P.nseg <= 0) return cudaSuccess;
+    const int nck = (P.a[0].r + KC - 1) / KC;
+    const dim3 grid((unsigned)(P.a[0].npairs * P.nseg), 2);
+    mrc_prof_pre(6, st);
+    if (nck <= 2) tcp_prep_kernel<2><<<grid, NSPLIT, TcL<dd>::XT, st>>>(P);
+    else if (nck == 3) tcp_prep_kernel<3><<<grid, NSPLIT, TcL<dd>::XT, st>>>(P);
+    else tcp_prep_kernel<4><<<grid, NSPLIT, TcL<dd>::XT, st>>>(P);
+    double bytes = 0;
+    for (int s = 0; s < P.nseg; ++s) bytes += (double)P.a[s].M * P.a[s].r * P.a[s].r * 16.0 + mrc_tcp_prep_bytes(P.a[s].M, P.a[s].r);
+    mrc_prof_post(6, st, bytes, 0);
+    return cudaGetLastError();
 }
 
 cudaError_t mrc_pairmul_dd_tcp(const void *zx, const void *zy, void *zc, int64_t M, int d, const void *tw, int tw_log,

@@ -82,6 +82,24 @@ __device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity, int sp
     return false;
 }
 
+// One arrival on the mbarrier that also expects `bytes` of asynchronous
+// copies to complete on it in the current phase
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned mbar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes)
+                 : "memory");
+}
+
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global memory into this CTA's shared memory, completing as
+// transaction bytes on the mbarrier
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
 // Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) of global
 // memory into L2, without a destination in shared memory
 __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
