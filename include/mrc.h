@@ -203,8 +203,8 @@ mrc_status mrc_inverse_host(mrc_ctx *ctx, int d, int64_t N, const double *A_host
  * correction stages group models by transform length pow2ceil(N).  Models
  * enter waves in decreasing cost (~ N d^2 (log2 N + d)) while the waves'
  * buffers (mrc_inverse_workspace_bytes per model) fit the budget: the
- * context cap if set, else min(96 GB, half the free device memory), at
- * least the largest model.  The whole batch is captured once into a CUDA
+ * context cap if set, else min(192 GB, three quarters of the device memory
+ * free besides the workspace), at least the largest model.  The whole batch is captured once into a CUDA
  * graph; a later call with the same (d, N, A, psi, prec, sweeps) lists
  * replays it with one launch on `stream`.  The context keeps the 8 most
  * recent graphs, and a workspace reallocation discards them.  The
@@ -348,9 +348,9 @@ mrc_status mrc_selftest_timeout(mrc_ctx *ctx, int spins, void *stream);
  * the summed device time (ms), the number of timed launches and the charged
  * bytes and flops, then switches recording off.  At most 8192 launches are
  * timed per begin/end; later launches are counted by mrc_launch_count only.
- * Launches on the context's low-priority side stream (the double-float
- * spectrum of A that a single-model mixed inverse computes while its Newton
- * levels run) are not timed: they overlap the critical path, so their event
+ * Launches on the context's side stream (the double-float spectrum of A and
+ * the residual product's prepared X that a mixed inverse computes while its
+ * Newton levels run) are not timed: they overlap the critical path, so their event
  * durations would include time spent waiting for SMs.  Not thread safe.
  */
 #define MRC_K_FFT_F64 1

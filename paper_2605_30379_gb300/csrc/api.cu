@@ -42,8 +42,9 @@ struct mrc_ctx {
     double *d_acc = nullptr;  // [4] norm accumulators
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // streams of the single-model mixed inverse, created on first use: the
-    // FP32 Newton levels on `hi` (highest priority) while the double-float
-    // spectrum of A is computed on `aux` (lowest priority)
+    // FP32 Newton levels on `hi` while the double-float spectrum of A (and
+    // its prepared digit tiles) are computed on `aux`, both at the highest
+    // priority
     cudaStream_t aux = nullptr, hi = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     // host-buffer inverse: copy stream and one event per uploaded row range
@@ -440,13 +441,15 @@ mrc_status newton_levels(mrc_ctx *c, Arena &ar, int prec, int d, int64_t N, cons
 bool valid_dN(int d, int64_t N) { return d >= 1 && d <= 512 && N >= 1 && N <= ((int64_t)1 << 20); }
 
 // Mixed precision: the double-float spectrum of A that every residual sweep
-// uses depends on A alone.  With `split` (single-model calls) it is computed
-// on the context's low-priority stream while the FP32 Newton levels run on
-// its high-priority one -- the double-float FFT keeps the FP32 pipes busy,
-// the FP32 passes mostly wait on memory, and the priorities let each Newton
-// kernel's CTAs go first instead of queueing behind the FFT's -- and `st`
-// waits for both before the first residual.  Without `split` (batched calls,
-// whose models already overlap on several streams) everything runs on `st`.
+// uses, and the residual product's prepared X, depend on A alone.  With
+// `split` (single-model calls) they are computed on the context's side
+// stream while the FP32 Newton levels run on its other one -- the
+// double-float FFT and the digit split keep the FP32 pipes busy, the FP32
+// passes mostly wait on memory; at equal priorities (d = 64, N = 2^18: step
+// 209.9 ms, against 216.7 with the side stream at the lowest priority, where
+// its work ran only in the gaps the levels left and finished late) -- and
+// `st` waits for both before the first residual.  Without `split` everything
+// runs on `st`.
 mrc_status inverse_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A, double *psi, int prec, int sweeps,
                         int *levels, cudaStream_t st, int *status = nullptr, bool split = false,
                         const RowWait *rw = nullptr)
@@ -950,7 +953,7 @@ mrc_status batch_wave(mrc_ctx *c, std::vector<BModel> &W, int prec, int sweeps, 
             CK(mrc_f64_to_f32_batch(*C, total, st));
         }
         // the double-float spectra of A that every residual sweep uses, by
-        // transform length, on the low-priority side stream while the FP32
+        // transform length, on the side stream while the FP32
         // levels run (as in the single-model inverse)
         mrc_status s = ensure_split_streams(c);
         if (s != MRC_OK) return s;
@@ -1388,8 +1391,8 @@ mrc_status mrc_inverse_batched(mrc_ctx *c, int nmodels, const int *d, const int6
 
     // Models in decreasing cost (~ N d^2 (log2 N + d), the FFT and product
     // terms of Prop 2.4) into waves whose buffers fit the budget: the context
-    // cap if set, else at most 96 GB and half the free device memory (but
-    // always room for the largest model)
+    // cap if set, else at most 192 GB and three quarters of the device memory
+    // free besides the workspace (but always room for the largest model)
     std::vector<BModel> bm(nmodels);
     size_t wmax = 0;
     for (int b = 0; b < nmodels; ++b) {
@@ -1411,10 +1414,10 @@ mrc_status mrc_inverse_batched(mrc_ctx *c, int nmodels, const int *d, const int6
     std::vector<int> order(nmodels);
     for (int b = 0; b < nmodels; ++b) order[b] = b;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return bm[x].cost > bm[y].cost; });
-    size_t budget = (size_t)96 << 30;
+    size_t budget = (size_t)192 << 30;
     {
         size_t fr = 0, tot = 0;
-        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) budget = std::min(budget, fr / 2 + c->ws_size / 2);
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) budget = std::min(budget, (fr + c->ws_size) / 4 * 3);
     }
     const size_t head = align_up(sizeof(int) * nmodels);
     if (c->cap) budget = std::min(budget, c->cap > head ? c->cap - head : 0);

@@ -5,7 +5,7 @@
 // mrc_profile_begin, CUDA events are recorded around each launch of that class
 // on its own stream, together with the algorithmic bytes and flops the launch
 // is charged with; mrc_profile_end sums them.  Launches on an untimed stream
-// (mrc_prof_set_untimed: the low-priority side stream whose kernels overlap
+// (mrc_prof_set_untimed: the side stream whose kernels overlap
 // the critical path, so that their event durations include time spent
 // waiting for SMs) are counted but not timed.  Not thread safe: profile one
 // host thread at a time.
