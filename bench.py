@@ -359,10 +359,7 @@ def run_mre(args, rank, world, local):
     torch.cuda.synchronize()
     launches = lib.mrc_launch_count() - l0
     pms, pn, pb, pf = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
-    if not batch:
-        lib.mrc_profile_end(ctypes.byref(pms), ctypes.byref(pn), ctypes.byref(pb), ctypes.byref(pf))
-    elif dominant in class_work:
-        pms.value, pn.value, pb.value, pf.value = class_work[dominant]
+    lib.mrc_profile_end(ctypes.byref(pms), ctypes.byref(pn), ctypes.byref(pb), ctypes.byref(pf))
     clocks = sampler.stop()
     ms_step = e0.elapsed_time(e1) / args.steps
     coeffs = N * d * d
@@ -398,7 +395,7 @@ def run_mre(args, rank, world, local):
     line = {"metric": "K_h coefficients/s (N*d^2), continuous-time transition function, mean-value rule",
             "value": coeffs / (ms_step * 1e-3), "unit": "coefficients/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak" if total_coeffs is None else "strong",
+            "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+dd" if args.prec == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "d": d, "N": N, "h": extra["h"], "prec": args.prec,
                        "l2": "inputs below L2 size (latency-bound case)", "parallelism": "single"},

@@ -205,8 +205,8 @@ size_t ws_inverse(int d, int64_t N, int prec)
     return gj + ahat + xpre + psi32 + std::max(newton, refine);
 }
 
-// Product kernel choices: 0..2 the FP32-pipe tile configurations 16/32/64
-// (pairmul_cfg), 3 the tensor-core digit kernel: for square 32 <= d <= 64
+// Product kernel choices: 0..2 and 4 the FP32-pipe tile configurations
+// 16/32/64 and 24 (pairmul_cfg), 3 the tensor-core digit kernel: for square 32 <= d <= 64
 // the pipelined one (pair_tc.cu; double-float or FP32), for double-float
 // 64 < d <= 512 the tiled one (ozaki_tc.cu).
 bool tensor_choice_exists(int prec, int r, int m, int c)
@@ -252,8 +252,8 @@ int tuned_choice(mrc_ctx *cx, int prec, const void *zx, const void *zy, void *zc
     auto it = cx->tune.find(key);
     if (it != cx->tune.end()) return it->second;
     if (cx->capturing) return -1;
-    int cands[4] = {0, 1, 2, 3};
-    const int nc = tensor_choice_exists(prec, r, m, c) ? 4 : 3;
+    int cands[5] = {0, 1, 2, 4, 3};
+    const int nc = tensor_choice_exists(prec, r, m, c) ? 5 : 4;
     float best = 1e30f;
     int pick = -1;
     for (int k = 0; k < nc; ++k) {
@@ -695,7 +695,7 @@ void tune_load(mrc_ctx *cx)
     unsigned long long k;
     int ch;
     while (fscanf(f, "%llu %d", &k, &ch) == 2)
-        if (ch >= 0 && ch <= ((k >> 62) ? 511 : 3)) cx->tune[(uint64_t)k] = ch;  // FFT plans / product choices
+        if (ch >= 0 && ch <= ((k >> 62) ? 511 : 4)) cx->tune[(uint64_t)k] = ch;  // FFT plans / product choices
     fclose(f);
 }
 
@@ -830,7 +830,7 @@ int product_choice(mrc_ctx *cx, int prec, int64_t M, int d)
         if (it != cx->tune.end()) return it->second;
     }
     if (tensor_choice_exists(prec, d, d, d) && (prec == PREC_DD || M >= 256)) return 3;
-    return d <= 16 ? 0 : (d <= 32 ? 1 : 2);
+    return d <= 16 ? 0 : (d <= 24 ? 4 : (d <= 32 ? 1 : 2));
 }
 
 struct PairJob {
@@ -848,7 +848,7 @@ struct PairJob {
 // configuration
 mrc_status product_stage(mrc_ctx *c, int prec, int64_t M, const std::vector<PairJob> &jobs, cudaStream_t st)
 {
-    std::vector<size_t> bycfg[3], tcp[10];  // tensor-core groups: K-chunk count, + 5 with X prepared
+    std::vector<size_t> bycfg[5], tcp[10];  // tensor-core groups: K-chunk count, + 5 with X prepared
     int *const old = c->cur_status;
     for (size_t i = 0; i < jobs.size(); ++i) {
         const int ch = jobs[i].xs ? 3 : product_choice(c, prec, M, jobs[i].d);
@@ -876,8 +876,8 @@ mrc_status product_stage(mrc_ctx *c, int prec, int64_t M, const std::vector<Pair
             }
             CK(mrc_tcp_seg(prec == PREC_DD, *P, jobs[tcp[g][i0]].status, st));
         }
-    const int bsz[3] = {16, 32, 64};
-    for (int cfg = 0; cfg < 3; ++cfg)
+    const int bsz[5] = {16, 32, 64, 0, 24};
+    for (int cfg = 0; cfg < 5; ++cfg)
         for (size_t i0 = 0; i0 < bycfg[cfg].size(); i0 += MRC_SEG_MAX) {
             const size_t i1 = std::min(bycfg[cfg].size(), i0 + (size_t)MRC_SEG_MAX);
             unsigned total = 0;

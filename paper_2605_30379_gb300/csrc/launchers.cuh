@@ -207,7 +207,8 @@ cudaError_t pairmul2_launch(const PairArgs &a, cudaStream_t st)
 }
 
 // product argument block and tile configuration: 0 = 16x16 (64 threads),
-// 1 = 32x32 (256), 2 = 64x64 (256); cfg < 0 picks by the larger output dimension
+// 1 = 32x32 (256), 2 = 64x64 (256), 4 = 24x24 (96: 17 <= d <= 24 fills 50 .. 100 %
+// of it against 28 .. 56 % of a 32x32 tile); cfg < 0 picks by the larger output dimension
 inline PairArgs pairmul_args(const void *zx, const void *zy, void *zc, int64_t M, int r, int m, int c, const void *tw,
                              int tw_log)
 {
@@ -220,12 +221,12 @@ inline PairArgs pairmul_args(const void *zx, const void *zy, void *zc, int64_t M
 inline int pairmul_cfg_for(int r, int c, int cfg)
 {
     const int mx = r > c ? r : c;
-    return cfg >= 0 ? cfg : (mx <= 16 ? 0 : (mx <= 32 ? 1 : 2));
+    return cfg >= 0 ? cfg : (mx <= 16 ? 0 : (mx <= 24 ? 4 : (mx <= 32 ? 1 : 2)));
 }
 // CTAs of one product: pairs x output tiles
 inline unsigned pairmul_ctas(const PairArgs &a, int cfg)
 {
-    const int b = cfg == 0 ? 16 : (cfg == 1 ? 32 : 64);
+    const int b = cfg == 0 ? 16 : (cfg == 1 ? 32 : (cfg == 4 ? 24 : 64));
     return (unsigned)a.npairs * (unsigned)(((a.r + b - 1) / b) * ((a.c + b - 1) / b));
 }
 
@@ -237,6 +238,7 @@ cudaError_t pairmul_run(const void *zx, const void *zy, void *zc, int64_t M, int
     cfg = pairmul_cfg_for(r, c, cfg);
     if (cfg == 0) return pairmul_launch<T, 16, 16, 16, 2, 2>(a, st);
     if (cfg == 1) return pairmul_launch<T, 32, 32, 16, 2, 2>(a, st);
+    if (cfg == 4) return pairmul_launch<T, 24, 24, 8, 3, 2>(a, st);
     // FP32, 64 x 64 tiles: the frequencies of a pair on two halves of the CTA
     // (half the registers per thread, two CTAs per SM: pairmul_f32 54.9 ->
     // 49.4 ms at d = 64, N = 2^18 against both frequencies in every thread)
@@ -254,6 +256,7 @@ cudaError_t pairmul_seg_run(int cfg, const SegParams<PairArgs> &P, unsigned ncta
     mrc_prof_pre(kclass_pair<T>(), st);
     if (cfg == 0) pairmul_seg_kernel<T, 16, 16, 16, 2, 2><<<nctas, 64, 0, st>>>(P);
     else if (cfg == 1) pairmul_seg_kernel<T, 32, 32, 16, 2, 2><<<nctas, 256, 0, st>>>(P);
+    else if (cfg == 4) pairmul_seg_kernel<T, 24, 24, 8, 3, 2><<<nctas, 96, 0, st>>>(P);
     else if constexpr (std::is_same<T, float>::value) pairmul2_seg_kernel<T, 64, 64, 8, 4, 4><<<nctas, 512, 0, st>>>(P);
     else pairmul_seg_kernel<T, 64, 64, 8, 4, 4><<<nctas, 256, 0, st>>>(P);
     mrc_prof_post(kclass_pair<T>(), st, bytes, flops);

@@ -950,7 +950,9 @@ cudaError_t tcp_launch(const SegParams<PairArgs> &P, int *status, cudaStream_t s
 // row scales (xs[p][0..63] = 2^-sigma_i for the split, [64..127] =
 // 2^(sigma_i - 1) for the output, from the same bounds as the product's) and
 // per pass and chunk the X digit tiles exactly as the split warps would
-// leave them in a slot.  CTA (gp, pass); one staging sub-slot in shared memory.
+// leave them in a slot.  One CTA per pair: the bounds and each chunk's raw
+// rows are read once for both passes (the second pass swaps the two rows and
+// takes the partner twiddle); one staging sub-slot in shared memory.
 template <int NCK>
 __global__ void __launch_bounds__(NSPLIT) tcp_prep_kernel(const __grid_constant__ SegParams<PairArgs> P)
 {
@@ -961,10 +963,10 @@ __global__ void __launch_bounds__(NSPLIT) tcp_prep_kernel(const __grid_constant_
     const PairArgs &a = P.a[0];
     const int64_t M = a.M;
     const unsigned npairs = (unsigned)a.npairs, gp = blockIdx.x;
-    const int pass = blockIdx.y, t = threadIdx.x;
+    const int t = threadIdx.x;
     const int sg = (int)(gp / npairs);
     const int64_t p = gp - (unsigned)sg * npairs, f = p, gZ = (M - p) & (M - 1);
-    if (pass == 1 && (M - p) == p) return;  // the self-paired frequency has one pass
+    const int np = (M - p) == p ? 1 : 2;  // the self-paired frequency has one pass
     const PairArgs &as = P.a[sg];
     const cx<dd> *ZX = reinterpret_cast<const cx<dd> *>(as.zx);
     const int d = as.r;
@@ -979,24 +981,32 @@ __global__ void __launch_bounds__(NSPLIT) tcp_prep_kernel(const __grid_constant_
     __syncthreads();
     if (t < 64) bnd_scales(bxy, bxy + 64, scb, d, t);  // bxy + 64: unused column bounds
     __syncthreads();
-    if (pass == 0 && t < 64) {
+    if (t < 64) {
         float *xs = reinterpret_cast<float *>(const_cast<void *>(as.xs)) + p * 128;
         xs[t] = scb[t];
         xs[64 + t] = scb[128 + t];
     }
     const cx<dd> *tw = reinterpret_cast<const cx<dd> *>(a.tw);
     const cx<dd> wf = tw[f << (a.tw_log - a.logM - 1)];
-    const cx<dd> w = pass ? c_neg(c_conj(wf)) : wf;
-    const int64_t na = pass ? gZ : f, nb = pass ? f : gZ;
-    unsigned char *out = reinterpret_cast<unsigned char *>(as.zc) + (size_t)(p * 2 + pass) * NCK * (size_t)L::XT;
+    const cx<dd> wg = c_neg(c_conj(wf));
+    unsigned char *out = reinterpret_cast<unsigned char *>(as.zc) + (size_t)p * 2 * NCK * (size_t)L::XT;
     Raw<dd> raw;
     for (int c = 0; c < NCK; ++c) {
-        load_x(raw, ZX, na, nb, d, c * KC, t);
-        split_chunk_x<dd>(raw, stage, scb, w, t);
-        __syncthreads();
-        for (int o = t * 16; o < L::XT; o += NSPLIT * 16)
-            *reinterpret_cast<uint4 *>(out + (size_t)c * L::XT + o) = *reinterpret_cast<const uint4 *>(stage + o);
-        __syncthreads();
+        load_x(raw, ZX, f, gZ, d, c * KC, t);
+        for (int ps = 0; ps < np; ++ps) {
+            if (ps == 1)  // the second pass: rows M - f and f
+                for (int n = 0; n < 4; ++n) {
+                    const cx<dd> v = raw.xa[n];
+                    raw.xa[n] = raw.xb[n];
+                    raw.xb[n] = v;
+                }
+            split_chunk_x<dd>(raw, stage, scb, ps ? wg : wf, t);
+            __syncthreads();
+            unsigned char *o = out + ((size_t)ps * NCK + c) * L::XT;
+            for (int q = t * 16; q < L::XT; q += NSPLIT * 16)
+                *reinterpret_cast<uint4 *>(o + q) = *reinterpret_cast<const uint4 *>(stage + q);
+            __syncthreads();
+        }
     }
 }
 
@@ -1060,7 +1070,7 @@ cudaError_t mrc_tcp_prep(const SegParams<PairArgs> &P, cudaStream_t st)
 {
     if (P.nseg <= 0) return cudaSuccess;
     const int nck = (P.a[0].r + KC - 1) / KC;
-    const dim3 grid((unsigned)(P.a[0].npairs * P.nseg), 2);
+    const unsigned grid = (unsigned)(P.a[0].npairs * P.nseg);
     mrc_prof_pre(6, st);
     if (nck <= 2) tcp_prep_kernel<2><<<grid, NSPLIT, TcL<dd>::XT, st>>>(P);
     else if (nck == 3) tcp_prep_kernel<3><<<grid, NSPLIT, TcL<dd>::XT, st>>>(P);
