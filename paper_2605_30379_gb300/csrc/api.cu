@@ -422,7 +422,7 @@ cudaError_t level_product(void *user, int prec, const void *zx, const void *zy, 
 // from the context workspace (the schedule itself is mrc_newton_levels).
 mrc_status newton_levels(mrc_ctx *c, Arena &ar, int prec, int d, int64_t N, const double *A, double *psi,
                          int64_t m0, int *levels, cudaStream_t st, const RowWait *rw = nullptr,
-                         float *A32 = nullptr, float *psi32 = nullptr)
+                         float *A32 = nullptr, float *psi32 = nullptr, int64_t a32_rows = 0)
 {
     const PrecOps &op = OPS[prec];
     const int E = d * d;
@@ -435,7 +435,7 @@ mrc_status newton_levels(mrc_ctx *c, Arena &ar, int prec, int d, int64_t N, cons
     b.b2 = ar.take((size_t)Mmax * E * op.cxb);
     b.bt = ar.take(mrc_fft_scratch_elems(Mmax, E) * op.cxb);
     return (mrc_status)mrc_newton_levels(prec, d, N, A, psi, m0, b, c->tw[prec], MRC_TW_LOG, level_fft,
-                                         level_product, c, st, rw, A32, psi32, levels);
+                                         level_product, c, st, rw, A32, psi32, levels, a32_rows);
 }
 
 bool valid_dN(int d, int64_t N) { return d >= 1 && d <= 512 && N >= 1 && N <= ((int64_t)1 << 20); }
@@ -463,6 +463,9 @@ mrc_status inverse_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A
     c->cur_status = status ? status : c->d_status;
     double *gjw = (double *)ar.take(sizeof(double) * 2 * E);
     void *ahat = nullptr, *ascr = nullptr, *xpt = nullptr, *xps = nullptr;
+    float *psi32 = nullptr, *A32 = nullptr;
+    size_t mark = 0;
+    int64_t a32_rows = 0;
     cudaStream_t sn = st;  // Newton levels
     if (prec == MRC_MIXED) {
         const int64_t Mr = pow2ceil(N);
@@ -471,6 +474,18 @@ mrc_status inverse_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A
         if (xpre_used(d)) {
             xpt = ar.take(mrc_tcp_prep_bytes(Mr, d));
             xps = ar.take(mrc_tcp_prep_scale_bytes(Mr));
+        }
+        // psi_0 is kept in binary32 (every entry the FP32 levels write is a
+        // binary32 number; the first m0 rows are rounded to it), and the FP32
+        // levels read a binary32 copy of A
+        psi32 = (float *)ar.take((size_t)N * E * sizeof(float));
+        mark = ar.off;
+        A32 = (float *)ar.take((size_t)N * E * sizeof(float));
+        if (!rw) {
+            // A is resident: one conversion before the side stream starts (level by
+            // level it ran beside the side stream's kernels and waited for SMs)
+            CK(mrc_f64_to_f32(A, A32, N * (int64_t)E, st));
+            a32_rows = N;
         }
         cudaStream_t sa = st;
         if (split) {
@@ -493,18 +508,14 @@ mrc_status inverse_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A
         }
         if (split) CK(cudaEventRecord(c->ev_join, c->aux));
     }
-    // mixed: psi_0 is kept in binary32 (every entry the FP32 levels write is
-    // a binary32 number; the first m0 rows are rounded to it)
-    float *psi32 = prec == MRC_MIXED ? (float *)ar.take((size_t)N * E * sizeof(float)) : nullptr;
     const int64_t m0 = base_size(d, N);
     if (rw) CK(rw->wait(sn, m0));
     CK(mrc_gauss_jordan(A, psi, gjw, d, status ? status : c->d_status, sn));
     CK(mrc_base_case(A, psi, d, m0, sn));
     if (psi32) CK(mrc_f64_to_f32(psi, psi32, m0 * (int64_t)E, sn));
-    const size_t mark = ar.off;
-    float *A32 = psi32 ? (float *)ar.take((size_t)N * E * sizeof(float)) : nullptr;
+    if (!psi32) mark = ar.off;
     mrc_status s = newton_levels(c, ar, prec == MRC_FP64 ? PREC_F64 : PREC_F32, d, N, A, psi, m0, levels, sn, rw,
-                                 A32, psi32);
+                                 A32, psi32, a32_rows);
     if (s != MRC_OK) return s;
     ar.off = mark;
     if (prec == MRC_MIXED) {
@@ -1085,11 +1096,11 @@ int64_t mrc_newton_maxM(int d, int64_t N)
 // (L = 2m): E = A*B (cyclic), R = -E[m, 2m), B[m, 2m) = (B*R)[0, m).
 int mrc_newton_levels(int prec, int d, int64_t N, const double *A, double *psi, int64_t m0, const NewtonBufs &b,
                       const void *tw, int tw_log, mrc_level_fft_fn fft, mrc_level_product_fn product, void *user,
-                      cudaStream_t st, const RowWait *rw, float *A32, float *psi32, int *levels)
+                      cudaStream_t st, const RowWait *rw, float *A32, float *psi32, int *levels, int64_t a32_rows)
 {
     const int E = d * d;
     const bool f32 = A32 && psi32;
-    int64_t conv = 0;  // rows of A32 converted so far
+    int64_t conv = a32_rows;  // rows of A32 converted so far
     int lv = 0;
     for (int64_t m = m0; m < N; m <<= 1, ++lv) {
         const int64_t M = m, m2 = std::min<int64_t>(2 * m, N);

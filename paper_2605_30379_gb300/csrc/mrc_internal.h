@@ -242,9 +242,12 @@ struct NewtonBufs {
 // converted here row range by row range, and psi is read and written in
 // binary32.  rw (nullable) delays each level until its rows of A arrived.
 // Returns 0 or 4 (a CUDA error, printed); *levels (nullable) = levels run.
+// a32_rows: rows of A32 already converted by the caller (the rest are
+// converted level by level, as each level first reads them)
 int mrc_newton_levels(int prec, int d, int64_t N, const double *A, double *psi, int64_t m0, const NewtonBufs &b,
                       const void *tw, int tw_log, mrc_level_fft_fn fft, mrc_level_product_fn product, void *user,
-                      cudaStream_t st, const RowWait *rw, float *A32, float *psi32, int *levels);
+                      cudaStream_t st, const RowWait *rw, float *A32, float *psi32, int *levels,
+                      int64_t a32_rows = 0);
 
 // misc.cu
 cudaError_t mrc_gauss_jordan(const double *A0, double *out, double *work, int d, int *status, cudaStream_t st);

@@ -60,9 +60,12 @@ def test_noalloc_matches_oracle_and_allocating_inverse_twice(libs):
     for (_, A, _, _), psi in zip(data, psis):  # warm-up: initialisation on this device
         assert call(A, psi) == 0
     torch.cuda.synchronize()
-    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
     for (_, A, ref_dev, ref), psi in zip(data, psis):
         psi.fill_(float("nan"))
+        # the device's free memory and torch's allocations around the call
+        # alone (torch's own temporaries below may reserve memory in between)
+        torch.cuda.synchronize()
+        free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
         assert call(A, psi) == 0
         torch.cuda.synchronize()
         assert torch.cuda.mem_get_info()[0] == free0
