@@ -42,10 +42,10 @@ struct mrc_ctx {
     double *d_acc = nullptr;  // [4] norm accumulators
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // streams of the single-model mixed inverse, created on first use: the
-    // FP32 Newton levels on `hi` while the double-float spectrum of A (and
+    // FP32 Newton levels on `lvl` while the double-float spectrum of A (and
     // its prepared digit tiles) are computed on `aux`, both at the highest
     // priority
-    cudaStream_t aux = nullptr, hi = nullptr;
+    cudaStream_t aux = nullptr, lvl = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     // host-buffer inverse: copy stream and one event per uploaded row range
     cudaStream_t cpy = nullptr;
@@ -491,9 +491,9 @@ mrc_status inverse_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A
         if (split) {
             CK(cudaEventRecord(c->ev_fork, st));
             CK(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
-            CK(cudaStreamWaitEvent(c->hi, c->ev_fork, 0));
+            CK(cudaStreamWaitEvent(c->lvl, c->ev_fork, 0));
             sa = c->aux;
-            sn = c->hi;
+            sn = c->lvl;
         }
         if (rw) CK(rw->wait(sa, N));
         FftSrc sx{SRC_REAL64, A, 0, N, (int)E, 0};
@@ -520,7 +520,7 @@ mrc_status inverse_impl(mrc_ctx *c, Arena &ar, int d, int64_t N, const double *A
     ar.off = mark;
     if (prec == MRC_MIXED) {
         if (split) {
-            CK(cudaEventRecord(c->ev_join2, c->hi));
+            CK(cudaEventRecord(c->ev_join2, c->lvl));
             CK(cudaStreamWaitEvent(st, c->ev_join2, 0));
             CK(cudaStreamWaitEvent(st, c->ev_join, 0));
         }
@@ -1139,7 +1139,7 @@ static mrc_status ensure_split_streams(mrc_ctx *c)
     CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
     CK(cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, greatest));
     mrc_prof_set_untimed(c->aux);
-    CK(cudaStreamCreateWithPriority(&c->hi, cudaStreamNonBlocking, greatest));
+    CK(cudaStreamCreateWithPriority(&c->lvl, cudaStreamNonBlocking, greatest));
     CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming));
@@ -1205,7 +1205,7 @@ mrc_status mrc_destroy(mrc_ctx *c)
         mrc_prof_set_untimed(nullptr);
         cudaStreamDestroy(c->aux);
     }
-    if (c->hi) cudaStreamDestroy(c->hi);
+    if (c->lvl) cudaStreamDestroy(c->lvl);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_join2) cudaEventDestroy(c->ev_join2);
